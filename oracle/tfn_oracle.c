@@ -1,0 +1,344 @@
+/*
+ * tfn_oracle.c -- plain, slow FP64 reference of Three-Filters-to-Normal (3F2N).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the oracle that the CUDA path is
+ * checked against.  Only tests/, __graft_entry__.smoke() and the CPU-baseline
+ * leg of bench.py may load it.  It shares no code, header, table or constant
+ * with the CUDA library and includes nothing from it.
+ *
+ * What it computes (Fan et al., "Three-Filters-to-Normal", RA-L 2021):
+ *   Sec. III, Eq. (intrinsic matrix): back-projection p = (Z(u-u0)/fx, Z(v-v0)/fy, Z).
+ *   Sec. III, text after Eq. (d1/z): gradient filters on the inverse-depth image 1/Z.
+ *   Sec. III, Eq. (nx2_ny2_nz2):      nx = fx d(1/Z)/du, ny = fy d(1/Z)/dv,
+ *                                    n_z = -Phi{ (dx_j nx + dy_j ny) / dz_j }, j = 1..8.
+ *   Sec. III, special case:          equal depths -> n = [0, 0, -1].
+ *   Sec. III, Eqs. (z_d), (dd_2_dz), (nx2_ny2_nz3): disparity form, Z = f t_c / d,
+ *                                    nx = dd/du, ny = dd/dv, same n_z rule.
+ *
+ * Readings where the paper is silent (each is listed in the design doc):
+ *   R1 a sample is valid iff it is finite and 2^-16 <= value <= 2^16 (depth in
+ *      any unit, disparity in pixels after scaling); anything else is a hole.
+ *   R2 a pixel is evaluable iff it is valid and every tap with a non-zero
+ *      weight in either gradient filter is inside the image and valid.
+ *   R3 gradients are correlations with [-1 0 1] (horizontal) and its transpose,
+ *      row/column weights FD (0 1 0)/2, Sobel (1 2 1)/8, Scharr (3 10 3)/32,
+ *      Prewitt (1 1 1)/6.
+ *   R4 candidates come from valid neighbours with dz != 0 only.
+ *   R5 Phi = median of an even count is the mean of the two middle values.
+ *   R6 if both gradients are exactly zero the normal is [0, 0, -1] (this holds
+ *      in particular when all neighbours share the centre depth).
+ *   R7 the output is n = -n'/|n'| with n' = (nx, ny, n_z): it faces the camera.
+ *   R8 invalid pixels get normal (0, 0, 0) and mask 0; evaluable ones mask 1.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { OR_DEPTH_F32 = 0, OR_DEPTH_F16 = 1, OR_DISP_U16 = 2, OR_DISP_F32 = 3, OR_DEPTH_F64 = 100 };
+enum { OR_FD = 0, OR_SOBEL = 1, OR_SCHARR = 2, OR_PREWITT = 3 };
+enum { OR_MEAN = 0, OR_MEDIAN = 1 };
+enum { OR_LITERAL = 0, OR_ALGEBRAIC = 1 };
+
+#define OR_OK 0
+#define OR_BAD_ARG 1
+
+static const double VALID_LO = 1.0 / 65536.0; /* 2^-16, reading R1 */
+static const double VALID_HI = 65536.0;       /* 2^16 */
+
+/* IEEE 754 binary16 -> double, from the format's definition. */
+static double half_to_double(uint16_t h)
+{
+    int sign = (h >> 15) & 1;
+    int expo = (h >> 10) & 0x1f;
+    int mant = h & 0x3ff;
+    double v;
+    if (expo == 0)
+        v = ldexp((double)mant, -24); /* subnormal: mant * 2^-14 * 2^-10 */
+    else if (expo == 31)
+        v = mant ? NAN : INFINITY;
+    else
+        v = ldexp((double)(mant + 1024), expo - 25);
+    return sign ? -v : v;
+}
+
+/* Reads the raw sample at (x, y) as a double, before the validity rule. */
+static double read_sample(const void *in, int64_t pitch, int type, double disp_scale, int x, int y)
+{
+    const char *row = (const char *)in + (int64_t)y * pitch;
+    switch (type) {
+    case OR_DEPTH_F32:
+    case OR_DISP_F32: return (double)((const float *)row)[x];
+    case OR_DEPTH_F16: return half_to_double(((const uint16_t *)row)[x]);
+    case OR_DISP_U16: {
+        uint16_t raw = ((const uint16_t *)row)[x];
+        return raw == 0 ? 0.0 : (double)raw * disp_scale;
+    }
+    case OR_DEPTH_F64: return ((const double *)row)[x];
+    }
+    return NAN;
+}
+
+static int is_valid(double s) { return isfinite(s) && s >= VALID_LO && s <= VALID_HI; }
+
+/* Row weights of the 3x3 gradient filters (reading R3); the horizontal filter
+ * is weight[dv] * [-1 0 1][du] / norm, the vertical one its transpose. */
+static void filter_weights(int grad, double w[3], double *norm)
+{
+    switch (grad) {
+    case OR_FD: w[0] = 0; w[1] = 1; w[2] = 0; *norm = 2; break;
+    case OR_SOBEL: w[0] = 1; w[1] = 2; w[2] = 1; *norm = 8; break;
+    case OR_SCHARR: w[0] = 3; w[1] = 10; w[2] = 3; *norm = 32; break;
+    default: w[0] = 1; w[1] = 1; w[2] = 1; *norm = 6; break;
+    }
+}
+
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+typedef struct {
+    const void *in;
+    int64_t pitch;
+    int H, W, type, grad, phi, form;
+    double disp_scale, fx, fy, u0, v0, tc;
+    double *normals;       /* 3 planes of H*W doubles */
+    uint8_t *mask;         /* H*W */
+    double *cands;         /* optional: 8 planes of H*W candidates (NAN = excluded) */
+    double *nprime;        /* optional: 3 planes of H*W unnormalised n' */
+} job_t;
+
+/* One pixel.  Writes normal, mask and (optionally) candidates / n'. */
+static void pixel(const job_t *J, int u, int v)
+{
+    const int64_t HW = (int64_t)J->H * J->W, idx = (int64_t)v * J->W + u;
+    const int disparity = (J->type == OR_DISP_U16 || J->type == OR_DISP_F32);
+    double s[3][3]; /* samples, s[dv+1][du+1] */
+    int ok[3][3];
+    for (int dv = -1; dv <= 1; ++dv)
+        for (int du = -1; du <= 1; ++du) {
+            int x = u + du, y = v + dv;
+            int inside = x >= 0 && x < J->W && y >= 0 && y < J->H;
+            double val = inside ? read_sample(J->in, J->pitch, J->type, J->disp_scale, x, y) : 0.0;
+            s[dv + 1][du + 1] = val;
+            ok[dv + 1][du + 1] = inside && is_valid(val);
+        }
+    double *n0 = J->normals, *n1 = J->normals + HW, *n2 = J->normals + 2 * HW;
+    if (J->cands)
+        for (int j = 0; j < 8; ++j) J->cands[j * HW + idx] = NAN;
+    if (J->nprime)
+        for (int c = 0; c < 3; ++c) J->nprime[c * HW + idx] = 0.0;
+
+    /* Reading R2: evaluable pixels. */
+    double wt[3], norm;
+    filter_weights(J->grad, wt, &norm);
+    int evaluable = ok[1][1];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            int du = b - 1, dv = a - 1;
+            /* tap weight in the horizontal filter: wt[dv+1]*du; vertical: wt[du+1]*dv */
+            int used = (wt[a] != 0 && du != 0) || (wt[b] != 0 && dv != 0);
+            if (used && !ok[a][b]) evaluable = 0;
+        }
+    if (!evaluable) {
+        n0[idx] = n1[idx] = n2[idx] = 0.0;
+        J->mask[idx] = 0;
+        return;
+    }
+
+    /* Sec. III: the filters run on the inverse-depth image 1/Z (depth form) or
+     * directly on the disparity image (disparity form, Eq. nx2_ny2_nz3). */
+    double img[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            img[a][b] = ok[a][b] ? (disparity ? s[a][b] : 1.0 / s[a][b]) : 0.0;
+    /* Correlation with [-1 0 1]: per row (column) the difference of the two
+     * outer taps, weighted by the row (column) weight.  Equal taps give an
+     * exact zero, so the special case below is decided exactly. */
+    double gu = 0, gv = 0;
+    for (int k = 0; k < 3; ++k) {
+        if (wt[k] == 0) continue;
+        gu += wt[k] * (img[k][2] - img[k][0]);
+        gv += wt[k] * (img[2][k] - img[0][k]);
+    }
+    gu /= norm;
+    gv /= norm;
+    J->mask[idx] = 1;
+    if (gu == 0.0 && gv == 0.0) { /* reading R6 / Sec. III special case */
+        n0[idx] = 0.0; n1[idx] = 0.0; n2[idx] = -1.0;
+        return;
+    }
+
+    /* Eq. (nx2_ny2_nz2) / (nx2_ny2_nz3). */
+    double nx, ny;
+    if (disparity) { nx = gu; ny = gv; }
+    else { nx = J->fx * gu; ny = J->fy * gv; }
+
+    /* Depth of every neighbour: Z directly, or Z = f t_c / d (Eq. z_d). */
+    double Z[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            Z[a][b] = ok[a][b] ? (disparity ? J->fx * J->tc / s[a][b] : s[a][b]) : 0.0;
+
+    double c[8];
+    int m = 0;
+    int j = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            int du = b - 1, dv = a - 1;
+            if (du == 0 && dv == 0) continue;
+            int slot = j++;
+            if (!ok[a][b]) continue;
+            double dz = Z[a][b] - Z[1][1];
+            if (dz == 0.0) continue; /* reading R4 */
+            double cand;
+            if (J->form == OR_LITERAL) {
+                /* Eq. (intrinsic matrix): back-project both points, r = q - p. */
+                double px = Z[1][1] * (u - J->u0) / J->fx, py = Z[1][1] * (v - J->v0) / J->fy;
+                double qx = Z[a][b] * (u + du - J->u0) / J->fx, qy = Z[a][b] * (v + dv - J->v0) / J->fy;
+                cand = ((qx - px) * nx + (qy - py) * ny) / dz;
+            } else {
+                /* Algebraic form: dx = (dz (u-u0) + Z_j du)/fx, dy likewise, so
+                 * c = [(u-u0) gu + (v-v0) gv + Z_j (du gu + dv gv)/dz] * k,
+                 * k = 1 (depth form) or 1/f (disparity form). */
+                double A = (u - J->u0) * gu + (v - J->v0) * gv;
+                double R = Z[a][b] * (du * gu + dv * gv) / dz;
+                cand = disparity ? (A + R) / J->fx : (A + R);
+            }
+            c[m++] = cand;
+            if (J->cands) J->cands[slot * HW + idx] = cand;
+        }
+
+    /* Phi: mean or median (reading R5).  m >= 1 here: a non-zero gradient
+     * needs two taps of different depth, and one of them differs from Z_i. */
+    double phi;
+    if (m == 0) {
+        phi = 0.0;
+    } else if (J->phi == OR_MEAN) {
+        double acc = 0;
+        for (int k = 0; k < m; ++k) acc += c[k];
+        phi = acc / m;
+    } else {
+        qsort(c, m, sizeof(double), cmp_double);
+        phi = (m & 1) ? c[m / 2] : 0.5 * (c[m / 2 - 1] + c[m / 2]);
+    }
+    double nz = -phi;
+    if (J->nprime) {
+        J->nprime[idx] = nx; J->nprime[HW + idx] = ny; J->nprime[2 * HW + idx] = nz;
+    }
+    double len = sqrt(nx * nx + ny * ny + nz * nz);
+    n0[idx] = -nx / len; /* reading R7 */
+    n1[idx] = -ny / len;
+    n2[idx] = -nz / len;
+}
+
+static void run_rows(const job_t *J, int y0, int y1)
+{
+    for (int v = y0; v < y1; ++v)
+        for (int u = 0; u < J->W; ++u) pixel(J, u, v);
+}
+
+static int check_args(const void *in, int64_t pitch, int H, int W, int type, int grad, int phi,
+                      int form, double fx, double fy, double tc, double disp_scale)
+{
+    if (!in || H < 1 || W < 1) return OR_BAD_ARG;
+    if (type != OR_DEPTH_F32 && type != OR_DEPTH_F16 && type != OR_DISP_U16 && type != OR_DISP_F32 &&
+        type != OR_DEPTH_F64)
+        return OR_BAD_ARG;
+    if (grad < 0 || grad > 3 || phi < 0 || phi > 1 || form < 0 || form > 1) return OR_BAD_ARG;
+    if (!(fx > 0) || !(fy > 0)) return OR_BAD_ARG;
+    int esz = type == OR_DEPTH_F64 ? 8 : (type == OR_DEPTH_F32 || type == OR_DISP_F32) ? 4 : 2;
+    if (pitch < (int64_t)W * esz) return OR_BAD_ARG;
+    if (type == OR_DISP_U16 || type == OR_DISP_F32) {
+        if (fx != fy || !(tc > 0)) return OR_BAD_ARG;
+        if (type == OR_DISP_U16 && !(disp_scale > 0)) return OR_BAD_ARG;
+    }
+    return OR_OK;
+}
+
+/*
+ * Normals of one frame.  `normals` receives 3 planes of H*W doubles (x, y, z),
+ * `mask` H*W bytes.  `cands` (8*H*W, neighbour raster order) and `nprime`
+ * (3*H*W) are optional diagnostics, NULL to skip.
+ */
+int tfn_oracle_normals(const void *in, int64_t pitch, int H, int W, int type, double disp_scale,
+                       double fx, double fy, double u0, double v0, double tc, int grad, int phi,
+                       int form, double *normals, uint8_t *mask, double *cands, double *nprime)
+{
+    int st = check_args(in, pitch, H, W, type, grad, phi, form, fx, fy, tc, disp_scale);
+    if (st || !normals || !mask) return st ? st : OR_BAD_ARG;
+    job_t J = {in, pitch, H, W, type, grad, phi, form, disp_scale, fx, fy, u0, v0, tc,
+               normals, mask, cands, nprime};
+    run_rows(&J, 0, H);
+    return OR_OK;
+}
+
+typedef struct {
+    job_t *jobs;
+    int n, next;
+    pthread_mutex_t lock;
+} pool_t;
+
+static void *worker(void *arg)
+{
+    pool_t *P = (pool_t *)arg;
+    for (;;) {
+        pthread_mutex_lock(&P->lock);
+        int k = P->next++;
+        pthread_mutex_unlock(&P->lock);
+        if (k >= P->n) return NULL;
+        run_rows(&P->jobs[k], 0, P->jobs[k].H);
+    }
+}
+
+/*
+ * Normals of n same-shaped frames stored back to back (frame stride =
+ * H * pitch bytes; outputs frame-major), spread over `threads` threads, one
+ * frame at a time per thread.
+ */
+int tfn_oracle_normals_batch(const void *in, int64_t pitch, int n, int H, int W, int type,
+                             double disp_scale, double fx, double fy, double u0, double v0,
+                             double tc, int grad, int phi, int form, double *normals,
+                             uint8_t *mask, int threads)
+{
+    int st = check_args(in, pitch, H, W, type, grad, phi, form, fx, fy, tc, disp_scale);
+    if (st || !normals || !mask || n < 0) return st ? st : OR_BAD_ARG;
+    if (threads < 1) threads = 1;
+    job_t *jobs = (job_t *)calloc(n > 0 ? n : 1, sizeof(job_t));
+    if (!jobs) return OR_BAD_ARG;
+    const int64_t HW = (int64_t)H * W;
+    for (int k = 0; k < n; ++k) {
+        job_t J = {(const char *)in + (int64_t)k * H * pitch, pitch, H, W, type, grad, phi, form,
+                   disp_scale, fx, fy, u0, v0, tc, normals + 3 * HW * k, mask + HW * k, NULL, NULL};
+        jobs[k] = J;
+    }
+    pool_t P = {jobs, n, 0, PTHREAD_MUTEX_INITIALIZER};
+    if (threads == 1) {
+        worker(&P);
+    } else {
+        pthread_t *t = (pthread_t *)calloc(threads, sizeof(pthread_t));
+        int started = 0;
+        for (int i = 0; i < threads; ++i)
+            if (pthread_create(&t[i], NULL, worker, &P) == 0) ++started;
+        if (started == 0) worker(&P);
+        for (int i = 0; i < started; ++i) pthread_join(t[i], NULL);
+        free(t);
+    }
+    free(jobs);
+    return OR_OK;
+}
+
+/* Angle in degrees between two 3-vectors, atan2(|a x b|, a.b) (Sec. IV-A, Eq.
+ * ea_ep defines psi = arccos of the normalised dot product; atan2 gives the
+ * same angle without the loss of accuracy of arccos near 0). */
+double tfn_oracle_angle_deg(const double a[3], const double b[3])
+{
+    double cx = a[1] * b[2] - a[2] * b[1];
+    double cy = a[2] * b[0] - a[0] * b[2];
+    double cz = a[0] * b[1] - a[1] * b[0];
+    double d = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+    return atan2(sqrt(cx * cx + cy * cy + cz * cz), d) * (180.0 / M_PI);
+}

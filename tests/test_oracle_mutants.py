@@ -1,0 +1,82 @@
+"""The oracle pins must catch plausible mistakes.
+
+Each case plants one mistake in a copy of the oracle source (never in the
+oracle itself), compiles it, and checks that at least one pin of
+test_oracle_pins (hand-derived values, exact plane recovery, sphere
+convergence order) rejects it.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from tests import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "tfn_oracle.c")
+
+MUTANTS = {
+    "candidate_sign": ("cand = ((qx - px) * nx + (qy - py) * ny) / dz;",
+                       "cand = ((qx - px) * nx - (qy - py) * ny) / dz;"),
+    "dropped_neighbour_offset": ("double qx = Z[a][b] * (u + du - J->u0) / J->fx",
+                                 "double qx = Z[a][b] * (u - J->u0) / J->fx"),
+    "wrong_focal_in_backprojection": ("double px = Z[1][1] * (u - J->u0) / J->fx, py = Z[1][1] * (v - J->v0) / J->fy;",
+                                      "double px = Z[1][1] * (u - J->u0) / J->fx, py = Z[1][1] * (v - J->v0) / J->fx;"),
+    "swapped_principal_point": ("double qx = Z[a][b] * (u + du - J->u0) / J->fx, qy = Z[a][b] * (v + dv - J->v0) / J->fy;",
+                                "double qx = Z[a][b] * (u + du - J->v0) / J->fx, qy = Z[a][b] * (v + dv - J->u0) / J->fy;"),
+    "convolution_not_correlation": ("gu += wt[k] * (img[k][2] - img[k][0]);",
+                                    "gu += wt[k] * (img[k][0] - img[k][2]);"),
+    "transposed_vertical_filter": ("gv += wt[k] * (img[2][k] - img[0][k]);",
+                                   "gv += wt[k] * (img[k][2] - img[k][0]);"),
+    "upper_median": ("phi = (m & 1) ? c[m / 2] : 0.5 * (c[m / 2 - 1] + c[m / 2]);",
+                     "phi = c[m / 2];"),
+    "mean_divides_by_eight": ("phi = acc / m;", "phi = acc / 8;"),
+    "no_dz_exclusion": ("if (dz == 0.0) continue; /* reading R4 */", ""),
+    "orientation_away_from_camera": ("n0[idx] = -nx / len; /* reading R7 */\n    n1[idx] = -ny / len;\n    n2[idx] = -nz / len;",
+                                     "n0[idx] = nx / len;\n    n1[idx] = ny / len;\n    n2[idx] = nz / len;"),
+    "nz_sign": ("double nz = -phi;", "double nz = phi;"),
+    "scharr_weights": ("case OR_SCHARR: w[0] = 3; w[1] = 10; w[2] = 3;",
+                       "case OR_SCHARR: w[0] = 3; w[1] = 10; w[2] = 4;"),
+    "sobel_weights": ("case OR_SOBEL: w[0] = 1; w[1] = 2; w[2] = 1;",
+                      "case OR_SOBEL: w[0] = 1; w[1] = 1; w[2] = 1;"),
+    # (Dropping f from Z = f t_c / d is no mistake: it rescales every depth
+    # alike and the estimated direction is invariant to a global depth scale.)
+    "disparity_gradient_on_inverse": ("(disparity ? s[a][b] : 1.0 / s[a][b])",
+                                      "(disparity ? 1.0 / s[a][b] : 1.0 / s[a][b])"),
+    "depth_instead_of_inverse": ("img[a][b] = ok[a][b] ? (disparity ? s[a][b] : 1.0 / s[a][b]) : 0.0;",
+                                 "img[a][b] = ok[a][b] ? s[a][b] : 0.0;"),
+    "prewitt_weights": ("default: w[0] = 1; w[1] = 1; w[2] = 1; *norm = 6;",
+                        "default: w[0] = 1; w[1] = 2; w[2] = 1; *norm = 6;"),
+    "nx_without_focal": ("else { nx = J->fx * gu; ny = J->fy * gv; }", "else { nx = gu; ny = J->fy * gv; }"),
+}
+
+
+def _pins_fail(lib):
+    if pins.check_golden(lib):
+        return True
+    for grad in pins.GRADS:
+        for phi in pins.PHIS:
+            if not (pins.plane_max_error(grad, phi, lib, H=16, W=20) < 1e-9):
+                return True
+    for phi in pins.PHIS:
+        o = pins.sphere_orders(phi, lib)
+        if not all(1.8 <= x <= 2.3 for x in o):
+            return True
+    return False
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    mutant = tmp_path / "mutant.c"
+    mutant.write_text(src.replace(old, new))
+    lib = oracle.open_library(oracle.compile_to(str(mutant), str(tmp_path / "libmutant.so")))
+    with np.errstate(all="ignore"):
+        assert _pins_fail(lib), f"mutant {name} passes every pin"
+
+
+def test_unmutated_copy_passes(tmp_path):
+    lib = oracle.open_library(oracle.compile_to(SRC, str(tmp_path / "libsame.so")))
+    assert not _pins_fail(lib)

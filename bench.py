@@ -1,0 +1,409 @@
+"""Benchmark of the GB300 Three-Filters-to-Normal path.
+
+One step = one pass of the whole estimator (decode, gradient filters,
+candidates, mean/median, normalisation, stores) over one batch of 256
+synthetic 480x640 FP32 depth frames (sigma = 0.0012 Z^2 noise, 3% holes),
+the batched workload of the paper's 480x640 datasets.  The default line is
+FD + mean (the paper's fastest variant, Sec. IV-B); other variants, the
+disparity and FP16 forms are reported under "variants".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own batch (replicas; frames are
+independent, so there is no data-path collective) and rank 0 prints one JSON
+line with the whole-job throughput.  --impl reference times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s and % of HBM-roofline at 480×640 (batched, FP32 vs FP16 I/O); p50/p99 latency"
+N_FRAMES = 256
+H, W = 480, 640
+BYTES_PER_PX = {"f32_in_f32_out": 4 + 12 + 1, "u16_in_f32_out": 2 + 12 + 1, "f16_in_f16_out": 2 + 6 + 1,
+                "f16_in_f16x4_out": 2 + 8 + 1}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--frames", type=int, default=N_FRAMES, help="frames per batch (profiling cases only)")
+    ap.add_argument("--grad", default="fd", choices=["fd", "sobel", "scharr", "prewitt"])
+    ap.add_argument("--phi", default="mean", choices=["mean", "median"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2005_08165_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def recorded_traffic(key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    if t.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    v = t.get(key)
+    return float(v) if v is not None else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------------------
+# the reference arm: the FP64 oracle on the host cores
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    import scenes
+    cores = os.cpu_count() or 1
+    sample = min(N_FRAMES, 2 * cores)
+    depth = scenes.noisy_batch(sample)
+    cam = scenes.CAMERA
+    for _ in range(args.warmup):
+        oracle.normals_batch(depth[:cores], **cam, grad="fd", phi="mean", threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.normals_batch(depth, **cam, grad="fd", phi="mean", threads=cores)
+    dt = time.perf_counter() - t0
+    fps = sample * args.steps / dt
+    desc = f"{sample} of the 256 noisy 480x640 frames per step, FD mean, FP64 oracle"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(fps, 3), "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "256 x 480x640 FP32 depth, sigma=0.0012 Z^2 noise, 3% holes; FD gradient, mean",
+                   "global_batch": N_FRAMES, "frame": "480x640", "parallelism": "host threads"},
+        "cpu_baseline": {"value": round(fps, 3), "unit": "frames/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": round(fps, 3), "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------------------------
+# our arm
+
+def cpu_baseline(seconds_target=12.0):
+    import oracle
+    import scenes
+    cores = os.cpu_count() or 1
+    depth = scenes.noisy_batch(cores)
+    t0 = time.perf_counter()
+    oracle.normals_batch(depth[:cores], **scenes.CAMERA, grad="fd", phi="mean", threads=cores)
+    one = time.perf_counter() - t0
+    reps = max(1, int(seconds_target / max(one * cores, 1e-3)))
+    n = min(N_FRAMES, cores * max(1, reps))
+    depth = scenes.noisy_batch(n)
+    t0 = time.perf_counter()
+    oracle.normals_batch(depth, **scenes.CAMERA, grad="fd", phi="mean", threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": round(n / dt, 3), "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} of the 256 noisy 480x640 frames, FD mean, FP64 oracle on {cores} threads "
+                      f"({dt:.1f} s wall)"}
+
+
+def time_launches(torch, fn, steps, warmup, stream):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for k in range(steps):
+        fn()
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    total_ms = ev[0].elapsed_time(ev[steps])
+    return total_ms, per
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2005_08165_gb300 as tfn
+    import scenes
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+        local = 0
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = tfn.Context(local)
+
+    # inputs resident in HBM: 256 x 1.2 MB (315 MB in, 1.0 GB out) -- far beyond the 129 MB L2
+    nf = args.frames
+    depth = scenes.noisy_batch(nf, seed0=1000 + 10000 * rank)
+    d = tfn.empty_image(depth.shape, torch.float32, dev)
+    d.copy_(torch.from_numpy(depth))
+    normals = tfn.empty_normals(H, W, "f32", dev, lead=(nf,))
+    masks = tfn.empty_image((nf, H, W), torch.uint8, dev)
+    ins = [d[k] for k in range(nf)]
+    outs = [normals[k] for k in range(nf)]
+    mks = [masks[k] for k in range(nf)]
+    cam = scenes.CAMERA
+
+    def step(grad=args.grad, phi=args.phi):
+        ctx.normals_batch(ins, cam, grad=grad, phi=phi, normals=outs, masks=mks, stream=stream)
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        total_ms, per = time_launches(torch, step, args.steps, 0, stream)
+        if world > 1:
+            torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    status = ctx.device_status()
+    ms_step = total_ms / args.steps
+    fps = world * nf * args.steps / (total_ms * 1e-3)
+    launch_ms = statistics.mean(per)
+    px = nf * H * W
+    achieved = BYTES_PER_PX["f32_in_f32_out"] * px / (launch_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = recorded_traffic(f"{args.grad}_{args.phi}_f32_b{nf}")
+
+    result = None
+    if rank == 0:
+        # end to end through the C ABI with host buffers: pinned in, pinned out,
+        # host<->device copies inside the timed region
+        hin = [torch.from_numpy(depth[k]).pin_memory() for k in range(nf)]
+        hout = torch.empty((nf, 3, H, W), dtype=torch.float32).pin_memory()
+        hmask = torch.empty((nf, H, W), dtype=torch.uint8).pin_memory()
+        houts = [hout[k] for k in range(nf)]
+        hmks = [hmask[k] for k in range(nf)]
+
+        def e2e_step():
+            ctx.normals_batch_host(hin, cam, houts, hmks, grad=args.grad, phi=args.phi, stream=stream)
+
+        e2e = None
+        if not args.no_e2e:
+            e2e_steps = 8
+            for _ in range(2):
+                e2e_step()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                e2e_step()
+            e2e_dt = time.perf_counter() - t0
+            e2e = {"value": round(nf * e2e_steps / e2e_dt, 1), "unit": "frames/s",
+                   "h2d_bytes_per_step": nf * H * W * 4, "d2h_bytes_per_step": nf * H * W * 13}
+
+        variants = {}
+        if not args.no_variants:
+            for grad in ("fd", "sobel", "scharr", "prewitt"):
+                for phi in ("mean", "median"):
+                    if (grad, phi) == (args.grad, args.phi):
+                        continue
+                    tot, pv = time_launches(torch, lambda: step(grad, phi), max(5, args.steps // 2), 3, stream)
+                    lm = statistics.mean(pv)
+                    variants[f"{grad}_{phi}_f32"] = {
+                        "frames_per_s": round(nf / (lm * 1e-3), 1),
+                        "hbm_gbs": round(BYTES_PER_PX["f32_in_f32_out"] * px / (lm * 1e-3) / 1e9, 1)}
+            variants.update(run_forms(torch, tfn, ctx, stream, dev, max(5, args.steps // 2)))
+
+        line = {
+            "metric": METRIC, "value": round(fps, 1), "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{nf} x 480x640 FP32 depth, sigma=0.0012 Z^2 noise, 3% holes; "
+                                   f"{args.grad} gradient, {args.phi}; FP32 planar normals + u8 mask out",
+                       "global_batch": nf * world, "frame": "480x640", "gradient": args.grad, "phi": args.phi,
+                       "l2": "inputs (315 MB) and outputs (1.0 GB) exceed the 129 MB L2; no flush",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                         else "fallback", "algorithmic_bytes_per_px": 17,
+                         "launch_ms": round(launch_ms, 4)},
+            "e2e": e2e,
+            "clocks": clk.summary(),
+            "gpu_launches": args.steps,
+            "device_status": status,
+            "variants": variants,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        result = line
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    ctx.close()
+    if result is not None:
+        print(json.dumps(result), flush=True)
+    return 0
+
+
+def run_forms(torch, tfn, ctx, stream, dev, steps):
+    """Disparity (u16, 1/16 px, median) and FP16 precision forms, 256 frames each."""
+    import numpy as np
+
+    import scenes
+    out = {}
+    px = N_FRAMES * H * W
+    raw = scenes.disparity_batch(N_FRAMES)
+    dd = tfn.empty_image(raw.shape, torch.int16, dev)
+    dd.copy_(torch.from_numpy(raw.view(np.int16)))
+    nrm = tfn.empty_normals(H, W, "f32", dev, lead=(N_FRAMES,))
+    msk = tfn.empty_image((N_FRAMES, H, W), torch.uint8, dev)
+    st = scenes.STEREO
+    cam = dict(fx=st["f"], fy=st["f"], u0=st["u0"], v0=st["v0"], baseline=st["baseline"])
+    ins = [dd[k] for k in range(N_FRAMES)]
+
+    def disp_step():
+        ctx.normals_batch(ins, cam, grad="fd", phi="median", disparity=True,
+                          normals=[nrm[k] for k in range(N_FRAMES)], masks=[msk[k] for k in range(N_FRAMES)],
+                          stream=stream)
+
+    tot, pv = time_launches(torch, disp_step, steps, 3, stream)
+    lm = statistics.mean(pv)
+    out["disparity_u16_fd_median"] = {"frames_per_s": round(N_FRAMES / (lm * 1e-3), 1),
+                                      "hbm_gbs": round(BYTES_PER_PX["u16_in_f32_out"] * px / (lm * 1e-3) / 1e9, 1)}
+    del dd, nrm
+    depth16 = scenes.render_batch(3000, N_FRAMES, scenes.Recipe()).astype(np.float16)
+    d16 = tfn.empty_image(depth16.shape, torch.float16, dev)
+    d16.copy_(torch.from_numpy(depth16))
+    for fmt, key in (("f16", "f16_in_f16_out"), ("bf16", "f16_in_f16_out"), ("f16x4", "f16_in_f16x4_out")):
+        o = tfn.empty_normals(H, W, fmt, dev, lead=(N_FRAMES,))
+        ins16 = [d16[k] for k in range(N_FRAMES)]
+
+        def f16_step():
+            ctx.normals_batch(ins16, scenes.CAMERA, grad="fd", phi="mean", output=fmt,
+                              normals=[o[k] for k in range(N_FRAMES)], masks=[msk[k] for k in range(N_FRAMES)],
+                              stream=stream)
+
+        tot, pv = time_launches(torch, f16_step, steps, 3, stream)
+        lm = statistics.mean(pv)
+        out[f"fp16_in_{fmt}_out_fd_mean"] = {"frames_per_s": round(N_FRAMES / (lm * 1e-3), 1),
+                                             "hbm_gbs": round(BYTES_PER_PX[key] * px / (lm * 1e-3) / 1e9, 1)}
+        del o
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,178 @@
+/*
+ * tfn.h -- C ABI of the GB300 Three-Filters-to-Normal library (libtfn.so).
+ *
+ * The library computes per-pixel unit surface normals and a validity mask
+ * from a depth or disparity image, following Fan et al., "Three-Filters-to-
+ * Normal: An Accurate and Ultrafast Surface Normal Estimator" (RA-L 2021):
+ *
+ *   Sec. III, Eq. (intrinsic matrix)   pinhole back-projection with fx, fy, u0, v0;
+ *   Sec. III, Eq. (d1/z_to_du_dv) and the text after it: a horizontal and a
+ *                                      vertical gradient filter on 1/Z;
+ *   Sec. III, Eq. (nx2_ny2_nz2)        nx = fx d(1/Z)/du, ny = fy d(1/Z)/dv,
+ *                                      n_z = -Phi{(dx_j nx + dy_j ny)/dz_j}, j = 1..8,
+ *                                      Phi = mean or median (the third filter);
+ *   Sec. III, special case             equal depths -> n = [0, 0, -1];
+ *   Sec. III, Eqs. (z_d), (nx2_ny2_nz3) the same estimator on a disparity image.
+ *
+ * Readings where the paper is silent (holes, borders, orientation, the
+ * median of an even count) are fixed as follows and are identical in the
+ * CPU reference used by the tests:
+ *   - a sample is a hole unless it is finite and 2^-16 <= value <= 2^16
+ *     (TFN_DISP_U16: unless the raw value is non-zero);
+ *   - a pixel is evaluable iff it and every tap of both gradient filters are
+ *     inside the image and not holes (FD: the 4 axis neighbours; Sobel,
+ *     Scharr, Prewitt: all 8); other pixels get normal (0,0,0), mask 0;
+ *   - neighbours that are holes or have the centre's depth give no candidate;
+ *   - the median of an even count is the mean of the two middle candidates;
+ *   - if both gradients are exactly zero the normal is [0, 0, -1];
+ *   - the normal is n = -n'/|n'|, n' = (nx, ny, n_z): it faces the camera.
+ *
+ * Memory.  Every image pointer in a tfn_frame is a DEVICE pointer owned by
+ * the caller; the library never frees it.  Rows of every image must start on
+ * 16-byte boundaries (pointer and pitches multiples of 16 bytes), else
+ * TFN_ERR_MISALIGNED.  The context owns only its scratch (frame descriptors,
+ * TMA tensor maps, staging buffers of the host-buffer path, a status word).
+ *
+ * Streams and errors.  Calls that take a stream validate their arguments
+ * synchronously, return a status, and then enqueue work on that stream
+ * (NULL = legacy default stream); outputs are valid once the stream reaches
+ * that point.  No C++ exception crosses the ABI.  A context is not
+ * thread-safe: use one per host thread or lock around it.  A context uses the
+ * CUDA device that was current when it was created; calls switch to that
+ * device for their duration.
+ */
+#ifndef TFN_H
+#define TFN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *tfn_stream; /* a cudaStream_t */
+typedef struct tfn_ctx tfn_ctx;
+
+typedef enum tfn_status {
+    TFN_OK = 0,
+    TFN_ERR_INVALID_ARG = 1,   /* null pointer, bad size, non-finite intrinsics, bad enum */
+    TFN_ERR_UNSUPPORTED = 2,   /* a valid but unsupported combination (disparity with fx != fy) */
+    TFN_ERR_MISALIGNED = 3,    /* a pointer or pitch not a multiple of 16 bytes */
+    TFN_ERR_OUT_OF_MEMORY = 4, /* scratch would exceed the context's memory budget */
+    TFN_ERR_CUDA = 5,          /* a CUDA runtime/driver call failed (see tfn_last_cuda_error) */
+    TFN_ERR_TIMEOUT = 6,       /* a host-side wait ran out of time */
+    TFN_ERR_CANCELLED = 7,     /* a request was cancelled before it ran */
+    TFN_ERR_BUSY = 8,          /* admission refused: no slot or memory free right now */
+    TFN_ERR_DEVICE = 9         /* a kernel reported a failed bounded wait (tfn_device_status) */
+} tfn_status;
+
+/* Input sample types. */
+typedef enum tfn_input {
+    TFN_DEPTH_F32 = 0, /* depth Z, any length unit, float32 */
+    TFN_DEPTH_F16 = 1, /* depth Z, IEEE binary16 */
+    TFN_DISP_U16 = 2,  /* stereo disparity, unsigned 16-bit fixed point (0 = hole) */
+    TFN_DISP_F32 = 3   /* stereo disparity in pixels, float32 */
+} tfn_input;
+
+/* Gradient filters (Sec. III; Sec. IV-B compares them): correlation with
+ * [-1 0 1] horizontally (its transpose vertically), row weights
+ * FD (0 1 0), Sobel (1 2 1), Scharr (3 10 3), Prewitt (1 1 1). */
+typedef enum tfn_grad { TFN_GRAD_FD = 0, TFN_GRAD_SOBEL = 1, TFN_GRAD_SCHARR = 2, TFN_GRAD_PREWITT = 3 } tfn_grad;
+
+/* Phi of Eq. (nx2_ny2_nz2). */
+typedef enum tfn_phi { TFN_PHI_MEAN = 0, TFN_PHI_MEDIAN = 1 } tfn_phi;
+
+/* Output layouts.  Planar: three planes (x, y, z) of H rows each, element
+ * type float32 / float16 / bfloat16.  Packed: one plane of 4 x 16-bit per
+ * pixel (x, y, z, 0). */
+typedef enum tfn_output {
+    TFN_OUT_F32 = 0,
+    TFN_OUT_F16 = 1,
+    TFN_OUT_BF16 = 2,
+    TFN_OUT_F16X4 = 3,
+    TFN_OUT_BF16X4 = 4
+} tfn_output;
+
+/* Pinhole intrinsics (Sec. III, Eq. intrinsic matrix), in pixels.  For
+ * disparity input fx must equal fy (= f of Eq. z_d) and `baseline` is the
+ * stereo baseline t_c (> 0); both cancel from the normal's direction. */
+typedef struct tfn_camera {
+    float fx, fy, u0, v0;
+    float baseline;
+} tfn_camera;
+
+/* One image and where its results go.  All pointers are device pointers. */
+typedef struct tfn_frame {
+    const void *input;            /* height rows of input_pitch bytes */
+    int64_t input_pitch;          /* bytes, multiple of 16, >= width * sample size */
+    int32_t height, width;        /* each >= 1 and <= 32768 */
+    int32_t input_type;           /* tfn_input */
+    float disp_scale;             /* pixels per raw unit for TFN_DISP_U16 (e.g. 1/16) */
+    tfn_camera cam;
+    void *normals;                /* planar: plane c at normals + c * normals_plane_stride */
+    int64_t normals_pitch;        /* bytes per row, multiple of 16 */
+    int64_t normals_plane_stride; /* bytes between planes (planar layouts), multiple of 16 */
+    uint8_t *mask;                /* height rows of mask_pitch bytes: 1 = evaluable, 0 = not */
+    int64_t mask_pitch;           /* bytes, multiple of 16 */
+} tfn_frame;
+
+/* Method selection. */
+typedef struct tfn_method {
+    int32_t grad;   /* tfn_grad */
+    int32_t phi;    /* tfn_phi */
+    int32_t output; /* tfn_output */
+    int32_t flags;  /* TFN_FLAG_* */
+} tfn_method;
+
+/* Compute every pixel on the compensated (double-float) path instead of only
+ * the rare pixels whose FP32 error bound is too loose.  For testing. */
+#define TFN_FLAG_REFINE_ALL 1
+
+/* ---- status and context ------------------------------------------------ */
+
+/* Static string for a status code. */
+const char *tfn_status_string(tfn_status status);
+
+/* Library version string. */
+const char *tfn_version(void);
+
+/* Text of the last CUDA error seen by this thread (static storage). */
+const char *tfn_last_cuda_error(void);
+
+/* Creates a context on `device` (-1: the current device).  Scratch that the
+ * context allocates never exceeds `mem_budget_bytes` (0: no limit).  On
+ * failure *ctx is NULL. */
+tfn_status tfn_create(tfn_ctx **ctx, int device, size_t mem_budget_bytes);
+
+/* Releases the context's scratch; waits for its work to finish. NULL is a no-op. */
+tfn_status tfn_destroy(tfn_ctx *ctx);
+
+/* ---- the estimator --------------------------------------------------------- */
+
+/* Normals of one frame: Sec. III end to end, one fused kernel launch. */
+tfn_status tfn_normals(tfn_ctx *ctx, const tfn_frame *frame, const tfn_method *method, tfn_stream stream);
+
+/* Normals of n frames (any mix of sizes, input types and intrinsics) in one
+ * persistent launch that walks a tile queue spanning all frames.  Frame
+ * descriptors are uploaded through the context's scratch; a call with the
+ * same frames and method as the previous one reuses them. */
+tfn_status tfn_normals_batch(tfn_ctx *ctx, const tfn_frame *frames, int n, const tfn_method *method,
+                             tfn_stream stream);
+
+/* Same as tfn_normals_batch, but every pointer in `frames` is a HOST pointer
+ * (page-locked memory is fastest).  The context stages the frames through
+ * device buffers in chunks, overlapping host-to-device copies, kernels and
+ * device-to-host copies; returns after every output is in host memory. */
+tfn_status tfn_normals_batch_host(tfn_ctx *ctx, const tfn_frame *frames, int n, const tfn_method *method,
+                                  tfn_stream stream);
+
+/* Reads and clears the device status word that kernels of this context set
+ * when a bounded wait gave up (0: none).  Synchronises `stream`. */
+tfn_status tfn_device_status(tfn_ctx *ctx, uint32_t *bits, tfn_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TFN_H */

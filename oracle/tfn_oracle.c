@@ -17,7 +17,8 @@
  *
  * Readings where the paper is silent (each is listed in the design doc):
  *   R1 a sample is valid iff it is finite and 2^-16 <= value <= 2^16 (depth in
- *      any unit, disparity in pixels after scaling); anything else is a hole.
+ *      any unit, float disparity in pixels); a 16-bit fixed-point disparity is
+ *      valid iff its raw value is non-zero.  Anything else is a hole.
  *   R2 a pixel is evaluable iff it is valid and every tap with a non-zero
  *      weight in either gradient filter is inside the image and valid.
  *   R3 gradients are correlations with [-1 0 1] (horizontal) and its transpose,
@@ -124,7 +125,8 @@ static void pixel(const job_t *J, int u, int v)
             int inside = x >= 0 && x < J->W && y >= 0 && y < J->H;
             double val = inside ? read_sample(J->in, J->pitch, J->type, J->disp_scale, x, y) : 0.0;
             s[dv + 1][du + 1] = val;
-            ok[dv + 1][du + 1] = inside && is_valid(val);
+            /* R1: fixed-point disparity is a hole only where the raw value is 0 */
+            ok[dv + 1][du + 1] = inside && (J->type == OR_DISP_U16 ? val > 0.0 : is_valid(val));
         }
     double *n0 = J->normals, *n1 = J->normals + HW, *n2 = J->normals + 2 * HW;
     if (J->cands)

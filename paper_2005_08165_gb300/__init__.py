@@ -1,0 +1,264 @@
+"""Python binding of libtfn (include/tfn.h): Three-Filters-to-Normal on GB300.
+
+The functions ``tfn_*`` mirror the C ABI one to one (ctypes); ``Context``
+adds argument marshalling for torch tensors (device pointers, pitches, the
+current CUDA stream).  Every step of the estimator runs in the library's CUDA
+kernels; nothing here computes normals, and importing fails loudly if the
+library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtfn.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libtfn.so not found at {LIB_PATH}: build it first "
+                      "(python -c 'import __graft_entry__ as g; g.build()' or python -m paper_2005_08165_gb300.build)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---- enums (tfn.h) ------------------------------------------------------------------------
+TFN_OK, TFN_ERR_INVALID_ARG, TFN_ERR_UNSUPPORTED, TFN_ERR_MISALIGNED, TFN_ERR_OUT_OF_MEMORY, TFN_ERR_CUDA, \
+    TFN_ERR_TIMEOUT, TFN_ERR_CANCELLED, TFN_ERR_BUSY, TFN_ERR_DEVICE = range(10)
+TFN_DEPTH_F32, TFN_DEPTH_F16, TFN_DISP_U16, TFN_DISP_F32 = range(4)
+TFN_GRAD_FD, TFN_GRAD_SOBEL, TFN_GRAD_SCHARR, TFN_GRAD_PREWITT = range(4)
+TFN_PHI_MEAN, TFN_PHI_MEDIAN = range(2)
+TFN_OUT_F32, TFN_OUT_F16, TFN_OUT_BF16, TFN_OUT_F16X4, TFN_OUT_BF16X4 = range(5)
+TFN_FLAG_REFINE_ALL = 1
+
+GRADS = {"fd": TFN_GRAD_FD, "sobel": TFN_GRAD_SOBEL, "scharr": TFN_GRAD_SCHARR, "prewitt": TFN_GRAD_PREWITT}
+PHIS = {"mean": TFN_PHI_MEAN, "median": TFN_PHI_MEDIAN}
+OUTPUTS = {"f32": TFN_OUT_F32, "f16": TFN_OUT_F16, "bf16": TFN_OUT_BF16, "f16x4": TFN_OUT_F16X4,
+           "bf16x4": TFN_OUT_BF16X4}
+
+
+class tfn_camera(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("u0", ctypes.c_float), ("v0", ctypes.c_float),
+                ("baseline", ctypes.c_float)]
+
+
+class tfn_frame(ctypes.Structure):
+    _fields_ = [("input", ctypes.c_void_p), ("input_pitch", ctypes.c_int64),
+                ("height", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("input_type", ctypes.c_int32), ("disp_scale", ctypes.c_float),
+                ("cam", tfn_camera),
+                ("normals", ctypes.c_void_p), ("normals_pitch", ctypes.c_int64),
+                ("normals_plane_stride", ctypes.c_int64),
+                ("mask", ctypes.c_void_p), ("mask_pitch", ctypes.c_int64)]
+
+
+class tfn_method(ctypes.Structure):
+    _fields_ = [("grad", ctypes.c_int32), ("phi", ctypes.c_int32), ("output", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_lib.tfn_status_string.restype = ctypes.c_char_p
+_lib.tfn_status_string.argtypes = [_I]
+_lib.tfn_version.restype = ctypes.c_char_p
+_lib.tfn_last_cuda_error.restype = ctypes.c_char_p
+_lib.tfn_create.argtypes = [ctypes.POINTER(_P), _I, ctypes.c_size_t]
+_lib.tfn_destroy.argtypes = [_P]
+_lib.tfn_normals.argtypes = [_P, ctypes.POINTER(tfn_frame), ctypes.POINTER(tfn_method), _P]
+_lib.tfn_normals_batch.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), _P]
+_lib.tfn_normals_batch_host.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), _P]
+_lib.tfn_device_status.argtypes = [_P, ctypes.POINTER(ctypes.c_uint32), _P]
+for _f in ("tfn_create", "tfn_destroy", "tfn_normals", "tfn_normals_batch", "tfn_normals_batch_host",
+           "tfn_device_status"):
+    getattr(_lib, _f).restype = _I
+
+# The C entry points under their own names.
+tfn_status_string = _lib.tfn_status_string
+tfn_version = _lib.tfn_version
+tfn_last_cuda_error = _lib.tfn_last_cuda_error
+tfn_create = _lib.tfn_create
+tfn_destroy = _lib.tfn_destroy
+tfn_normals = _lib.tfn_normals
+tfn_normals_batch = _lib.tfn_normals_batch
+tfn_normals_batch_host = _lib.tfn_normals_batch_host
+tfn_device_status = _lib.tfn_device_status
+
+EXPORTED = ["tfn_status_string", "tfn_version", "tfn_last_cuda_error", "tfn_create", "tfn_destroy", "tfn_normals",
+            "tfn_normals_batch", "tfn_normals_batch_host", "tfn_device_status"]
+
+
+class TfnError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        msg = tfn_status_string(status).decode()
+        if status == TFN_ERR_CUDA:
+            msg += f" ({tfn_last_cuda_error().decode()})"
+        super().__init__(f"{what}: {msg}" if what else msg)
+        self.status = status
+
+
+def check(status: int, what: str = ""):
+    if status != TFN_OK:
+        raise TfnError(status, what)
+
+
+# ---- tensor marshalling -----------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _input_type(t, disparity: bool) -> int:
+    torch = _torch()
+    if disparity:
+        if t.dtype in (getattr(torch, "uint16", None), torch.int16):  # int16: raw u16 bits
+            return TFN_DISP_U16
+        if t.dtype == torch.float32:
+            return TFN_DISP_F32
+    else:
+        if t.dtype == torch.float32:
+            return TFN_DEPTH_F32
+        if t.dtype == torch.float16:
+            return TFN_DEPTH_F16
+    raise TypeError(f"unsupported input dtype {t.dtype} (disparity={disparity})")
+
+
+def padded_width(width: int, elem_bytes: int) -> int:
+    """Smallest row length (elements) >= width whose byte size is a multiple of 16."""
+    per = 16 // elem_bytes
+    return (width + per - 1) // per * per
+
+
+def empty_image(shape, dtype, device="cuda"):
+    """(..., H, W) tensor whose rows start on 16-byte boundaries (a view of a padded buffer)."""
+    torch = _torch()
+    *lead, H, W = shape
+    es = torch.empty((), dtype=dtype).element_size()
+    Wp = padded_width(W, es)
+    buf = torch.empty((*lead, H, Wp), dtype=dtype, device=device)
+    return buf[..., :W]
+
+
+def empty_normals(H, W, output="f32", device="cuda", lead=()):
+    """Output buffer for one layout: planar (..., 3, H, W) or packed (..., H, W, 4)."""
+    torch = _torch()
+    fmt = OUTPUTS[output] if isinstance(output, str) else output
+    if fmt in (TFN_OUT_F32, TFN_OUT_F16, TFN_OUT_BF16):
+        dt = {TFN_OUT_F32: torch.float32, TFN_OUT_F16: torch.float16, TFN_OUT_BF16: torch.bfloat16}[fmt]
+        return empty_image((*lead, 3, H, W), dt, device)
+    dt = torch.float16 if fmt == TFN_OUT_F16X4 else torch.bfloat16
+    es = 8
+    Wp = padded_width(W, es)
+    buf = torch.empty((*lead, H, Wp, 4), dtype=dt, device=device)
+    return buf[..., :W, :]
+
+
+def make_frame(inp, normals, mask, cam, disparity=False, disp_scale=1.0 / 16, output="f32") -> tfn_frame:
+    """tfn_frame describing torch tensors `inp` (H, W), `normals`, `mask` (H, W)."""
+    fmt = OUTPUTS[output] if isinstance(output, str) else output
+    H, W = inp.shape
+    f = tfn_frame()
+    f.input = inp.data_ptr()
+    f.input_pitch = inp.stride(0) * inp.element_size()
+    f.height, f.width = H, W
+    f.input_type = _input_type(inp, disparity)
+    f.disp_scale = disp_scale
+    f.cam = tfn_camera(cam["fx"], cam["fy"], cam["u0"], cam["v0"], cam.get("baseline", 1.0))
+    f.normals = normals.data_ptr()
+    if fmt in (TFN_OUT_F32, TFN_OUT_F16, TFN_OUT_BF16):
+        f.normals_pitch = normals.stride(1) * normals.element_size()
+        f.normals_plane_stride = normals.stride(0) * normals.element_size()
+    else:
+        f.normals_pitch = normals.stride(0) * normals.element_size()
+        f.normals_plane_stride = 0
+    f.mask = mask.data_ptr()
+    f.mask_pitch = mask.stride(0) * mask.element_size()
+    return f
+
+
+def make_method(grad="fd", phi="mean", output="f32", flags=0) -> tfn_method:
+    m = tfn_method()
+    m.grad = GRADS[grad] if isinstance(grad, str) else grad
+    m.phi = PHIS[phi] if isinstance(phi, str) else phi
+    m.output = OUTPUTS[output] if isinstance(output, str) else output
+    m.flags = flags
+    return m
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """A libtfn context on one CUDA device (argument marshalling only)."""
+
+    def __init__(self, device: int = -1, mem_budget: int = 0):
+        h = ctypes.c_void_p()
+        check(tfn_create(ctypes.byref(h), device, mem_budget), "tfn_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            tfn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def normals(self, inp, cam, *, grad="fd", phi="mean", output="f32", disparity=False, disp_scale=1.0 / 16,
+                normals=None, mask=None, stream=None, flags=0):
+        """Normals of one (H, W) device image -> (normals, mask)."""
+        H, W = inp.shape
+        if normals is None:
+            normals = empty_normals(H, W, output, inp.device)
+        if mask is None:
+            mask = empty_image((H, W), _torch().uint8, inp.device)
+        f = make_frame(inp, normals, mask, cam, disparity, disp_scale, output)
+        m = make_method(grad, phi, output, flags)
+        check(tfn_normals(self.handle, ctypes.byref(f), ctypes.byref(m), _stream_handle(stream)), "tfn_normals")
+        return normals, mask
+
+    def normals_batch(self, inputs, cams, *, grad="fd", phi="mean", output="f32", disparity=False,
+                      disp_scale=1.0 / 16, normals=None, masks=None, stream=None, flags=0):
+        """Normals of a list of (H_i, W_i) device images (or an (N, H, W) stack) in one launch."""
+        n = len(inputs)
+        if isinstance(cams, dict):
+            cams = [cams] * n
+        if normals is None:
+            normals = [empty_normals(x.shape[0], x.shape[1], output, x.device) for x in inputs]
+        if masks is None:
+            masks = [empty_image(tuple(x.shape), _torch().uint8, x.device) for x in inputs]
+        frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output)
+                                   for k in range(n)])
+        m = make_method(grad, phi, output, flags)
+        check(tfn_normals_batch(self.handle, frames, n, ctypes.byref(m), _stream_handle(stream)), "tfn_normals_batch")
+        return normals, masks
+
+    def normals_batch_host(self, inputs, cams, normals, masks, *, grad="fd", phi="mean", output="f32",
+                           disparity=False, disp_scale=1.0 / 16, stream=None, flags=0):
+        """Like normals_batch, with every tensor in host memory (pinned is fastest); synchronous."""
+        n = len(inputs)
+        if isinstance(cams, dict):
+            cams = [cams] * n
+        frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output)
+                                   for k in range(n)])
+        m = make_method(grad, phi, output, flags)
+        check(tfn_normals_batch_host(self.handle, frames, n, ctypes.byref(m), _stream_handle(stream)),
+              "tfn_normals_batch_host")
+        return normals, masks
+
+    def device_status(self, stream=None) -> int:
+        bits = ctypes.c_uint32()
+        check(tfn_device_status(self.handle, ctypes.byref(bits), _stream_handle(stream)), "tfn_device_status")
+        return bits.value

@@ -1,0 +1,606 @@
+// tfn_api.cu -- host side of the C ABI declared in include/tfn.h.
+//
+// Validates requests, builds per-frame descriptors and TMA tensor maps in a
+// ring of scratch slots, launches the persistent kernel, and implements the
+// pipelined host-buffer path.  No C++ exception leaves this file.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/tfn.h"
+#include "tfn_internal.h"
+
+namespace tfn {
+KernelFn kernels_depth_f32(int grad, int phi, int cfg);
+KernelFn kernels_depth_f16(int grad, int phi, int cfg);
+KernelFn kernels_disp_u16(int grad, int phi, int cfg);
+KernelFn kernels_disp_f32(int grad, int phi, int cfg);
+
+KernelFn kernel_for(int kind, int grad, int phi, int cfg)
+{
+    switch (kind) {
+    case KIND_DEPTH_F32: return kernels_depth_f32(grad, phi, cfg);
+    case KIND_DEPTH_F16: return kernels_depth_f16(grad, phi, cfg);
+    case KIND_DISP_U16: return kernels_disp_u16(grad, phi, cfg);
+    case KIND_DISP_F32: return kernels_disp_f32(grad, phi, cfg);
+    }
+    return nullptr;
+}
+}  // namespace tfn
+
+using namespace tfn;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+bool cuda_ok(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return true;
+    snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", what, cudaGetErrorString(e));
+    return false;
+}
+
+#define TFN_CUDA(call)                                   \
+    do {                                                 \
+        if (!cuda_ok((call), #call)) return TFN_ERR_CUDA; \
+    } while (0)
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+bool load_encode()
+{
+    std::call_once(g_encode_once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    });
+    return g_encode != nullptr;
+}
+
+constexpr int kSlots = 4;
+
+// One scratch slot: descriptors + tensor maps for one launch.
+struct Slot {
+    void *dev = nullptr;   // FrameDesc[cap] then CUtensorMap[cap]
+    void *host = nullptr;  // pinned mirror
+    int cap = 0;
+    size_t bytes = 0;
+    cudaEvent_t done = nullptr;  // recorded after the launch that used it
+    std::vector<unsigned char> key;
+    bool has_key = false;
+};
+
+// Staging of the host-buffer path: one set per pipeline stream.
+struct Stage {
+    cudaStream_t stream = nullptr;
+    void *in = nullptr, *out = nullptr, *mask = nullptr;
+    size_t in_bytes = 0, out_bytes = 0, mask_bytes = 0;
+};
+
+}  // namespace
+
+struct tfn_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t budget = 0, used = 0;
+    uint32_t *status = nullptr;
+    uint32_t *status_host = nullptr;
+    Slot slots[kSlots];
+    int next_slot = 0, last_slot = -1;
+    int cfg = 0;
+    Stage stages[3];
+    std::vector<tfn_frame> chunk_frames;
+};
+
+namespace {
+
+struct DeviceGuard {  // switches to the context's device for the call's duration
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cuda_ok(cudaSetDevice(dev), "cudaSetDevice");
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+tfn_status ctx_alloc(tfn_ctx *c, void **p, size_t bytes)
+{
+    if (c->budget && c->used + bytes > c->budget) return TFN_ERR_OUT_OF_MEMORY;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return TFN_ERR_OUT_OF_MEMORY;
+    }
+    if (!cuda_ok(e, "cudaMalloc")) return TFN_ERR_CUDA;
+    c->used += bytes;
+    return TFN_OK;
+}
+
+void ctx_free(tfn_ctx *c, void *&p, size_t bytes)
+{
+    if (p) {
+        cudaFree(p);
+        c->used -= bytes;
+        p = nullptr;
+    }
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+bool mult16(int64_t x) { return (x & 15) == 0; }
+
+int out_elem_bytes(int fmt) { return fmt == OUT_F32 ? 4 : (fmt == OUT_F16 || fmt == OUT_BF16) ? 2 : 8; }
+
+tfn_status validate_method(const tfn_method *m)
+{
+    if (!m) return TFN_ERR_INVALID_ARG;
+    if (m->grad < 0 || m->grad >= GRAD_COUNT || m->phi < 0 || m->phi >= PHI_COUNT || m->output < 0 ||
+        m->output > OUT_BF16X4 || (m->flags & ~TFN_FLAG_REFINE_ALL))
+        return TFN_ERR_INVALID_ARG;
+    return TFN_OK;
+}
+
+bool finite_in(float x, float lo, float hi) { return std::isfinite(x) && x >= lo && x <= hi; }
+
+// `host` relaxes nothing but the meaning of the pointers (host vs device).
+tfn_status validate_frame(const tfn_frame *f, int out_fmt)
+{
+    if (!f || !f->input || !f->normals || !f->mask) return TFN_ERR_INVALID_ARG;
+    if (f->height < 1 || f->width < 1 || f->height > 32768 || f->width > 32768) return TFN_ERR_INVALID_ARG;
+    if (f->input_type < 0 || f->input_type >= KIND_COUNT) return TFN_ERR_INVALID_ARG;
+    const tfn_camera &c = f->cam;
+    if (!finite_in(c.fx, 1.0f / 256, 16777216.f) || !finite_in(c.fy, 1.0f / 256, 16777216.f) ||
+        !finite_in(c.u0, -16777216.f, 16777216.f) || !finite_in(c.v0, -16777216.f, 16777216.f))
+        return TFN_ERR_INVALID_ARG;
+    const bool disp = f->input_type == KIND_DISP_U16 || f->input_type == KIND_DISP_F32;
+    if (disp) {
+        if (!(c.baseline > 0) || !std::isfinite(c.baseline)) return TFN_ERR_INVALID_ARG;
+        if (f->input_type == KIND_DISP_U16 && !(f->disp_scale > 0 && std::isfinite(f->disp_scale)))
+            return TFN_ERR_INVALID_ARG;
+        if (c.fx != c.fy) return TFN_ERR_UNSUPPORTED;
+    }
+    const int64_t es = kind_elem_size(f->input_type);
+    const int64_t ob = out_elem_bytes(out_fmt);
+    if (f->input_pitch < f->width * es || f->normals_pitch < f->width * ob || f->mask_pitch < f->width)
+        return TFN_ERR_INVALID_ARG;
+    const bool planar = out_fmt <= OUT_BF16;
+    if (planar && f->normals_plane_stride < f->normals_pitch * (int64_t)f->height) return TFN_ERR_INVALID_ARG;
+    if (!aligned16(f->input) || !aligned16(f->normals) || !aligned16(f->mask) || !mult16(f->input_pitch) ||
+        !mult16(f->normals_pitch) || !mult16(f->mask_pitch) || (planar && !mult16(f->normals_plane_stride)))
+        return TFN_ERR_MISALIGNED;
+    return TFN_OK;
+}
+
+// Per-pixel refinement threshold: a pixel is recomputed in double-float when
+// its FP32 error bound, (6 + 4 cA + 32/min(fx,fy)) u + K1 u bound/|n'|, could
+// exceed 3/4 of the 1e-3 degree budget.  bound is sum |num_p|(|rho_j| +
+// |rho_-j|)/m for the mean (candidate-sum cancellation; K1 = 23 covers the
+// per-edge reciprocal, rho, numerator, product and accumulation roundings and
+// the approximate 1/m) and the larger |middle candidate| for the median
+// (K1 = 11).  cA bounds |A|/|n'|: A = (u-u0) G_u + (v-v0) G_v and
+// |n'| >= (fx |G_u|, fy |G_v|).
+float refine_threshold(const tfn_frame &f, int phi)
+{
+    const double u = std::ldexp(1.0, -24);
+    const double tol_part = 0.75 * 1e-3 * M_PI / 180.0;
+    const double mu = std::max(std::fabs(0.0 - f.cam.u0), std::fabs(f.width - 1.0 - f.cam.u0));
+    const double mv = std::max(std::fabs(0.0 - f.cam.v0), std::fabs(f.height - 1.0 - f.cam.v0));
+    const double cA = std::sqrt((mu / f.cam.fx) * (mu / f.cam.fx) + (mv / f.cam.fy) * (mv / f.cam.fy));
+    const double fixed = (6.0 + 4.0 * cA + 32.0 / std::min(f.cam.fx, f.cam.fy)) * u;
+    const double k1 = phi == PHI_MEAN ? 23.0 : 11.0;
+    const double t = (tol_part - fixed) / (k1 * u);
+    return t > 0 ? (float)t : 0.f;
+}
+
+void append_key(std::vector<unsigned char> &k, const void *p, size_t n)
+{
+    const unsigned char *b = (const unsigned char *)p;
+    k.insert(k.end(), b, b + n);
+}
+
+void frame_key(std::vector<unsigned char> &k, const tfn_frame &f)
+{
+    append_key(k, &f.input, sizeof f.input);
+    append_key(k, &f.input_pitch, sizeof f.input_pitch);
+    append_key(k, &f.height, sizeof f.height);
+    append_key(k, &f.width, sizeof f.width);
+    append_key(k, &f.input_type, sizeof f.input_type);
+    append_key(k, &f.disp_scale, sizeof f.disp_scale);
+    append_key(k, &f.cam, sizeof f.cam);
+    append_key(k, &f.normals, sizeof f.normals);
+    append_key(k, &f.normals_pitch, sizeof f.normals_pitch);
+    append_key(k, &f.normals_plane_stride, sizeof f.normals_plane_stride);
+    append_key(k, &f.mask, sizeof f.mask);
+    append_key(k, &f.mask_pitch, sizeof f.mask_pitch);
+}
+
+tfn_status encode_map(CUtensorMap *map, const tfn_frame &f, int cfg)
+{
+    if (!load_encode()) {
+        snprintf(g_cuda_err, sizeof g_cuda_err, "cuTensorMapEncodeTiled unavailable");
+        return TFN_ERR_CUDA;
+    }
+    const int kind = f.input_type;
+    CUtensorMapDataType dt = kind == KIND_DEPTH_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                             : kind == KIND_DISP_U16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    cuuint64_t dims[2] = {(cuuint64_t)f.width, (cuuint64_t)f.height};
+    cuuint64_t strides[1] = {(cuuint64_t)f.input_pitch};
+    cuuint32_t box[2] = {(cuuint32_t)box_w(kind, cfg), (cuuint32_t)box_h(cfg)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, dt, 2, const_cast<void *>(f.input), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        snprintf(g_cuda_err, sizeof g_cuda_err, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return TFN_ERR_CUDA;
+    }
+    return TFN_OK;
+}
+
+size_t slot_bytes(int cap) { return (size_t)cap * sizeof(FrameDesc) + 128 + (size_t)cap * sizeof(CUtensorMap); }
+
+tfn_status slot_reserve(tfn_ctx *c, Slot &s, int n)
+{
+    if (s.cap >= n) return TFN_OK;
+    if (s.done) TFN_CUDA(cudaEventSynchronize(s.done));
+    int cap = std::max(n, std::max(8, s.cap * 2));
+    ctx_free(c, s.dev, s.bytes);
+    if (s.host) cudaFreeHost(s.host);
+    s.host = nullptr;
+    s.cap = 0;
+    s.has_key = false;
+    size_t bytes = slot_bytes(cap);
+    tfn_status st = ctx_alloc(c, &s.dev, bytes);
+    if (st) return st;
+    if (!cuda_ok(cudaMallocHost(&s.host, bytes), "cudaMallocHost")) {
+        ctx_free(c, s.dev, bytes);
+        return TFN_ERR_CUDA;
+    }
+    s.bytes = bytes;
+    s.cap = cap;
+    return TFN_OK;
+}
+
+FrameDesc *slot_descs(void *base) { return (FrameDesc *)base; }
+CUtensorMap *slot_maps(void *base, int cap)
+{
+    uintptr_t p = (uintptr_t)base + (size_t)cap * sizeof(FrameDesc);
+    return (CUtensorMap *)((p + 127) & ~(uintptr_t)127);
+}
+
+// One launch over frames[0..n) (all of one input kind).
+tfn_status launch_group(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method &m, cudaStream_t stream)
+{
+    const int kind = frames[0].input_type;
+    const int cfg = c->cfg;
+    std::vector<unsigned char> key;
+    key.reserve(16 + (size_t)n * 96);
+    append_key(key, &m, sizeof m);
+    append_key(key, &cfg, sizeof cfg);
+    for (int i = 0; i < n; ++i) frame_key(key, frames[i]);
+
+    int si = -1;
+    if (c->last_slot >= 0 && c->slots[c->last_slot].has_key && c->slots[c->last_slot].key == key) si = c->last_slot;
+    int total = 0;
+    for (int i = 0; i < n; ++i) {
+        const int tw = kCfgs[cfg].tw, th = kCfgs[cfg].th;
+        total += ((frames[i].width + tw - 1) / tw) * ((frames[i].height + th - 1) / th);
+    }
+    if (si < 0) {
+        si = c->next_slot;
+        c->next_slot = (c->next_slot + 1) % kSlots;
+        Slot &s = c->slots[si];
+        if (s.done) TFN_CUDA(cudaEventSynchronize(s.done));  // the previous launch from this slot is finished
+        tfn_status st = slot_reserve(c, s, n);
+        if (st) return st;
+        FrameDesc *d = slot_descs(s.host);
+        CUtensorMap *maps = slot_maps(s.host, s.cap);
+        int tb = 0;
+        for (int i = 0; i < n; ++i) {
+            const tfn_frame &f = frames[i];
+            const int tw = kCfgs[cfg].tw, th = kCfgs[cfg].th;
+            FrameDesc fd;
+            memset(&fd, 0, sizeof fd);
+            fd.out = (char *)f.normals;
+            fd.out_pitch = f.normals_pitch;
+            fd.out_plane = f.normals_plane_stride;
+            fd.mask = f.mask;
+            fd.mask_pitch = f.mask_pitch;
+            fd.H = f.height;
+            fd.W = f.width;
+            fd.tiles_x = (f.width + tw - 1) / tw;
+            fd.tile_begin = tb;
+            tb += fd.tiles_x * ((f.height + th - 1) / th);
+            fd.fx = f.cam.fx;
+            fd.fy = f.cam.fy;
+            fd.u0 = f.cam.u0;
+            fd.v0 = f.cam.v0;
+            fd.thr = refine_threshold(f, m.phi);
+            fd.kind = kind;
+            d[i] = fd;
+            st = encode_map(&maps[i], f, cfg);
+            if (st) return st;
+        }
+        const size_t off_maps = (uintptr_t)slot_maps(s.host, s.cap) - (uintptr_t)s.host;
+        TFN_CUDA(cudaMemcpyAsync(s.dev, s.host, (size_t)n * sizeof(FrameDesc), cudaMemcpyHostToDevice, stream));
+        TFN_CUDA(cudaMemcpyAsync((char *)s.dev + off_maps, (char *)s.host + off_maps, (size_t)n * sizeof(CUtensorMap),
+                                 cudaMemcpyHostToDevice, stream));
+        s.key.swap(key);
+        s.has_key = true;
+    }
+    Slot &s = c->slots[si];
+    c->last_slot = si;
+    if (!s.done) TFN_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+
+    KernelFn fn = kernel_for(kind, m.grad, m.phi, cfg);
+    if (!fn) return TFN_ERR_UNSUPPORTED;
+    const int threads = cfg_threads(cfg);
+    const size_t smem = smem_bytes(kind, cfg);
+    TFN_CUDA(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    TFN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, threads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int grid = std::min(total, per_sm * c->num_sms);
+    if (grid < 1) return TFN_OK;
+    LaunchArgs a;
+    a.frames = slot_descs(s.dev);
+    a.maps = slot_maps(s.dev, s.cap);
+    a.status = c->status;
+    a.nframes = n;
+    a.total_tiles = total;
+    a.out_fmt = m.output;
+    a.flags = m.flags;
+    void *params[] = {&a};
+    TFN_CUDA(cudaLaunchKernel((const void *)fn, dim3(grid), dim3(threads), params, smem, stream));
+    TFN_CUDA(cudaEventRecord(s.done, stream));
+    return TFN_OK;
+}
+
+tfn_status run_batch(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method &m, cudaStream_t stream)
+{
+    // frames of one input kind go to one launch; keep the caller's order
+    int i = 0;
+    while (i < n) {
+        int j = i + 1;
+        while (j < n && frames[j].input_type == frames[i].input_type) ++j;
+        tfn_status st = launch_group(c, frames + i, j - i, m, stream);
+        if (st) return st;
+        i = j;
+    }
+    return TFN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tfn_status_string(tfn_status s)
+{
+    switch (s) {
+    case TFN_OK: return "ok";
+    case TFN_ERR_INVALID_ARG: return "invalid argument";
+    case TFN_ERR_UNSUPPORTED: return "unsupported combination";
+    case TFN_ERR_MISALIGNED: return "pointer or pitch not a multiple of 16 bytes";
+    case TFN_ERR_OUT_OF_MEMORY: return "out of memory (context budget or device)";
+    case TFN_ERR_CUDA: return "CUDA error";
+    case TFN_ERR_TIMEOUT: return "timed out";
+    case TFN_ERR_CANCELLED: return "cancelled";
+    case TFN_ERR_BUSY: return "busy";
+    case TFN_ERR_DEVICE: return "a kernel reported a failed bounded wait";
+    }
+    return "unknown status";
+}
+
+const char *tfn_version(void) { return "tfn 0.1 (sm_103a)"; }
+
+const char *tfn_last_cuda_error(void) { return g_cuda_err; }
+
+tfn_status tfn_create(tfn_ctx **out, int device, size_t budget)
+{
+    if (!out) return TFN_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (device < 0 && !cuda_ok(cudaGetDevice(&device), "cudaGetDevice")) return TFN_ERR_CUDA;
+    int ndev = 0;
+    if (!cuda_ok(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount")) return TFN_ERR_CUDA;
+    if (device >= ndev) return TFN_ERR_INVALID_ARG;
+    DeviceGuard g(device);
+    if (!g.ok) return TFN_ERR_CUDA;
+    tfn_ctx *c = new (std::nothrow) tfn_ctx();
+    if (!c) return TFN_ERR_OUT_OF_MEMORY;
+    c->device = device;
+    c->budget = budget;
+    if (!cuda_ok(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device), "cudaDeviceGetAttribute")) {
+        delete c;
+        return TFN_ERR_CUDA;
+    }
+    tfn_status st = ctx_alloc(c, (void **)&c->status, 256);
+    if (st || !cuda_ok(cudaMemset(c->status, 0, 256), "cudaMemset") ||
+        !cuda_ok(cudaMallocHost((void **)&c->status_host, sizeof(uint32_t)), "cudaMallocHost")) {
+        tfn_destroy(c);
+        return st ? st : TFN_ERR_CUDA;
+    }
+    *out = c;
+    return TFN_OK;
+}
+
+tfn_status tfn_destroy(tfn_ctx *c)
+{
+    if (!c) return TFN_OK;
+    DeviceGuard g(c->device);
+    for (Slot &s : c->slots) {
+        if (s.done) {
+            cudaEventSynchronize(s.done);
+            cudaEventDestroy(s.done);
+        }
+        ctx_free(c, s.dev, s.bytes);
+        if (s.host) cudaFreeHost(s.host);
+    }
+    for (Stage &s : c->stages) {
+        if (s.stream) {
+            cudaStreamSynchronize(s.stream);
+            cudaStreamDestroy(s.stream);
+        }
+        ctx_free(c, s.in, s.in_bytes);
+        ctx_free(c, s.out, s.out_bytes);
+        ctx_free(c, s.mask, s.mask_bytes);
+    }
+    void *st = c->status;
+    ctx_free(c, st, 256);
+    if (c->status_host) cudaFreeHost(c->status_host);
+    delete c;
+    return TFN_OK;
+}
+
+tfn_status tfn_normals(tfn_ctx *c, const tfn_frame *frame, const tfn_method *m, tfn_stream stream)
+{
+    return tfn_normals_batch(c, frame, 1, m, stream);
+}
+
+tfn_status tfn_normals_batch(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method *m, tfn_stream stream)
+{
+    if (!c || n < 0 || (n > 0 && !frames)) return TFN_ERR_INVALID_ARG;
+    tfn_status st = validate_method(m);
+    if (st) return st;
+    for (int i = 0; i < n; ++i)
+        if ((st = validate_frame(&frames[i], m->output))) return st;
+    if (n == 0) return TFN_OK;
+    DeviceGuard g(c->device);
+    if (!g.ok) return TFN_ERR_CUDA;
+    return run_batch(c, frames, n, *m, (cudaStream_t)stream);
+}
+
+tfn_status tfn_normals_batch_host(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method *m, tfn_stream stream)
+{
+    if (!c || n < 0 || (n > 0 && !frames)) return TFN_ERR_INVALID_ARG;
+    tfn_status st = validate_method(m);
+    if (st) return st;
+    for (int i = 0; i < n; ++i) {
+        const tfn_frame &f = frames[i];
+        if (!f.input || !f.normals || !f.mask || f.height < 1 || f.width < 1 || f.height > 32768 || f.width > 32768 ||
+            f.input_type < 0 || f.input_type >= KIND_COUNT)
+            return TFN_ERR_INVALID_ARG;
+    }
+    if (n == 0) return TFN_OK;
+    DeviceGuard g(c->device);
+    if (!g.ok) return TFN_ERR_CUDA;
+    const int fmt = m->output;
+    const bool planar = fmt <= OUT_BF16;
+    const int ob = out_elem_bytes(fmt);
+    // chunk size: about 64 MB of input per chunk, at least one frame
+    size_t max_in = 0, max_out = 0, max_mask = 0;
+    for (int i = 0; i < n; ++i) {
+        const tfn_frame &f = frames[i];
+        const size_t ip = ((size_t)f.width * kind_elem_size(f.input_type) + 15) & ~(size_t)15;
+        const size_t op = ((size_t)f.width * ob + 15) & ~(size_t)15;
+        const size_t mp = ((size_t)f.width + 15) & ~(size_t)15;
+        max_in = std::max(max_in, ip * f.height);
+        max_out = std::max(max_out, op * f.height * (planar ? 3 : 1));
+        max_mask = std::max(max_mask, mp * f.height);
+    }
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, (64u << 20) / std::max<size_t>(max_in, 1)));
+    const int nst = 3;
+    for (int k = 0; k < nst; ++k) {
+        Stage &s = c->stages[k];
+        if (!s.stream) TFN_CUDA(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+        const size_t need_in = max_in * chunk, need_out = max_out * chunk, need_mask = max_mask * chunk;
+        if (s.in_bytes < need_in || s.out_bytes < need_out || s.mask_bytes < need_mask) {
+            TFN_CUDA(cudaStreamSynchronize(s.stream));
+            ctx_free(c, s.in, s.in_bytes);
+            ctx_free(c, s.out, s.out_bytes);
+            ctx_free(c, s.mask, s.mask_bytes);
+            s.in_bytes = s.out_bytes = s.mask_bytes = 0;
+            if ((st = ctx_alloc(c, &s.in, need_in)) || (st = ctx_alloc(c, &s.out, need_out)) ||
+                (st = ctx_alloc(c, &s.mask, need_mask)))
+                return st;
+            s.in_bytes = need_in;
+            s.out_bytes = need_out;
+            s.mask_bytes = need_mask;
+            for (Slot &sl : c->slots) sl.has_key = false;  // device pointers changed
+        }
+    }
+    cudaEvent_t start;
+    TFN_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    cuda_ok(cudaEventRecord(start, (cudaStream_t)stream), "cudaEventRecord");
+    for (int k = 0; k < nst; ++k) cuda_ok(cudaStreamWaitEvent(c->stages[k].stream, start, 0), "cudaStreamWaitEvent");
+    cudaEventDestroy(start);
+    std::vector<tfn_frame> dframes;
+    for (int base = 0, ci = 0; base < n && st == TFN_OK; base += chunk, ++ci) {
+        Stage &s = c->stages[ci % nst];
+        const int cnt = std::min(chunk, n - base);
+        dframes.resize(cnt);
+        for (int i = 0; i < cnt; ++i) {
+            const tfn_frame &f = frames[base + i];
+            tfn_frame d = f;
+            const size_t ip = ((size_t)f.width * kind_elem_size(f.input_type) + 15) & ~(size_t)15;
+            const size_t op = ((size_t)f.width * ob + 15) & ~(size_t)15;
+            const size_t mp = ((size_t)f.width + 15) & ~(size_t)15;
+            d.input = (char *)s.in + max_in * i;
+            d.input_pitch = ip;
+            d.normals = (char *)s.out + max_out * i;
+            d.normals_pitch = op;
+            d.normals_plane_stride = op * f.height;
+            d.mask = (uint8_t *)s.mask + max_mask * i;
+            d.mask_pitch = mp;
+            if ((st = validate_frame(&d, fmt))) break;
+            if (!cuda_ok(cudaMemcpy2DAsync((void *)d.input, ip, f.input, f.input_pitch,
+                                           (size_t)f.width * kind_elem_size(f.input_type), f.height,
+                                           cudaMemcpyHostToDevice, s.stream),
+                         "cudaMemcpy2DAsync(H2D)")) {
+                st = TFN_ERR_CUDA;
+                break;
+            }
+            dframes[i] = d;
+        }
+        if (st) break;
+        if ((st = run_batch(c, dframes.data(), cnt, *m, s.stream))) break;
+        for (int i = 0; i < cnt && st == TFN_OK; ++i) {
+            const tfn_frame &f = frames[base + i];
+            const tfn_frame &d = dframes[i];
+            for (int p = 0; p < (planar ? 3 : 1); ++p)
+                if (!cuda_ok(cudaMemcpy2DAsync((char *)f.normals + p * f.normals_plane_stride, f.normals_pitch,
+                                               (char *)d.normals + p * d.normals_plane_stride, d.normals_pitch,
+                                               (size_t)f.width * ob, f.height, cudaMemcpyDeviceToHost, s.stream),
+                             "cudaMemcpy2DAsync(D2H)"))
+                    st = TFN_ERR_CUDA;
+            if (st == TFN_OK &&
+                !cuda_ok(cudaMemcpy2DAsync(f.mask, f.mask_pitch, d.mask, d.mask_pitch, f.width, f.height,
+                                           cudaMemcpyDeviceToHost, s.stream),
+                         "cudaMemcpy2DAsync(D2H)"))
+                st = TFN_ERR_CUDA;
+        }
+    }
+    for (int k = 0; k < nst; ++k)
+        if (!cuda_ok(cudaStreamSynchronize(c->stages[k].stream), "cudaStreamSynchronize") && st == TFN_OK)
+            st = TFN_ERR_CUDA;
+    return st;
+}
+
+tfn_status tfn_device_status(tfn_ctx *c, uint32_t *bits, tfn_stream stream)
+{
+    if (!c || !bits) return TFN_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!g.ok) return TFN_ERR_CUDA;
+    TFN_CUDA(cudaMemcpyAsync(c->status_host, c->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    TFN_CUDA(cudaMemsetAsync(c->status, 0, sizeof(uint32_t), (cudaStream_t)stream));
+    TFN_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    *bits = *c->status_host;
+    return TFN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,70 @@
+// tfn_internal.h -- types shared by the host side (tfn_api.cu) and the kernels.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tfn {
+
+enum Kind { KIND_DEPTH_F32 = 0, KIND_DEPTH_F16 = 1, KIND_DISP_U16 = 2, KIND_DISP_F32 = 3, KIND_COUNT = 4 };
+enum Grad { GRAD_FD = 0, GRAD_SOBEL = 1, GRAD_SCHARR = 2, GRAD_PREWITT = 3, GRAD_COUNT = 4 };
+enum Phi { PHI_MEAN = 0, PHI_MEDIAN = 1, PHI_COUNT = 2 };
+enum OutFmt { OUT_F32 = 0, OUT_F16 = 1, OUT_BF16 = 2, OUT_F16X4 = 3, OUT_BF16X4 = 4 };
+
+// Device status bits written by kernels.
+enum : uint32_t { DEVERR_TMA_WAIT = 1u };
+
+// Per-frame descriptor in device memory (one per frame of a launch).
+struct alignas(16) FrameDesc {
+    char *out;           // normals: plane c at out + c * out_plane
+    int64_t out_pitch;   // bytes
+    int64_t out_plane;   // bytes
+    uint8_t *mask;
+    int64_t mask_pitch;  // bytes
+    int32_t H, W;
+    int32_t tiles_x;     // tiles per row of this frame
+    int32_t tile_begin;  // global index of this frame's first tile
+    float fx, fy, u0, v0;
+    float thr;           // refinement threshold (see refine_threshold in tfn_api.cu)
+    int32_t kind;        // Kind of this frame (a launch holds frames of one kind)
+    int32_t pad[2];
+};
+static_assert(sizeof(FrameDesc) == 96, "FrameDesc layout");
+
+// Kernel arguments (passed by value as a __grid_constant__).
+struct LaunchArgs {
+    const FrameDesc *frames;
+    const CUtensorMap *maps;  // one 2D tiled map per frame, 64-byte aligned
+    uint32_t *status;         // device status word (DEVERR_* bits)
+    int32_t nframes;
+    int32_t total_tiles;
+    int32_t out_fmt;
+    int32_t flags;
+};
+
+// Tile shapes the kernels are compiled for: TW x TH pixels per tile, PR
+// pixel rows per thread (4 pixel columns per thread); every shape has 256
+// threads.
+struct TileCfg {
+    int tw, th, pr;
+};
+constexpr int kNumCfg = 3;
+constexpr TileCfg kCfgs[kNumCfg] = {{64, 32, 2}, {128, 16, 2}, {64, 16, 1}};
+constexpr int kStages = 3;
+
+inline int cfg_threads(int) { return 256; }
+inline int kind_elem_size(int kind) { return (kind == KIND_DEPTH_F32 || kind == KIND_DISP_F32) ? 4 : 2; }
+// Halo columns loaded on each side so that the TMA box starts on a 16-byte boundary.
+inline int kind_padx(int kind) { return 16 / kind_elem_size(kind); }
+inline int box_w(int kind, int c) { return kCfgs[c].tw + 2 * kind_padx(kind); }
+inline int box_h(int c) { return kCfgs[c].th + 2; }
+inline size_t stage_bytes(int kind, int c) { return (size_t)box_w(kind, c) * box_h(c) * kind_elem_size(kind); }
+inline size_t stage_stride(int kind, int c) { return (stage_bytes(kind, c) + 1023) & ~(size_t)1023; }
+inline size_t smem_bytes(int kind, int c) { return kStages * stage_stride(kind, c) + 128; }
+
+// Kernel entry points, one per (kind, grad, phi, cfg); defined in tfn_k_*.cu.
+typedef void (*KernelFn)(LaunchArgs);
+KernelFn kernel_for(int kind, int grad, int phi, int cfg);
+
+}  // namespace tfn

@@ -1,0 +1,7 @@
+// Kernels for one input kind (depth_f32); the instantiations are split by kind so
+// that the translation units compile in parallel.
+#include "tfn_kernel.cuh"
+
+namespace tfn {
+KernelFn kernels_depth_f32(int grad, int phi, int cfg) { return dev::select_kernel<KIND_DEPTH_F32>(grad, phi, cfg); }
+}  // namespace tfn

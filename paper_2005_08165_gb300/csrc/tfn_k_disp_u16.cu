@@ -1,0 +1,7 @@
+// Kernels for one input kind (disp_u16); the instantiations are split by kind so
+// that the translation units compile in parallel.
+#include "tfn_kernel.cuh"
+
+namespace tfn {
+KernelFn kernels_disp_u16(int grad, int phi, int cfg) { return dev::select_kernel<KIND_DISP_U16>(grad, phi, cfg); }
+}  // namespace tfn

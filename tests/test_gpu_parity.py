@@ -1,0 +1,272 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import scenes
+from tests.parity import compare
+
+pytestmark = pytest.mark.gpu
+
+GRADS = ["fd", "sobel", "scharr", "prewitt"]
+PHIS = ["mean", "median"]
+SIZES = [(67, 131), (130, 200), (33, 64), (5, 7)]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def tfn(torch):
+    import paper_2005_08165_gb300 as tfn
+    return tfn
+
+
+@pytest.fixture(scope="module")
+def ctx(tfn):
+    c = tfn.Context(0)
+    yield c
+    assert c.device_status() == 0
+    c.close()
+
+
+def small_recipe(H, W, **kw):
+    f = 481.2 * W / 640
+    return scenes.Recipe(H=H, W=W, fx=f, fy=f, u0=(W - 1) / 2, v0=(H - 1) / 2, **kw)
+
+
+def to_dev(torch, tfn, img):
+    if img.dtype == np.uint16:  # raw u16 bits travel as int16
+        t = tfn.empty_image(img.shape, torch.int16)
+        t.copy_(torch.from_numpy(img.view(np.int16)))
+        return t
+    dt = {np.float32: torch.float32, np.float16: torch.float16}[img.dtype.type]
+    t = tfn.empty_image(img.shape, dt)
+    t.copy_(torch.from_numpy(img))
+    return t
+
+
+def depth_frames(sizes, seed, noise=0.0012, holes=0.03):
+    out = []
+    for k, (H, W) in enumerate(sizes):
+        r = small_recipe(H, W, noise_k=noise, hole_frac=holes)
+        out.append((scenes.render(seed + k, r), r.camera))
+    return out
+
+
+def disparity_frames(sizes, seed):
+    out = []
+    for k, (H, W) in enumerate(sizes):
+        f = 615.0 * W / 640
+        r = scenes.Recipe(H=H, W=W, fx=f, fy=f, u0=(W - 1) / 2, v0=(H - 1) / 2, zmin=0.640625, zmax=61.5,
+                          plane_z0=0.640625, plane_z1=61.5, sphere_z0=2, sphere_z1=50, radius0=0.5, radius1=5)
+        d = scenes.render(seed + k, r)
+        raw = scenes.disparity_u16(d, f * 0.1, frac_bits=4, hole_frac=0.05, seed=seed + 100 + k)
+        cam = dict(r.camera, baseline=0.1)
+        out.append((raw, cam))
+    return out
+
+
+def run_batch(torch, tfn, ctx, frames, *, grad, phi, disparity=False, output="f32", flags=0):
+    inputs = [to_dev(torch, tfn, img) for img, _ in frames]
+    cams = [cam for _, cam in frames]
+    n, m = ctx.normals_batch(inputs, cams, grad=grad, phi=phi, disparity=disparity, output=output, flags=flags)
+    torch.cuda.synchronize()
+    return [x.float().cpu().numpy() for x in n], [x.cpu().numpy() for x in m]
+
+
+@pytest.mark.parametrize("grad", GRADS)
+@pytest.mark.parametrize("phi", PHIS)
+def test_depth_f32_ragged_sizes(torch, tfn, ctx, grad, phi):
+    frames = depth_frames(SIZES, 500)
+    n, m = run_batch(torch, tfn, ctx, frames, grad=grad, phi=phi)
+    for (img, cam), nk, mk in zip(frames, n, m):
+        compare(nk, mk, img, cam, grad=grad, phi=phi)
+
+
+@pytest.mark.parametrize("grad", GRADS)
+@pytest.mark.parametrize("phi", PHIS)
+def test_depth_f16_input(torch, tfn, ctx, grad, phi):
+    frames = [(img.astype(np.float16), cam) for img, cam in depth_frames(SIZES[:2], 600, noise=0.0)]
+    n, m = run_batch(torch, tfn, ctx, frames, grad=grad, phi=phi)
+    for (img, cam), nk, mk in zip(frames, n, m):
+        compare(nk, mk, img, cam, grad=grad, phi=phi)
+
+
+@pytest.mark.parametrize("grad", GRADS)
+@pytest.mark.parametrize("phi", PHIS)
+def test_disparity_u16(torch, tfn, ctx, grad, phi):
+    frames = disparity_frames(SIZES[:3], 700)
+    n, m = run_batch(torch, tfn, ctx, frames, grad=grad, phi=phi, disparity=True)
+    for (img, cam), nk, mk in zip(frames, n, m):
+        compare(nk, mk, img, cam, grad=grad, phi=phi, disparity=True, baseline=cam["baseline"])
+
+
+@pytest.mark.parametrize("grad", ["fd", "scharr"])
+@pytest.mark.parametrize("phi", PHIS)
+def test_disparity_f32(torch, tfn, ctx, grad, phi):
+    frames = []
+    for raw, cam in disparity_frames(SIZES[:2], 800):
+        frames.append(((raw.astype(np.float32) / 16).astype(np.float32), cam))
+    n, m = run_batch(torch, tfn, ctx, frames, grad=grad, phi=phi, disparity=True)
+    for (img, cam), nk, mk in zip(frames, n, m):
+        compare(nk, mk, img, cam, grad=grad, phi=phi, disparity=True, baseline=cam["baseline"])
+
+
+@pytest.mark.parametrize("grad", ["fd", "sobel", "scharr"])
+@pytest.mark.parametrize("phi", PHIS)
+def test_full_size_noisy_frames(torch, tfn, ctx, grad, phi):
+    # the 480x640 workload: sigma = 0.0012 Z^2 noise, 3% holes
+    frames = [(scenes.render_batch(1000 + k, 1, scenes.Recipe(noise_k=0.0012, hole_frac=0.03))[0], scenes.CAMERA)
+              for k in (0, 1)]
+    n, m = run_batch(torch, tfn, ctx, frames, grad=grad, phi=phi)
+    for (img, cam), nk, mk in zip(frames, n, m):
+        compare(nk, mk, img, cam, grad=grad, phi=phi)
+
+
+def test_full_size_clean_frame_fd_mean(torch, tfn, ctx):
+    frames = [(scenes.single_frame(), scenes.CAMERA)]
+    n, m = run_batch(torch, tfn, ctx, frames, grad="fd", phi="mean")
+    compare(n[0], m[0], frames[0][0], scenes.CAMERA, grad="fd", phi="mean")
+
+
+@pytest.mark.parametrize("grad", GRADS)
+@pytest.mark.parametrize("phi", PHIS)
+def test_refine_all_path_is_tight(torch, tfn, ctx, grad, phi):
+    # every pixel through the double-float path: agreement far below the tolerance
+    frames = depth_frames(SIZES[:2], 900)
+    n, m = run_batch(torch, tfn, ctx, frames, grad=grad, phi=phi, flags=tfn.TFN_FLAG_REFINE_ALL)
+    for (img, cam), nk, mk in zip(frames, n, m):
+        st = compare(nk, mk, img, cam, grad=grad, phi=phi, tol=1e-5)
+        assert st["over"] == 0 or phi == "median"
+
+
+@pytest.mark.parametrize("output", ["f16", "bf16", "f16x4", "bf16x4"])
+def test_reduced_precision_outputs_round_the_f32_result(torch, tfn, ctx, output):
+    img, cam = depth_frames([(61, 99)], 1100)[0]
+    d = to_dev(torch, tfn, img)
+    n32, m32 = ctx.normals(d, cam)
+    n16, m16 = ctx.normals(d, cam, output=output)
+    torch.cuda.synchronize()
+    dt = torch.float16 if output.startswith("f16") else torch.bfloat16
+    want = n32.to(dt)
+    got = n16 if output in ("f16", "bf16") else n16[..., :3].permute(2, 0, 1)
+    assert torch.equal(got.contiguous().view(torch.int16), want.contiguous().view(torch.int16))
+    if output in ("f16x4", "bf16x4"):
+        assert (n16[..., 3] == 0).all()
+    assert torch.equal(m16, m32)
+
+
+def test_batch_composition_and_alone_bit_identical(torch, tfn, ctx):
+    frames = depth_frames([(67, 131), (480, 640), (33, 64)], 1200)
+    n_mix, m_mix = run_batch(torch, tfn, ctx, frames, grad="scharr", phi="median")
+    for k, fr in enumerate(frames):
+        n1, m1 = run_batch(torch, tfn, ctx, [fr], grad="scharr", phi="median")
+        assert np.array_equal(n1[0], n_mix[k]) and np.array_equal(m1[0], m_mix[k])
+
+
+def test_mixed_input_kinds_in_one_call(torch, tfn, ctx):
+    dep = depth_frames([(40, 52)], 1300)[0]
+    inputs = [to_dev(torch, tfn, dep[0]), to_dev(torch, tfn, dep[0].astype(np.float16))]
+    n, m = ctx.normals_batch(inputs, [dep[1], dep[1]])
+    torch.cuda.synchronize()
+    compare(n[0].cpu().numpy(), m[0].cpu().numpy(), dep[0], dep[1], grad="fd", phi="mean")
+    compare(n[1].cpu().numpy(), m[1].cpu().numpy(), dep[0].astype(np.float16), dep[1], grad="fd", phi="mean")
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (2, 2), (3, 3), (1, 9), (9, 1), (3, 5)])
+def test_tiny_images(torch, tfn, ctx, shape):
+    rng = np.random.default_rng(1)
+    img = rng.uniform(1, 2, size=shape).astype(np.float32)
+    cam = dict(fx=3.0, fy=3.0, u0=(shape[1] - 1) / 2, v0=(shape[0] - 1) / 2)
+    for grad in ("fd", "sobel"):
+        for phi in PHIS:
+            n, m = run_batch(torch, tfn, ctx, [(img, cam)], grad=grad, phi=phi)
+            compare(n[0], m[0], img, cam, grad=grad, phi=phi)
+
+
+def test_special_values_all_holes_constant(torch, tfn, ctx):
+    H, W = 23, 37
+    img = np.full((H, W), 2.5, np.float32)
+    img[3, 4:11] = [np.nan, np.inf, -np.inf, -1.0, 0.0, 2.0 ** -17, 2.0 ** 17]
+    img[10, 10] = 2.0 ** -16
+    img[12, 12] = 2.0 ** 16
+    cam = dict(fx=20.0, fy=21.0, u0=18.0, v0=11.0)
+    for grad in GRADS:
+        for phi in PHIS:
+            n, m = run_batch(torch, tfn, ctx, [(img, cam)], grad=grad, phi=phi)
+            compare(n[0], m[0], img, cam, grad=grad, phi=phi)
+    holes = np.zeros((H, W), np.float32)
+    n, m = run_batch(torch, tfn, ctx, [(holes, cam)], grad="fd", phi="mean")
+    assert (m[0] == 0).all() and (n[0] == 0).all()
+
+
+def test_invalid_arguments_are_rejected(torch, tfn, ctx):
+    img = tfn.empty_image((16, 16), torch.float32)
+    img.fill_(1.0)
+    n = tfn.empty_normals(16, 16)
+    m = tfn.empty_image((16, 16), torch.uint8)
+    meth = tfn.make_method()
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call(**over):
+        f = tfn.make_frame(img, n, m, dict(fx=10.0, fy=10.0, u0=8.0, v0=8.0))
+        for k, v in over.items():
+            setattr(f, k, v)
+        return tfn.tfn_normals(ctx.handle, ctypes.byref(f), ctypes.byref(meth), s)
+
+    assert call() == tfn.TFN_OK
+    assert call(input_pitch=72) == tfn.TFN_ERR_MISALIGNED
+    assert call(input=img.data_ptr() + 4) == tfn.TFN_ERR_MISALIGNED
+    assert call(width=0) == tfn.TFN_ERR_INVALID_ARG
+    assert call(input_type=9) == tfn.TFN_ERR_INVALID_ARG
+    assert call(input=None) == tfn.TFN_ERR_INVALID_ARG
+    f = tfn.make_frame(img, n, m, dict(fx=10.0, fy=11.0, u0=8.0, v0=8.0))
+    f.input_type = tfn.TFN_DISP_F32
+    assert tfn.tfn_normals(ctx.handle, ctypes.byref(f), ctypes.byref(meth), s) == tfn.TFN_ERR_UNSUPPORTED
+    f = tfn.make_frame(img, n, m, dict(fx=float("nan"), fy=10.0, u0=8.0, v0=8.0))
+    assert tfn.tfn_normals(ctx.handle, ctypes.byref(f), ctypes.byref(meth), s) == tfn.TFN_ERR_INVALID_ARG
+    bad = tfn.make_method(grad=7)
+    f = tfn.make_frame(img, n, m, dict(fx=10.0, fy=10.0, u0=8.0, v0=8.0))
+    assert tfn.tfn_normals(ctx.handle, ctypes.byref(f), ctypes.byref(bad), s) == tfn.TFN_ERR_INVALID_ARG
+
+
+def test_host_buffer_path_matches_device_path(torch, tfn, ctx):
+    frames = depth_frames([(120, 160), (480, 640), (77, 90)], 1400)
+    n_dev, m_dev = run_batch(torch, tfn, ctx, frames, grad="fd", phi="median")
+    inputs = [torch.from_numpy(img).pin_memory() for img, _ in frames]
+    normals = [torch.empty((3, img.shape[0], img.shape[1]), dtype=torch.float32).pin_memory() for img, _ in frames]
+    masks = [torch.empty(img.shape, dtype=torch.uint8).pin_memory() for img, _ in frames]
+    ctx.normals_batch_host(inputs, [c for _, c in frames], normals, masks, grad="fd", phi="median")
+    for k in range(len(frames)):
+        assert np.array_equal(normals[k].numpy(), n_dev[k]) and np.array_equal(masks[k].numpy(), m_dev[k])
+
+
+def test_full_batch_256_sampled_against_oracle(torch, tfn, ctx):
+    # the benchmark's launch: 256 noisy 480x640 frames in one call; three
+    # frames are compared with the oracle pixel by pixel, all frames for
+    # properties that hold at any size.
+    depth = scenes.noisy_batch(256)
+    d = tfn.empty_image(depth.shape, torch.float32)
+    d.copy_(torch.from_numpy(depth))
+    normals = tfn.empty_normals(480, 640, lead=(256,))
+    masks = tfn.empty_image((256, 480, 640), torch.uint8)
+    ctx.normals_batch([d[k] for k in range(256)], scenes.CAMERA, normals=[normals[k] for k in range(256)],
+                      masks=[masks[k] for k in range(256)])
+    torch.cuda.synchronize()
+    for k in (0, 97, 255):
+        compare(normals[k].cpu().numpy(), masks[k].cpu().numpy(), depth[k], scenes.CAMERA, grad="fd", phi="mean")
+    v = masks.bool()
+    nn = (normals.float() ** 2).sum(1)
+    assert torch.isfinite(normals).all()
+    assert ((nn - 1).abs()[v] < 1e-5).all() and (nn[~v] == 0).all()
+    border = torch.zeros((480, 640), dtype=torch.bool, device=v.device)
+    border[0, :] = border[-1, :] = True
+    border[:, 0] = border[:, -1] = True
+    assert not v[:, border].any()

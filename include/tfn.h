@@ -171,6 +171,37 @@ tfn_status tfn_normals_batch_host(tfn_ctx *ctx, const tfn_frame *frames, int n, 
  * when a bounded wait gave up (0: none).  Synchronises `stream`. */
 tfn_status tfn_device_status(tfn_ctx *ctx, uint32_t *bits, tfn_stream stream);
 
+/* ---- without any allocation ------------------------------------------------- */
+
+/* Largest n that tfn_normals_noalloc accepts. */
+#define TFN_NOALLOC_MAX_FRAMES 64
+
+/* Same result as tfn_normals_batch, for callers that may not allocate device
+ * memory at all: a host framework or plugin interface that owns every device
+ * byte and forbids cudaMalloc, or a latency-critical loop where cudaMalloc /
+ * cudaFree could synchronise the device.  (The paper has no counterpart: this
+ * is an interface concern of this library.)
+ *
+ * It takes no context.  The scratch the kernel needs (frame descriptors, TMA
+ * tensor maps, a status word; about 14 KB) lives in one fixed array compiled
+ * into the library, which every device that loads the library keeps until the
+ * process exits.  Limits and behaviour:
+ *   - n > TFN_NOALLOC_MAX_FRAMES returns TFN_ERR_INVALID_ARG before anything
+ *     is enqueued; otherwise arguments are validated as for tfn_normals_batch;
+ *   - works on the current CUDA device; the first call on each device looks
+ *     up the array's device address there (make that first call before any
+ *     stream capture);
+ *   - it calls no cudaMalloc, cudaFree or other allocating routine; the
+ *     descriptors are staged in thread-local host storage and copied into the
+ *     array on `stream`;
+ *   - every call reuses the same array and overwrites the previous call's
+ *     contents, so calls whose GPU work overlaps (other streams, or earlier
+ *     work still running on another stream) race and must be serialised by
+ *     the caller;
+ *   - kernel-side wait failures are not reported (there is no context to
+ *     hold them); use tfn_normals_batch where that matters. */
+tfn_status tfn_normals_noalloc(const tfn_frame *frames, int n, const tfn_method *method, tfn_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,8 +67,9 @@ _lib.tfn_normals.argtypes = [_P, ctypes.POINTER(tfn_frame), ctypes.POINTER(tfn_m
 _lib.tfn_normals_batch.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), _P]
 _lib.tfn_normals_batch_host.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), _P]
 _lib.tfn_device_status.argtypes = [_P, ctypes.POINTER(ctypes.c_uint32), _P]
+_lib.tfn_normals_noalloc.argtypes = [ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), _P]
 for _f in ("tfn_create", "tfn_destroy", "tfn_normals", "tfn_normals_batch", "tfn_normals_batch_host",
-           "tfn_device_status"):
+           "tfn_device_status", "tfn_normals_noalloc"):
     getattr(_lib, _f).restype = _I
 
 # The C entry points under their own names.
@@ -81,9 +82,12 @@ tfn_normals = _lib.tfn_normals
 tfn_normals_batch = _lib.tfn_normals_batch
 tfn_normals_batch_host = _lib.tfn_normals_batch_host
 tfn_device_status = _lib.tfn_device_status
+# For callers that may not allocate device memory (see include/tfn.h).
+tfn_normals_noalloc = _lib.tfn_normals_noalloc
+TFN_NOALLOC_MAX_FRAMES = 64
 
 EXPORTED = ["tfn_status_string", "tfn_version", "tfn_last_cuda_error", "tfn_create", "tfn_destroy", "tfn_normals",
-            "tfn_normals_batch", "tfn_normals_batch_host", "tfn_device_status"]
+            "tfn_normals_batch", "tfn_normals_batch_host", "tfn_device_status", "tfn_normals_noalloc"]
 
 
 class TfnError(RuntimeError):

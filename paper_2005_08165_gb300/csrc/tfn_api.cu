@@ -36,7 +36,7 @@ KernelFn kernel_for(int kind, int grad, int phi, int cfg)
 
 using namespace tfn;
 
-namespace {
+namespace tfn {
 
 thread_local char g_cuda_err[256] = "";
 
@@ -46,6 +46,10 @@ bool cuda_ok(cudaError_t e, const char *what)
     snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", what, cudaGetErrorString(e));
     return false;
 }
+
+}  // namespace tfn
+
+namespace {
 
 #define TFN_CUDA(call)                                   \
     do {                                                 \
@@ -141,6 +145,10 @@ void ctx_free(tfn_ctx *c, void *&p, size_t bytes)
     }
 }
 
+}  // namespace
+
+namespace tfn {
+
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 bool mult16(int64_t x) { return (x & 15) == 0; }
 
@@ -207,28 +215,6 @@ float refine_threshold(const tfn_frame &f, int phi)
     return t > 0 ? (float)t : 0.f;
 }
 
-void append_key(std::vector<unsigned char> &k, const void *p, size_t n)
-{
-    const unsigned char *b = (const unsigned char *)p;
-    k.insert(k.end(), b, b + n);
-}
-
-void frame_key(std::vector<unsigned char> &k, const tfn_frame &f)
-{
-    append_key(k, &f.input, sizeof f.input);
-    append_key(k, &f.input_pitch, sizeof f.input_pitch);
-    append_key(k, &f.height, sizeof f.height);
-    append_key(k, &f.width, sizeof f.width);
-    append_key(k, &f.input_type, sizeof f.input_type);
-    append_key(k, &f.disp_scale, sizeof f.disp_scale);
-    append_key(k, &f.cam, sizeof f.cam);
-    append_key(k, &f.normals, sizeof f.normals);
-    append_key(k, &f.normals_pitch, sizeof f.normals_pitch);
-    append_key(k, &f.normals_plane_stride, sizeof f.normals_plane_stride);
-    append_key(k, &f.mask, sizeof f.mask);
-    append_key(k, &f.mask_pitch, sizeof f.mask_pitch);
-}
-
 tfn_status encode_map(CUtensorMap *map, const tfn_frame &f, int cfg)
 {
     if (!load_encode()) {
@@ -251,6 +237,96 @@ tfn_status encode_map(CUtensorMap *map, const tfn_frame &f, int cfg)
         return TFN_ERR_CUDA;
     }
     return TFN_OK;
+}
+
+// Fills the device descriptor of one frame for tile shape `cfg`.
+FrameDesc describe_frame(const tfn_frame &f, int cfg, int phi, int tile_begin)
+{
+    const int tw = kCfgs[cfg].tw;
+    FrameDesc fd;
+    memset(&fd, 0, sizeof fd);
+    fd.out = (char *)f.normals;
+    fd.out_pitch = f.normals_pitch;
+    fd.out_plane = f.normals_plane_stride;
+    fd.mask = f.mask;
+    fd.mask_pitch = f.mask_pitch;
+    fd.H = f.height;
+    fd.W = f.width;
+    fd.tiles_x = (f.width + tw - 1) / tw;
+    fd.tile_begin = tile_begin;
+    fd.fx = f.cam.fx;
+    fd.fy = f.cam.fy;
+    fd.u0 = f.cam.u0;
+    fd.v0 = f.cam.v0;
+    fd.thr = refine_threshold(f, phi);
+    fd.kind = f.input_type;
+    return fd;
+}
+
+int frame_tiles(const tfn_frame &f, int cfg)
+{
+    const int tw = kCfgs[cfg].tw, th = kCfgs[cfg].th;
+    return ((f.width + tw - 1) / tw) * ((f.height + th - 1) / th);
+}
+
+// Launches the kernel for frames of one input kind whose descriptors and
+// tensor maps are already in device memory.
+tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
+                          uint32_t *d_status, int nframes, int total_tiles, int num_sms, cudaStream_t stream)
+{
+    KernelFn fn = kernel_for(kind, m.grad, m.phi, cfg);
+    if (!fn) return TFN_ERR_UNSUPPORTED;
+    const int threads = cfg_threads(cfg);
+    const size_t smem = smem_bytes(kind, cfg);
+    if (!cuda_ok(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                 "cudaFuncSetAttribute"))
+        return TFN_ERR_CUDA;
+    int per_sm = 0;
+    if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, threads, smem),
+                 "cudaOccupancyMaxActiveBlocksPerMultiprocessor"))
+        return TFN_ERR_CUDA;
+    if (per_sm < 1) per_sm = 1;
+    const int grid = std::min(total_tiles, per_sm * num_sms);
+    if (grid < 1) return TFN_OK;
+    LaunchArgs a;
+    a.frames = d_frames;
+    a.maps = d_maps;
+    a.status = d_status;
+    a.nframes = nframes;
+    a.total_tiles = total_tiles;
+    a.out_fmt = m.output;
+    a.flags = m.flags;
+    void *params[] = {&a};
+    if (!cuda_ok(cudaLaunchKernel((const void *)fn, dim3(grid), dim3(threads), params, smem, stream),
+                 "cudaLaunchKernel"))
+        return TFN_ERR_CUDA;
+    return TFN_OK;
+}
+
+}  // namespace tfn
+
+namespace {
+
+void append_key(std::vector<unsigned char> &k, const void *p, size_t n)
+{
+    const unsigned char *b = (const unsigned char *)p;
+    k.insert(k.end(), b, b + n);
+}
+
+void frame_key(std::vector<unsigned char> &k, const tfn_frame &f)
+{
+    append_key(k, &f.input, sizeof f.input);
+    append_key(k, &f.input_pitch, sizeof f.input_pitch);
+    append_key(k, &f.height, sizeof f.height);
+    append_key(k, &f.width, sizeof f.width);
+    append_key(k, &f.input_type, sizeof f.input_type);
+    append_key(k, &f.disp_scale, sizeof f.disp_scale);
+    append_key(k, &f.cam, sizeof f.cam);
+    append_key(k, &f.normals, sizeof f.normals);
+    append_key(k, &f.normals_pitch, sizeof f.normals_pitch);
+    append_key(k, &f.normals_plane_stride, sizeof f.normals_plane_stride);
+    append_key(k, &f.mask, sizeof f.mask);
+    append_key(k, &f.mask_pitch, sizeof f.mask_pitch);
 }
 
 size_t slot_bytes(int cap) { return (size_t)cap * sizeof(FrameDesc) + 128 + (size_t)cap * sizeof(CUtensorMap); }
@@ -298,10 +374,7 @@ tfn_status launch_group(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_me
     int si = -1;
     if (c->last_slot >= 0 && c->slots[c->last_slot].has_key && c->slots[c->last_slot].key == key) si = c->last_slot;
     int total = 0;
-    for (int i = 0; i < n; ++i) {
-        const int tw = kCfgs[cfg].tw, th = kCfgs[cfg].th;
-        total += ((frames[i].width + tw - 1) / tw) * ((frames[i].height + th - 1) / th);
-    }
+    for (int i = 0; i < n; ++i) total += frame_tiles(frames[i], cfg);
     if (si < 0) {
         si = c->next_slot;
         c->next_slot = (c->next_slot + 1) % kSlots;
@@ -314,26 +387,8 @@ tfn_status launch_group(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_me
         int tb = 0;
         for (int i = 0; i < n; ++i) {
             const tfn_frame &f = frames[i];
-            const int tw = kCfgs[cfg].tw, th = kCfgs[cfg].th;
-            FrameDesc fd;
-            memset(&fd, 0, sizeof fd);
-            fd.out = (char *)f.normals;
-            fd.out_pitch = f.normals_pitch;
-            fd.out_plane = f.normals_plane_stride;
-            fd.mask = f.mask;
-            fd.mask_pitch = f.mask_pitch;
-            fd.H = f.height;
-            fd.W = f.width;
-            fd.tiles_x = (f.width + tw - 1) / tw;
-            fd.tile_begin = tb;
-            tb += fd.tiles_x * ((f.height + th - 1) / th);
-            fd.fx = f.cam.fx;
-            fd.fy = f.cam.fy;
-            fd.u0 = f.cam.u0;
-            fd.v0 = f.cam.v0;
-            fd.thr = refine_threshold(f, m.phi);
-            fd.kind = kind;
-            d[i] = fd;
+            d[i] = describe_frame(f, cfg, m.phi, tb);
+            tb += frame_tiles(f, cfg);
             st = encode_map(&maps[i], f, cfg);
             if (st) return st;
         }
@@ -348,26 +403,9 @@ tfn_status launch_group(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_me
     c->last_slot = si;
     if (!s.done) TFN_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
 
-    KernelFn fn = kernel_for(kind, m.grad, m.phi, cfg);
-    if (!fn) return TFN_ERR_UNSUPPORTED;
-    const int threads = cfg_threads(cfg);
-    const size_t smem = smem_bytes(kind, cfg);
-    TFN_CUDA(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    TFN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, threads, smem));
-    if (per_sm < 1) per_sm = 1;
-    int grid = std::min(total, per_sm * c->num_sms);
-    if (grid < 1) return TFN_OK;
-    LaunchArgs a;
-    a.frames = slot_descs(s.dev);
-    a.maps = slot_maps(s.dev, s.cap);
-    a.status = c->status;
-    a.nframes = n;
-    a.total_tiles = total;
-    a.out_fmt = m.output;
-    a.flags = m.flags;
-    void *params[] = {&a};
-    TFN_CUDA(cudaLaunchKernel((const void *)fn, dim3(grid), dim3(threads), params, smem, stream));
+    tfn_status lst = launch_normals(kind, m, cfg, slot_descs(s.dev), slot_maps(s.dev, s.cap), c->status, n, total,
+                                    c->num_sms, stream);
+    if (lst) return lst;
     TFN_CUDA(cudaEventRecord(s.done, stream));
     return TFN_OK;
 }

@@ -68,3 +68,20 @@ typedef void (*KernelFn)(LaunchArgs);
 KernelFn kernel_for(int kind, int grad, int phi, int cfg);
 
 }  // namespace tfn
+
+#include "../../include/tfn.h"
+
+namespace tfn {
+
+// Host helpers shared by the entry points (tfn_api.cu).
+bool cuda_ok(cudaError_t e, const char *what);
+tfn_status validate_method(const tfn_method *m);
+tfn_status validate_frame(const tfn_frame *f, int out_fmt);
+float refine_threshold(const tfn_frame &f, int phi);
+tfn_status encode_map(CUtensorMap *map, const tfn_frame &f, int cfg);
+FrameDesc describe_frame(const tfn_frame &f, int cfg, int phi, int tile_begin);
+int frame_tiles(const tfn_frame &f, int cfg);
+tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
+                          uint32_t *d_status, int nframes, int total_tiles, int num_sms, cudaStream_t stream);
+
+}  // namespace tfn

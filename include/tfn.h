@@ -160,6 +160,25 @@ tfn_status tfn_normals(tfn_ctx *ctx, const tfn_frame *frame, const tfn_method *m
 tfn_status tfn_normals_batch(tfn_ctx *ctx, const tfn_frame *frames, int n, const tfn_method *method,
                              tfn_stream stream);
 
+/* ---- plans: a frozen batch replayed as a CUDA graph ---------------------- */
+
+typedef struct tfn_plan tfn_plan;
+
+/* Freezes a batch (frames, pointers, shapes, intrinsics, method): validates it
+ * as tfn_normals_batch does, uploads its frame descriptors and TMA tensor maps
+ * once into scratch the plan owns (counted against the context's budget;
+ * this call synchronises), and captures its kernel launches into a CUDA
+ * graph.  The images themselves are not copied: the plan reads and writes the
+ * caller's buffers each time it is launched. */
+tfn_status tfn_plan_create(tfn_ctx *ctx, const tfn_frame *frames, int n, const tfn_method *method, tfn_plan **plan);
+
+/* Replays the plan's graph on `stream`: the whole estimator over the batch,
+ * with no host work beyond one graph launch. */
+tfn_status tfn_plan_launch(tfn_plan *plan, tfn_stream stream);
+
+/* Waits for the device, releases the plan's scratch and graph. NULL is a no-op. */
+tfn_status tfn_plan_destroy(tfn_plan *plan);
+
 /* Same as tfn_normals_batch, but every pointer in `frames` is a HOST pointer
  * (page-locked memory is fastest).  The context stages the frames through
  * device buffers in chunks, overlapping host-to-device copies, kernels and
@@ -170,6 +189,12 @@ tfn_status tfn_normals_batch_host(tfn_ctx *ctx, const tfn_frame *frames, int n, 
 /* Reads and clears the device status word that kernels of this context set
  * when a bounded wait gave up (0: none).  Synchronises `stream`. */
 tfn_status tfn_device_status(tfn_ctx *ctx, uint32_t *bits, tfn_stream stream);
+
+/* Reads and clears the number of pixels that kernels of this context sent to
+ * the double-float path (whose FP32 error bound was too loose; see the
+ * accuracy notes of the kernel).  Diagnostics; counts wrap at 2^32.
+ * Synchronises `stream`. */
+tfn_status tfn_refined_pixels(tfn_ctx *ctx, uint64_t *count, tfn_stream stream);
 
 /* ---- without any allocation ------------------------------------------------- */
 

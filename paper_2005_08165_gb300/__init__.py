@@ -67,9 +67,14 @@ _lib.tfn_normals.argtypes = [_P, ctypes.POINTER(tfn_frame), ctypes.POINTER(tfn_m
 _lib.tfn_normals_batch.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), _P]
 _lib.tfn_normals_batch_host.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), _P]
 _lib.tfn_device_status.argtypes = [_P, ctypes.POINTER(ctypes.c_uint32), _P]
+_lib.tfn_plan_create.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), ctypes.POINTER(_P)]
+_lib.tfn_plan_launch.argtypes = [_P, _P]
+_lib.tfn_plan_destroy.argtypes = [_P]
+_lib.tfn_refined_pixels.argtypes = [_P, ctypes.POINTER(ctypes.c_uint64), _P]
 _lib.tfn_normals_noalloc.argtypes = [ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), _P]
 for _f in ("tfn_create", "tfn_destroy", "tfn_normals", "tfn_normals_batch", "tfn_normals_batch_host",
-           "tfn_device_status", "tfn_normals_noalloc"):
+           "tfn_device_status", "tfn_refined_pixels", "tfn_normals_noalloc", "tfn_plan_create", "tfn_plan_launch",
+           "tfn_plan_destroy"):
     getattr(_lib, _f).restype = _I
 
 # The C entry points under their own names.
@@ -82,12 +87,17 @@ tfn_normals = _lib.tfn_normals
 tfn_normals_batch = _lib.tfn_normals_batch
 tfn_normals_batch_host = _lib.tfn_normals_batch_host
 tfn_device_status = _lib.tfn_device_status
+tfn_refined_pixels = _lib.tfn_refined_pixels
+tfn_plan_create = _lib.tfn_plan_create
+tfn_plan_launch = _lib.tfn_plan_launch
+tfn_plan_destroy = _lib.tfn_plan_destroy
 # For callers that may not allocate device memory (see include/tfn.h).
 tfn_normals_noalloc = _lib.tfn_normals_noalloc
 TFN_NOALLOC_MAX_FRAMES = 64
 
 EXPORTED = ["tfn_status_string", "tfn_version", "tfn_last_cuda_error", "tfn_create", "tfn_destroy", "tfn_normals",
-            "tfn_normals_batch", "tfn_normals_batch_host", "tfn_device_status", "tfn_normals_noalloc"]
+            "tfn_normals_batch", "tfn_normals_batch_host", "tfn_device_status", "tfn_refined_pixels",
+            "tfn_normals_noalloc", "tfn_plan_create", "tfn_plan_launch", "tfn_plan_destroy"]
 
 
 class TfnError(RuntimeError):
@@ -262,7 +272,53 @@ class Context:
               "tfn_normals_batch_host")
         return normals, masks
 
+    def plan(self, inputs, cams, *, grad="fd", phi="mean", output="f32", disparity=False, disp_scale=1.0 / 16,
+             normals=None, masks=None, flags=0):
+        """Freezes a batch into a Plan (descriptors uploaded once, launches captured in a CUDA graph)."""
+        n = len(inputs)
+        if isinstance(cams, dict):
+            cams = [cams] * n
+        if normals is None:
+            normals = [empty_normals(x.shape[0], x.shape[1], output, x.device) for x in inputs]
+        if masks is None:
+            masks = [empty_image(tuple(x.shape), _torch().uint8, x.device) for x in inputs]
+        frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output)
+                                   for k in range(n)])
+        m = make_method(grad, phi, output, flags)
+        h = ctypes.c_void_p()
+        check(tfn_plan_create(self.handle, frames, n, ctypes.byref(m), ctypes.byref(h)), "tfn_plan_create")
+        return Plan(h, inputs, normals, masks)
+
+    def refined_pixels(self, stream=None) -> int:
+        """Pixels sent to the double-float path since the last call (diagnostics)."""
+        n = ctypes.c_uint64()
+        check(tfn_refined_pixels(self.handle, ctypes.byref(n), _stream_handle(stream)), "tfn_refined_pixels")
+        return n.value
+
     def device_status(self, stream=None) -> int:
         bits = ctypes.c_uint32()
         check(tfn_device_status(self.handle, ctypes.byref(bits), _stream_handle(stream)), "tfn_device_status")
         return bits.value
+
+
+class Plan:
+    """A frozen batch; launch() replays its CUDA graph on a stream."""
+
+    def __init__(self, handle, inputs, normals, masks):
+        self.handle = handle
+        self.inputs, self.normals, self.masks = inputs, normals, masks  # keep the buffers alive
+
+    def launch(self, stream=None):
+        check(tfn_plan_launch(self.handle, _stream_handle(stream)), "tfn_plan_launch")
+        return self.normals, self.masks
+
+    def close(self):
+        if self.handle:
+            tfn_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -107,6 +107,15 @@ struct tfn_ctx {
     std::vector<tfn_frame> chunk_frames;
 };
 
+struct tfn_plan {
+    tfn_ctx *ctx = nullptr;
+    void *dev = nullptr;  // FrameDesc[n] then CUtensorMap[n]
+    size_t bytes = 0;
+    int n = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 namespace {
 
 struct DeviceGuard {  // switches to the context's device for the call's duration
@@ -627,6 +636,106 @@ tfn_status tfn_normals_batch_host(tfn_ctx *c, const tfn_frame *frames, int n, co
         if (!cuda_ok(cudaStreamSynchronize(c->stages[k].stream), "cudaStreamSynchronize") && st == TFN_OK)
             st = TFN_ERR_CUDA;
     return st;
+}
+
+tfn_status tfn_plan_create(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method *m, tfn_plan **out)
+{
+    if (!out) return TFN_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!c || n < 1 || !frames) return TFN_ERR_INVALID_ARG;
+    tfn_status st = validate_method(m);
+    if (st) return st;
+    for (int i = 0; i < n; ++i)
+        if ((st = validate_frame(&frames[i], m->output))) return st;
+    DeviceGuard g(c->device);
+    if (!g.ok) return TFN_ERR_CUDA;
+    tfn_plan *p = new (std::nothrow) tfn_plan();
+    if (!p) return TFN_ERR_OUT_OF_MEMORY;
+    p->ctx = c;
+    p->n = n;
+    p->bytes = slot_bytes(n);
+    if ((st = ctx_alloc(c, &p->dev, p->bytes))) {
+        delete p;
+        return st;
+    }
+    const int cfg = c->cfg;
+    std::vector<unsigned char> host(p->bytes + 128);
+    void *hbase = (void *)(((uintptr_t)host.data() + 127) & ~(uintptr_t)127);
+    FrameDesc *d = slot_descs(hbase);
+    CUtensorMap *maps = slot_maps(hbase, n);
+    for (int i = 0, tb = 0; i < n; ++i) {
+        if (i > 0 && frames[i].input_type != frames[i - 1].input_type) tb = 0;
+        d[i] = describe_frame(frames[i], cfg, m->phi, tb);
+        tb += frame_tiles(frames[i], cfg);
+        if ((st = encode_map(&maps[i], frames[i], cfg))) break;
+    }
+    cudaStream_t cs = nullptr;
+    if (st == TFN_OK && !cuda_ok(cudaMemcpy(p->dev, hbase, p->bytes, cudaMemcpyHostToDevice), "cudaMemcpy"))
+        st = TFN_ERR_CUDA;
+    if (st == TFN_OK && !cuda_ok(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate"))
+        st = TFN_ERR_CUDA;
+    // capture one launch per run of frames of the same input kind
+    if (st == TFN_OK && cuda_ok(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture")) {
+        tfn_status lst = TFN_OK;
+        for (int i = 0; i < n && lst == TFN_OK;) {
+            int j = i + 1;
+            while (j < n && frames[j].input_type == frames[i].input_type) ++j;
+            int total = 0;
+            for (int k = i; k < j; ++k) total += frame_tiles(frames[k], cfg);
+            lst = launch_normals(frames[i].input_type, *m, cfg, slot_descs(p->dev) + i, slot_maps(p->dev, n) + i,
+                                 c->status, j - i, total, c->num_sms, cs);
+            i = j;
+        }
+        if (!cuda_ok(cudaStreamEndCapture(cs, &p->graph), "cudaStreamEndCapture") && lst == TFN_OK) lst = TFN_ERR_CUDA;
+        st = lst;
+        if (st == TFN_OK && !cuda_ok(cudaGraphInstantiate(&p->exec, p->graph, 0), "cudaGraphInstantiate"))
+            st = TFN_ERR_CUDA;
+    } else if (st == TFN_OK) {
+        st = TFN_ERR_CUDA;
+    }
+    if (cs) cudaStreamDestroy(cs);
+    if (st) {
+        tfn_plan_destroy(p);
+        return st;
+    }
+    *out = p;
+    return TFN_OK;
+}
+
+tfn_status tfn_plan_launch(tfn_plan *p, tfn_stream stream)
+{
+    if (!p || !p->exec) return TFN_ERR_INVALID_ARG;
+    DeviceGuard g(p->ctx->device);
+    if (!g.ok) return TFN_ERR_CUDA;
+    TFN_CUDA(cudaGraphLaunch(p->exec, (cudaStream_t)stream));
+    return TFN_OK;
+}
+
+tfn_status tfn_plan_destroy(tfn_plan *p)
+{
+    if (!p) return TFN_OK;
+    DeviceGuard g(p->ctx->device);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->dev) {
+        cudaDeviceSynchronize();  // a replay may still read the descriptors
+        ctx_free(p->ctx, p->dev, p->bytes);
+    }
+    delete p;
+    return TFN_OK;
+}
+
+tfn_status tfn_refined_pixels(tfn_ctx *c, uint64_t *count, tfn_stream stream)
+{
+    if (!c || !count) return TFN_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!g.ok) return TFN_ERR_CUDA;
+    TFN_CUDA(cudaMemcpyAsync(c->status_host, c->status + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                             (cudaStream_t)stream));
+    TFN_CUDA(cudaMemsetAsync(c->status + 1, 0, sizeof(uint32_t), (cudaStream_t)stream));
+    TFN_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    *count = *c->status_host;
+    return TFN_OK;
 }
 
 tfn_status tfn_device_status(tfn_ctx *c, uint32_t *bits, tfn_stream stream)

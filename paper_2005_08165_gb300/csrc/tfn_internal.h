@@ -36,7 +36,7 @@ static_assert(sizeof(FrameDesc) == 96, "FrameDesc layout");
 struct LaunchArgs {
     const FrameDesc *frames;
     const CUtensorMap *maps;  // one 2D tiled map per frame, 64-byte aligned
-    uint32_t *status;         // device status word (DEVERR_* bits)
+    uint32_t *status;         // [0]: DEVERR_* bits, [1]: refined-pixel count
     int32_t nframes;
     int32_t total_tiles;
     int32_t out_fmt;
@@ -51,7 +51,7 @@ struct TileCfg {
 };
 constexpr int kNumCfg = 3;
 constexpr TileCfg kCfgs[kNumCfg] = {{64, 32, 2}, {128, 16, 2}, {64, 16, 1}};
-constexpr int kStages = 3;
+constexpr int kStages = 6;
 
 inline int cfg_threads(int) { return 256; }
 inline int kind_elem_size(int kind) { return (kind == KIND_DEPTH_F32 || kind == KIND_DISP_F32) ? 4 : 2; }

@@ -459,16 +459,11 @@ struct PixelResult {
 // instructions; invalid pixels, the special case and pixels that need the
 // double-float path are resolved by selects at the end.
 template <int KIND, int GRAD, int PHI, int ROWS>
-__device__ __forceinline__ PixelResult pixel_normal(const Win<KIND, ROWS> &W, int a, int c, int u, int v, float fx,
-                                                    float fy, float u0, float v0, float thr, bool refine_all)
+__device__ __forceinline__ PixelResult pixel_normal(const Win<KIND, ROWS> &W, unsigned evmask, int a, int c, int u, int v,
+                                                    float fx, float fy, float u0, float v0, float thr, bool refine_all)
 {
-    // evaluable: the centre and every filter tap valid
-    const unsigned m3 = 7u << (c - 1), m1 = 1u << c;
-    bool ev;
-    if (GRAD == GRAD_FD)
-        ev = ((W.ok[a] & m3) == m3) && (W.ok[a - 1] & m1) && (W.ok[a + 1] & m1);
-    else
-        ev = ((W.ok[a - 1] & W.ok[a] & W.ok[a + 1] & m3) == m3);
+    // evaluable: the centre and every filter tap valid (bit c of the row's mask)
+    const bool ev = (evmask >> c) & 1u;
     df Gu, Gv;
     gradients_win<KIND, GRAD, ROWS>(W, a, c, Gu, Gv);
     const float gu = __fadd_rn(Gu.h, Gu.l), gv = __fadd_rn(Gv.h, Gv.l);
@@ -555,16 +550,41 @@ __device__ __forceinline__ PixelResult pixel_normal(const Win<KIND, ROWS> &W, in
     return res;
 }
 
-template <int KIND, int GRAD, int PHI, int ROWS>
-__device__ __forceinline__ Vec3 refine_at(const Win<KIND, ROWS> &W, int a, int c, int u, int v, float fx, float fy,
-                                          float u0, float v0)
+// Double-float recomputation of the pixel whose 3x3 window starts at
+// element `base` of the tile in shared memory (the tile is still resident:
+// its buffer is released only after the refinement).  One call site keeps
+// the rare path out of the main instruction stream.
+template <int KIND, int GRAD, int PHI>
+__device__ __noinline__ Vec3 refine_from_tile(const void *tile, int base, int SW, int u, int v, float fx, float fy,
+                                              float u0, float v0)
 {
-    const unsigned okbits = ((W.ok[a - 1] >> (c - 1)) & 7u) | (((W.ok[a] >> (c - 1)) & 7u) << 3) |
-                            (((W.ok[a + 1] >> (c - 1)) & 7u) << 6);
-    return refine_pixel<KIND, GRAD, PHI>(W.z[a - 1][c - 1], W.z[a - 1][c], W.z[a - 1][c + 1], W.z[a][c - 1], W.z[a][c],
-                                         W.z[a][c + 1], W.z[a + 1][c - 1], W.z[a + 1][c], W.z[a + 1][c + 1], okbits, u,
-                                         v, fx, fy, u0, v0);
+    typedef typename KindTraits<KIND>::T T;
+    const T *t = reinterpret_cast<const T *>(tile) + base;
+    float z[9];
+    unsigned okbits = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            bool ok;
+            z[3 * a + b] = decode<KIND>(t[a * SW + b], ok);
+            okbits |= (unsigned)ok << (3 * a + b);
+        }
+    return refine_pixel<KIND, GRAD, PHI>(z[0], z[1], z[2], z[3], z[4], z[5], z[6], z[7], z[8], okbits, u, v, fx, fy, u0,
+                                         v0);
 }
+
+// Bit c (1..4) set iff pixel column c of window row a is evaluable: the centre
+// and every tap of both filters valid.
+template <int GRAD, int KIND, int ROWS>
+__device__ __forceinline__ unsigned evaluable_row(const Win<KIND, ROWS> &W, int a)
+{
+    const unsigned m = W.ok[a];
+    if (GRAD == GRAD_FD) return m & (m >> 1) & (m << 1) & W.ok[a - 1] & W.ok[a + 1];
+    const unsigned t = W.ok[a - 1] & m & W.ok[a + 1];
+    return t & (t >> 1) & (t << 1);
+}
+
 
 // ------------------------------------------------------------ TMA / mbarrier
 
@@ -582,17 +602,26 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
 
 // Bounded wait for the phase with parity `phase`; false if it did not
 // complete within kWaitCycles.
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase)
+{
+    uint32_t done;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(done)
+                 : "r"(bar), "r"(phase)
+                 : "memory");
+    return done != 0;
+}
+
+// Bounded wait for the phase with parity `phase`; false if it did not
+// complete within kWaitCycles (the clock is read every 16 polls).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase)
 {
+    if (mbar_try(bar, phase)) return true;
     const long long t0 = clock64();
     for (;;) {
-        uint32_t done;
-        asm volatile(
-            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-            : "=r"(done)
-            : "r"(bar), "r"(phase)
-            : "memory");
-        if (done) return true;
+#pragma unroll 1
+        for (int k = 0; k < 16; ++k)
+            if (mbar_try(bar, phase)) return true;
         if (clock64() - t0 > kWaitCycles) return false;
     }
 }
@@ -615,6 +644,14 @@ __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy
 
 // ------------------------------------------------------------ stores
 
+// Where a tile's results go (copied to registers once per tile).
+struct OutDesc {
+    char *out;
+    int64_t out_pitch, out_plane;
+    uint8_t *mask;
+    int64_t mask_pitch;
+};
+
 __device__ __forceinline__ uint32_t pack2(float a, float b, int fmt)
 {
     if (fmt == OUT_F16 || fmt == OUT_F16X4) {
@@ -626,7 +663,7 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, int fmt)
 }
 
 // Stores 4 consecutive pixels (n valid of them, starting at column u).
-__device__ __forceinline__ void store4(const FrameDesc &fd, int fmt, int u, int v, int n, const float (&x)[4],
+__device__ __forceinline__ void store4(const OutDesc &fd, int fmt, int u, int v, int n, const float (&x)[4],
                                        const float (&y)[4], const float (&zz)[4], const uint8_t (&mk)[4])
 {
     char *row = fd.out + (int64_t)v * fd.out_pitch;
@@ -673,24 +710,9 @@ __device__ __forceinline__ void store4(const FrameDesc &fd, int fmt, int u, int 
     }
 }
 
-// Refines pixel slot b = pr * 4 + c of the thread's window (compile-time
-// window indices in every branch, so the window stays in registers).
-template <int KIND, int GRAD, int PHI, int ROWS>
-__device__ __forceinline__ Vec3 refine_slot(const Win<KIND, ROWS> &W, int b, int x0, int y0, float fx, float fy,
-                                            float u0, float v0)
-{
-#define TFN_R(PRV, CV)                                                                                    \
-    if (b == PRV * 4 + CV) return refine_at<KIND, GRAD, PHI, ROWS>(W, PRV + 1, CV + 1, x0 + CV, y0 + PRV, fx, fy, u0, v0);
-    TFN_R(0, 0) TFN_R(0, 1) TFN_R(0, 2) TFN_R(0, 3)
-    if constexpr (ROWS > 1) {
-        TFN_R(1, 0) TFN_R(1, 1) TFN_R(1, 2) TFN_R(1, 3)
-    }
-#undef TFN_R
-    return {0.f, 0.f, 0.f};
-}
 
 // Stores one pixel's normal (the mask is already written).
-__device__ __forceinline__ void store1(const FrameDesc &fd, int fmt, int u, int v, Vec3 n)
+__device__ __forceinline__ void store1(const OutDesc &fd, int fmt, int u, int v, Vec3 n)
 {
     char *row = fd.out + (int64_t)v * fd.out_pitch;
     if (fmt == OUT_F32) {
@@ -796,9 +818,16 @@ __global__ void __launch_bounds__(kThreads, 2) normals_kernel(const __grid_const
             if (lane == 0) atomicOr(args.status, DEVERR_TMA_WAIT);
             return;
         }
+        unsigned pending = 0;  // pixels (pr * 4 + c) that need the double-float path
         const StageInfo &si = info[s];
         const FrameDesc &fd = si.fd;
         const int W = fd.W, H = fd.H;
+        OutDesc out;
+        out.out = fd.out;
+        out.out_pitch = fd.out_pitch;
+        out.out_plane = fd.out_plane;
+        out.mask = fd.mask;
+        out.mask_pitch = fd.mask_pitch;
         const int x0 = si.x0 + 4 * tx;
         const int y0 = si.y0 + PR * ty;
         if (x0 < W && y0 < H) {
@@ -806,33 +835,43 @@ __global__ void __launch_bounds__(kThreads, 2) normals_kernel(const __grid_const
             Win<KIND, PR> win;
             load_window<KIND, PR>(smem + s * STRIDE, SW, PADX, PR * ty, 4 * tx, win);
             const int nvalid = min(4, W - x0);
-            unsigned pending = 0;  // pixels (pr * 4 + c) that need the double-float path
 #pragma unroll
             for (int pr = 0; pr < PR; ++pr) {
                 const int v = y0 + pr;
+                const unsigned evm = evaluable_row<GRAD, KIND, PR>(win, pr + 1);
                 float ox[4], oy[4], oz[4];
                 uint8_t mk[4];
+                unsigned rbits = 0;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const PixelResult r = pixel_normal<KIND, GRAD, PHI, PR>(win, pr + 1, c + 1, x0 + c, v, fx, fy, u0,
-                                                                            v0, thr, refine_all);
+                    const PixelResult r = pixel_normal<KIND, GRAD, PHI, PR>(win, evm, pr + 1, c + 1, x0 + c, v, fx, fy,
+                                                                            u0, v0, thr, refine_all);
                     ox[c] = r.x;
                     oy[c] = r.y;
                     oz[c] = r.z;
                     mk[c] = r.valid ? 1 : 0;
-                    pending |= (unsigned)(r.refine && c < nvalid && v < H) << (pr * 4 + c);
+                    rbits |= r.refine ? 1u << c : 0u;
                 }
-                if (v < H) store4(fd, args.out_fmt, x0, v, nvalid, ox, oy, oz, mk);
+                if (v < H) {
+                    store4(out, args.out_fmt, x0, v, nvalid, ox, oy, oz, mk);
+                    pending |= (rbits & ((1u << nvalid) - 1u)) << (pr * 4);
+                }
             }
             // Deferred refinement: rare, so it runs after the stores and off the
             // main instruction stream; a later store to the same pixel wins.
-            while (pending) {
-                const int b = __ffs(pending) - 1;
-                pending &= pending - 1;
-                const Vec3 n = refine_slot<KIND, GRAD, PHI, PR>(win, b, x0, y0, fx, fy, u0, v0);
-                store1(fd, args.out_fmt, x0 + (b & 3), y0 + (b >> 2), n);
+            unsigned todo = pending;
+            while (todo) {
+                const int b = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int pr = b >> 2, c = b & 3;
+                const Vec3 n = refine_from_tile<KIND, GRAD, PHI>(smem + s * STRIDE, (PR * ty + pr) * SW + PADX + 4 * tx + c - 1,
+                                                                 SW, x0 + c, y0 + pr, fx, fy, u0, v0);
+                store1(out, args.out_fmt, x0 + c, y0 + pr, n);
             }
         }
+        // count of refined pixels (diagnostics): one atomic per warp, only if any
+        const unsigned nref = __reduce_add_sync(0xffffffffu, (unsigned)__popc(pending));
+        if (lane == 0 && nref) atomicAdd(args.status + 1, nref);
         // release the buffer; the last warp out refills it
         __syncwarp();
         if (lane == 0) {

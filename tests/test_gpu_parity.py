@@ -270,3 +270,29 @@ def test_full_batch_256_sampled_against_oracle(torch, tfn, ctx):
     border[0, :] = border[-1, :] = True
     border[:, 0] = border[:, -1] = True
     assert not v[:, border].any()
+
+
+def test_plan_graph_replay_matches_batch(torch, tfn, ctx):
+    # a frozen batch replayed as a CUDA graph gives the same bits as the direct call
+    frames = depth_frames([(67, 131), (480, 640), (33, 64)], 1500)
+    inputs = [to_dev(torch, tfn, img) for img, _ in frames]
+    cams = [cam for _, cam in frames]
+    n_ref, m_ref = ctx.normals_batch(inputs, cams, grad="sobel", phi="median")
+    plan = ctx.plan(inputs, cams, grad="sobel", phi="median")
+    s = torch.cuda.Stream()
+    for _ in range(3):
+        for x in plan.normals:
+            x.zero_()
+        plan.launch(s)
+        s.synchronize()
+        for a, b, ma, mb in zip(plan.normals, n_ref, plan.masks, m_ref):
+            assert torch.equal(a, b) and torch.equal(ma, mb)
+    # the plan reads the caller's buffers at each launch: new input, new result
+    inputs[0].mul_(2.0)  # a global depth scale leaves the normals unchanged
+    inputs[1].copy_(torch.from_numpy(depth_frames([(480, 640)], 1600)[0][0]))
+    plan.launch(s)
+    s.synchronize()
+    assert torch.equal(plan.normals[0], n_ref[0])
+    compare(plan.normals[1].cpu().numpy(), plan.masks[1].cpu().numpy(), inputs[1].cpu().numpy(), cams[1],
+            grad="sobel", phi="median")
+    plan.close()

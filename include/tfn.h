@@ -160,6 +160,19 @@ tfn_status tfn_normals(tfn_ctx *ctx, const tfn_frame *frame, const tfn_method *m
 tfn_status tfn_normals_batch(tfn_ctx *ctx, const tfn_frame *frames, int n, const tfn_method *method,
                              tfn_stream stream);
 
+/* ---- tile shapes ------------------------------------------------------------ */
+
+/* Number of tile shapes the kernels are compiled for. */
+int tfn_tile_shape_count(void);
+
+/* Tile width and height in pixels and pixel rows per thread of shape `index`
+ * (each thread computes 4 columns x rows_per_thread pixels). */
+tfn_status tfn_tile_shape_info(int index, int *tile_w, int *tile_h, int *rows_per_thread);
+
+/* Selects the tile shape used by later calls of this context (default 0).
+ * Results do not depend on the shape; speed does (an autotuner picks it). */
+tfn_status tfn_set_tile_shape(tfn_ctx *ctx, int index);
+
 /* ---- plans: a frozen batch replayed as a CUDA graph ---------------------- */
 
 typedef struct tfn_plan tfn_plan;

@@ -67,6 +67,11 @@ _lib.tfn_normals.argtypes = [_P, ctypes.POINTER(tfn_frame), ctypes.POINTER(tfn_m
 _lib.tfn_normals_batch.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), _P]
 _lib.tfn_normals_batch_host.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), _P]
 _lib.tfn_device_status.argtypes = [_P, ctypes.POINTER(ctypes.c_uint32), _P]
+_lib.tfn_tile_shape_count.restype = _I
+_lib.tfn_tile_shape_info.argtypes = [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]
+_lib.tfn_tile_shape_info.restype = _I
+_lib.tfn_set_tile_shape.argtypes = [_P, _I]
+_lib.tfn_set_tile_shape.restype = _I
 _lib.tfn_plan_create.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), ctypes.POINTER(_P)]
 _lib.tfn_plan_launch.argtypes = [_P, _P]
 _lib.tfn_plan_destroy.argtypes = [_P]
@@ -88,6 +93,9 @@ tfn_normals_batch = _lib.tfn_normals_batch
 tfn_normals_batch_host = _lib.tfn_normals_batch_host
 tfn_device_status = _lib.tfn_device_status
 tfn_refined_pixels = _lib.tfn_refined_pixels
+tfn_tile_shape_count = _lib.tfn_tile_shape_count
+tfn_tile_shape_info = _lib.tfn_tile_shape_info
+tfn_set_tile_shape = _lib.tfn_set_tile_shape
 tfn_plan_create = _lib.tfn_plan_create
 tfn_plan_launch = _lib.tfn_plan_launch
 tfn_plan_destroy = _lib.tfn_plan_destroy
@@ -97,7 +105,8 @@ TFN_NOALLOC_MAX_FRAMES = 64
 
 EXPORTED = ["tfn_status_string", "tfn_version", "tfn_last_cuda_error", "tfn_create", "tfn_destroy", "tfn_normals",
             "tfn_normals_batch", "tfn_normals_batch_host", "tfn_device_status", "tfn_refined_pixels",
-            "tfn_normals_noalloc", "tfn_plan_create", "tfn_plan_launch", "tfn_plan_destroy"]
+            "tfn_normals_noalloc", "tfn_plan_create", "tfn_plan_launch", "tfn_plan_destroy", "tfn_tile_shape_count",
+            "tfn_tile_shape_info", "tfn_set_tile_shape"]
 
 
 class TfnError(RuntimeError):
@@ -289,6 +298,9 @@ class Context:
         check(tfn_plan_create(self.handle, frames, n, ctypes.byref(m), ctypes.byref(h)), "tfn_plan_create")
         return Plan(h, inputs, normals, masks)
 
+    def set_tile_shape(self, index: int):
+        check(tfn_set_tile_shape(self.handle, index), "tfn_set_tile_shape")
+
     def refined_pixels(self, stream=None) -> int:
         """Pixels sent to the double-float path since the last call (diagnostics)."""
         n = ctypes.c_uint64()
@@ -299,6 +311,16 @@ class Context:
         bits = ctypes.c_uint32()
         check(tfn_device_status(self.handle, ctypes.byref(bits), _stream_handle(stream)), "tfn_device_status")
         return bits.value
+
+
+def tile_shapes():
+    """[(tile_w, tile_h, rows_per_thread)] for every compiled tile shape."""
+    out = []
+    for i in range(tfn_tile_shape_count()):
+        w, h, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(tfn_tile_shape_info(i, ctypes.byref(w), ctypes.byref(h), ctypes.byref(r)), "tfn_tile_shape_info")
+        out.append((w.value, h.value, r.value))
+    return out
 
 
 class Plan:

@@ -725,6 +725,25 @@ tfn_status tfn_plan_destroy(tfn_plan *p)
     return TFN_OK;
 }
 
+int tfn_tile_shape_count(void) { return kNumCfg; }
+
+tfn_status tfn_tile_shape_info(int index, int *tile_w, int *tile_h, int *rows_per_thread)
+{
+    if (index < 0 || index >= kNumCfg) return TFN_ERR_INVALID_ARG;
+    if (tile_w) *tile_w = kCfgs[index].tw;
+    if (tile_h) *tile_h = kCfgs[index].th;
+    if (rows_per_thread) *rows_per_thread = kCfgs[index].pr;
+    return TFN_OK;
+}
+
+tfn_status tfn_set_tile_shape(tfn_ctx *c, int index)
+{
+    if (!c || index < 0 || index >= kNumCfg) return TFN_ERR_INVALID_ARG;
+    c->cfg = index;
+    c->last_slot = -1;  // descriptors depend on the tile shape
+    return TFN_OK;
+}
+
 tfn_status tfn_refined_pixels(tfn_ctx *c, uint64_t *count, tfn_stream stream)
 {
     if (!c || !count) return TFN_ERR_INVALID_ARG;

@@ -52,6 +52,7 @@ struct TileCfg {
 constexpr int kNumCfg = 3;
 constexpr TileCfg kCfgs[kNumCfg] = {{64, 32, 2}, {128, 16, 2}, {64, 16, 1}};
 constexpr int kStages = 6;
+constexpr int kFrameTableMax = 160;  // frames whose descriptors a CTA keeps in shared memory
 
 inline int cfg_threads(int) { return 256; }
 inline int kind_elem_size(int kind) { return (kind == KIND_DEPTH_F32 || kind == KIND_DISP_F32) ? 4 : 2; }
@@ -61,7 +62,10 @@ inline int box_w(int kind, int c) { return kCfgs[c].tw + 2 * kind_padx(kind); }
 inline int box_h(int c) { return kCfgs[c].th + 2; }
 inline size_t stage_bytes(int kind, int c) { return (size_t)box_w(kind, c) * box_h(c) * kind_elem_size(kind); }
 inline size_t stage_stride(int kind, int c) { return (stage_bytes(kind, c) + 1023) & ~(size_t)1023; }
-inline size_t smem_bytes(int kind, int c) { return kStages * stage_stride(kind, c) + 128; }
+inline size_t smem_bytes(int kind, int c)
+{
+    return kStages * stage_stride(kind, c) + kFrameTableMax * sizeof(FrameDesc) + 128;
+}
 
 // Kernel entry points, one per (kind, grad, phi, cfg); defined in tfn_k_*.cu.
 typedef void (*KernelFn)(LaunchArgs);

@@ -323,8 +323,8 @@ struct EdgeR {
 };
 __device__ __forceinline__ EdgeR edge_recip(float delta)
 {
-    const float r = delta * rcp_approx(__fmaf_rn(delta, delta, kEdgeEps));
-    return {r, delta * r};
+    const float r = __fmul_rn(delta, rcp_approx(__fmaf_rn(delta, delta, kEdgeEps)));
+    return {r, __fmul_rn(delta, r)};
 }
 
 // The register window of one thread: ROWS+2 sample rows x 6 columns around
@@ -415,8 +415,8 @@ __device__ __forceinline__ float rho(const Win<KIND, ROWS> &W, int a, int c, int
     const bool fwd = dv > 0 || (dv == 0 && du > 0);  // i precedes j in raster order
     const EdgeR e = fwd ? edge<KIND, ROWS>(W, a, c, a2, c2) : edge<KIND, ROWS>(W, a2, c2, a, c);
     k = e.k;
-    if (KindTraits<KIND>::disparity) return fwd ? -W.z[a][c] * e.r : W.z[a][c] * e.r;
-    return fwd ? W.z[a2][c2] * e.r : -W.z[a2][c2] * e.r;
+    if (KindTraits<KIND>::disparity) return fwd ? -__fmul_rn(W.z[a][c], e.r) : __fmul_rn(W.z[a][c], e.r);
+    return fwd ? __fmul_rn(W.z[a2][c2], e.r) : -__fmul_rn(W.z[a2][c2], e.r);
 }
 
 // Exact difference of two taps as h + l (w-differences carry the w residuals).
@@ -457,7 +457,9 @@ struct PixelResult {
 
 // Main FP32 path of one pixel, branch-free: every lane runs the same
 // instructions; invalid pixels, the special case and pixels that need the
-// double-float path are resolved by selects at the end.
+// double-float path are resolved by selects at the end.  Every product is an
+// explicit __fmul_rn (never contracted into an FMA), so a pixel's bits do not
+// depend on which row of a thread's window it sits in or on the tile shape.
 template <int KIND, int GRAD, int PHI, int ROWS>
 __device__ __forceinline__ PixelResult pixel_normal(const Win<KIND, ROWS> &W, unsigned evmask, int a, int c, int u, int v,
                                                     float fx, float fy, float u0, float v0, float thr, bool refine_all)
@@ -490,8 +492,8 @@ __device__ __forceinline__ PixelResult pixel_normal(const Win<KIND, ROWS> &W, un
         float S = 0.f, Sabs = 0.f, m = 0.f;
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
-            S = __fmaf_rn(num[p], rj[p] - rm[p], S);
-            Sabs = __fmaf_rn(fabsf(num[p]), fabsf(rj[p]) + fabsf(rm[p]), Sabs);
+            S = __fmaf_rn(num[p], __fsub_rn(rj[p], rm[p]), S);
+            Sabs = __fmaf_rn(fabsf(num[p]), __fadd_rn(fabsf(rj[p]), fabsf(rm[p])), Sabs);
             if (GRAD == GRAD_FD && !KindTraits<KIND>::disparity && p >= 2) {
                 // FD: a diagonal neighbour may be a hole (its rho is 0 already)
                 m += (W.z[a + dv_[p]][c + du_[p]] != 0.f ? kj[p] : 0.f);
@@ -509,7 +511,7 @@ __device__ __forceinline__ PixelResult pixel_normal(const Win<KIND, ROWS> &W, un
         unsigned sgn = 0;  // sign bit of the next sentinel: +inf, -inf, +inf, ...
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
-            const float cand[2] = {num[p] * rj[p], -num[p] * rm[p]};
+            const float cand[2] = {__fmul_rn(num[p], rj[p]), -__fmul_rn(num[p], rm[p])};
             const float rr[2] = {rj[p], rm[p]};
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
@@ -533,20 +535,21 @@ __device__ __forceinline__ PixelResult pixel_normal(const Win<KIND, ROWS> &W, un
         TFN_CE(1, 2) TFN_CE(3, 4) TFN_CE(5, 6)
 #undef TFN_CE
         const bool odd = cnt & 1;
-        mF = odd ? s[3] : 0.5f * (s[3] + s[4]);
+        mF = odd ? s[3] : __fmul_rn(0.5f, __fadd_rn(s[3], s[4]));
         mbound = odd ? fabsf(s[3]) : fmaxf(fabsf(s[3]), fabsf(s[4]));
         scale = 1.f;
     }
-    const float A = __fmaf_rn((float)u - u0, gu, ((float)v - v0) * gv);
-    const float nxp = (scale * fx) * gu, nyp = (scale * fy) * gv, nzp = -__fmaf_rn(scale, A, mF);
-    const float nn = __fmaf_rn(nxp, nxp, __fmaf_rn(nyp, nyp, nzp * nzp));
+    const float A = __fmaf_rn(__fsub_rn((float)u, u0), gu, __fmul_rn(__fsub_rn((float)v, v0), gv));
+    const float nxp = __fmul_rn(__fmul_rn(scale, fx), gu), nyp = __fmul_rn(__fmul_rn(scale, fy), gv);
+    const float nzp = -__fmaf_rn(scale, A, mF);
+    const float nn = __fmaf_rn(nxp, nxp, __fmaf_rn(nyp, nyp, __fmul_rn(nzp, nzp)));
     const float rs = rsqrt_approx(nn);
     PixelResult res;
     res.valid = ev;
-    res.refine = ev && !flat && (refine_all || mbound > thr * (nn * rs));
-    res.x = ev && !flat ? -nxp * rs : 0.f;
-    res.y = ev && !flat ? -nyp * rs : 0.f;
-    res.z = ev ? (flat ? -1.f : -nzp * rs) : 0.f;
+    res.refine = ev && !flat && (refine_all || mbound > __fmul_rn(thr, __fmul_rn(nn, rs)));
+    res.x = ev && !flat ? -__fmul_rn(nxp, rs) : 0.f;
+    res.y = ev && !flat ? -__fmul_rn(nyp, rs) : 0.f;
+    res.z = ev ? (flat ? -1.f : -__fmul_rn(nzp, rs)) : 0.f;
     return res;
 }
 
@@ -605,10 +608,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase)
 {
     uint32_t done;
-    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                 : "=r"(done)
-                 : "r"(bar), "r"(phase)
-                 : "memory");
+    // the suspend-time hint (ns) lets a waiting warp sleep instead of spinning
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(bar), "r"(phase), "r"(20000)
+        : "memory");
     return done != 0;
 }
 
@@ -766,10 +771,21 @@ __global__ void __launch_bounds__(kThreads, 2) normals_kernel(const __grid_const
     __shared__ int released[kStages];
     __shared__ __align__(16) StageInfo info[kStages];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    // The launch's frame table, copied once into shared memory when it fits,
+    // so that refilling a buffer never waits on global memory.
+    FrameDesc *ftab = reinterpret_cast<FrameDesc *>(smem + kStages * STRIDE);
+    const bool ftab_smem = args.nframes <= kFrameTableMax;
+    const FrameDesc *frames = ftab_smem ? ftab : args.frames;
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int total = args.total_tiles, first = blockIdx.x, step = gridDim.x;
 
+    if (ftab_smem) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(args.frames);
+        uint4 *dst = reinterpret_cast<uint4 *>(ftab);
+        const int words = args.nframes * (int)(sizeof(FrameDesc) / 16);
+        for (int k = tid; k < words; k += kThreads) dst[k] = __ldg(src + k);
+    }
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(smem_addr(&full[s]), 1);
@@ -783,17 +799,17 @@ __global__ void __launch_bounds__(kThreads, 2) normals_kernel(const __grid_const
     // Filling side (whichever lane fills a buffer): frame cursor, last fenced map.
     int pf = 0, fenced = -1;
     auto fill = [&](int t, int s) {
-        while (pf + 1 < args.nframes && __ldg(&args.frames[pf + 1].tile_begin) <= t) ++pf;
+        while (pf + 1 < args.nframes && frames[pf + 1].tile_begin <= t) ++pf;
         const CUtensorMap *map = args.maps + pf;
         if (pf != fenced) {
             fence_tensormap_acquire(map);
             fenced = pf;
         }
         StageInfo &si = info[s];
-        const uint4 *src = reinterpret_cast<const uint4 *>(args.frames + pf);
+        const uint4 *src = reinterpret_cast<const uint4 *>(frames + pf);
         uint4 *dst = reinterpret_cast<uint4 *>(&si.fd);
 #pragma unroll
-        for (int k = 0; k < (int)(sizeof(FrameDesc) / 16); ++k) dst[k] = __ldg(src + k);
+        for (int k = 0; k < (int)(sizeof(FrameDesc) / 16); ++k) dst[k] = src[k];
         const int lt = t - si.fd.tile_begin;
         const int txs = si.fd.tiles_x;
         si.x0 = (lt % txs) * TW;

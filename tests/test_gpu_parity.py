@@ -296,3 +296,24 @@ def test_plan_graph_replay_matches_batch(torch, tfn, ctx):
     compare(plan.normals[1].cpu().numpy(), plan.masks[1].cpu().numpy(), inputs[1].cpu().numpy(), cams[1],
             grad="sobel", phi="median")
     plan.close()
+
+
+@pytest.mark.parametrize("grad,phi", [("fd", "mean"), ("scharr", "median")])
+def test_tile_shapes_give_identical_bits(torch, tfn, grad, phi):
+    # every compiled tile shape (the autotuner's choices) computes the same bits
+    frames = depth_frames([(67, 131), (480, 640), (33, 64)], 1700)
+    inputs = [to_dev(torch, tfn, img) for img, _ in frames]
+    cams = [cam for _, cam in frames]
+    ref = None
+    with tfn.Context(0) as c:
+        for shape in range(tfn.tfn_tile_shape_count()):
+            c.set_tile_shape(shape)
+            n, m = c.normals_batch(inputs, cams, grad=grad, phi=phi)
+            torch.cuda.synchronize()
+            got = [x.cpu() for x in n] + [x.cpu() for x in m]
+            if ref is None:
+                ref = got
+                compare(n[1].cpu().numpy(), m[1].cpu().numpy(), frames[1][0], cams[1], grad=grad, phi=phi)
+            else:
+                assert all(torch.equal(a, b) for a, b in zip(got, ref)), f"tile shape {shape} differs"
+        assert c.device_status() == 0

@@ -334,7 +334,7 @@ def run_ours(args):
             "config": {"workload": f"{nf} x 480x640 FP32 depth, sigma=0.0012 Z^2 noise, 3% holes; "
                                    f"{args.grad} gradient, {args.phi}; FP32 planar normals + u8 mask out",
                        "global_batch": nf * world, "frame": "480x640", "gradient": args.grad, "phi": args.phi,
-                       "l2": "inputs (315 MB) and outputs (1.0 GB) exceed the 129 MB L2; no flush",
+                       "l2": f"inputs ({px * 4 / 1e6:.0f} MB) and outputs ({px * 13 / 1e6:.0f} MB) exceed the 129 MB L2; no flush",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,

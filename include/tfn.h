@@ -64,7 +64,8 @@ typedef enum tfn_status {
     TFN_ERR_TIMEOUT = 6,       /* a host-side wait ran out of time */
     TFN_ERR_CANCELLED = 7,     /* a request was cancelled before it ran */
     TFN_ERR_BUSY = 8,          /* admission refused: no slot or memory free right now */
-    TFN_ERR_DEVICE = 9         /* a kernel reported a failed bounded wait (tfn_device_status) */
+    TFN_ERR_DEVICE = 9,        /* a kernel reported a failed bounded wait (tfn_device_status) */
+    TFN_ERR_IO = 10            /* a file could not be opened, read or written */
 } tfn_status;
 
 /* Input sample types. */
@@ -169,9 +170,39 @@ int tfn_tile_shape_count(void);
  * (each thread computes 4 columns x rows_per_thread pixels). */
 tfn_status tfn_tile_shape_info(int index, int *tile_w, int *tile_h, int *rows_per_thread);
 
-/* Selects the tile shape used by later calls of this context (default 0).
- * Results do not depend on the shape; speed does (an autotuner picks it). */
+/* Forces the tile shape used by later calls of this context; index -1 (the
+ * default) uses the context's tune table (see tfn_autotune), and shape 0 for
+ * combinations the table does not hold.  Results do not depend on the shape;
+ * speed does.  Plans and batches built before the call keep their shape. */
 tfn_status tfn_set_tile_shape(tfn_ctx *ctx, int index);
+
+/* Autotuner.  Times every compiled tile shape on the caller's batch (`reps`
+ * timed runs of tfn_normals_batch each, after one untimed run; CUDA events on
+ * `stream`; the outputs are written as by tfn_normals_batch) and records the
+ * fastest in the context's tune table for each input type in the batch with
+ * the method's gradient, phi and output.  Returns the chosen index in *best
+ * and, if ms_per_shape is not NULL, the mean milliseconds per run of each
+ * shape in ms_per_shape[0 .. tfn_tile_shape_count()).  Synchronises `stream`.
+ * A forced shape (tfn_set_tile_shape >= 0) stays forced. */
+tfn_status tfn_autotune(tfn_ctx *ctx, const tfn_frame *frames, int n, const tfn_method *method, int reps,
+                        tfn_stream stream, int *best, float *ms_per_shape);
+
+/* The tune table's shape for (input_type, method's grad/phi/output), or -1
+ * in *index if the table holds none. */
+tfn_status tfn_tuned_shape(tfn_ctx *ctx, int input_type, const tfn_method *method, int *index);
+
+/* Writes the tune table to a text file: a version line, a line naming the
+ * device (name, SM count, compute capability), one line per entry with the
+ * tile geometry and the time measured.  TFN_ERR_IO if the file cannot be
+ * written. */
+tfn_status tfn_tune_cache_save(tfn_ctx *ctx, const char *path);
+
+/* Reads a file written by tfn_tune_cache_save into the tune table (entries
+ * replace existing ones; shapes this build does not compile are skipped).
+ * TFN_ERR_IO: cannot be read; TFN_ERR_INVALID_ARG: not a well-formed cache
+ * (nothing is loaded); TFN_ERR_UNSUPPORTED: tuned on another kind of device
+ * (nothing is loaded). */
+tfn_status tfn_tune_cache_load(tfn_ctx *ctx, const char *path);
 
 /* ---- plans: a frozen batch replayed as a CUDA graph ---------------------- */
 
@@ -208,6 +239,84 @@ tfn_status tfn_device_status(tfn_ctx *ctx, uint32_t *bits, tfn_stream stream);
  * accuracy notes of the kernel).  Diagnostics; counts wrap at 2^32.
  * Synchronises `stream`. */
 tfn_status tfn_refined_pixels(tfn_ctx *ctx, uint64_t *count, tfn_stream stream);
+
+/* ---- serving: a request server with continuous batching ------------------- */
+
+/* A thread-safe server that takes single frames from any number of client
+ * threads and runs them in batches: requests queue up while earlier batches
+ * run, and each time one of its pipelines frees up the server admits as many
+ * queued requests as fit -- in arrival order, at most max_batch_frames, with
+ * their device staging inside the memory budget -- and computes them with one
+ * persistent launch per input type (the tfn_normals_batch path).  A
+ * request's result does not depend on which other requests share its batch.
+ * (The paper has no serving layer; this is the library's.) */
+typedef struct tfn_server tfn_server;
+
+typedef struct tfn_server_opts {
+    tfn_method method;        /* gradient, phi, output layout and flags of every request */
+    size_t mem_budget_bytes;  /* device memory for staging host-buffer requests (0: 1 GiB); allocated once */
+    int32_t max_batch_frames; /* most requests per batch (0: 256) */
+    int32_t max_queue;        /* most requests waiting for admission (0: 65536) */
+    int32_t max_delay_us;     /* hold a partial batch up to this long after its oldest request
+                                 arrived while the device is busy (0: never hold) */
+    int32_t pipelines;        /* batches in flight at once, 1..4 (0: 2) */
+} tfn_server_opts;
+
+/* tfn_submit flag: the frame's pointers are HOST pointers (page-locked
+ * memory is fastest); the server copies the input into device staging memory
+ * and the results back.  Without it they are device pointers, used in place. */
+#define TFN_REQ_HOST 1
+
+typedef struct tfn_serving_stats {
+    uint64_t submitted, completed, failed, cancelled;
+    uint64_t rejected;           /* submissions refused with TFN_ERR_BUSY */
+    uint64_t batches;            /* batches launched */
+    uint64_t pixels;             /* pixels of completed requests */
+    double elapsed_s;            /* since creation or the last reset */
+    double frames_per_s;         /* completed / elapsed_s */
+    double mean_batch_frames;
+    double latency_p50_us;       /* submit -> results in the client's buffers, over the */
+    double latency_p99_us;       /* last latency_samples (at most 65536) completions */
+    double latency_max_us;
+    uint64_t latency_samples;
+    int32_t queued;              /* requests waiting for admission */
+    int32_t in_flight;           /* requests admitted and not yet complete */
+    size_t staging_bytes_in_use;
+    size_t staging_bytes_capacity;
+} tfn_serving_stats;
+
+/* Creates a server on ctx's device.  The server owns a context of its own
+ * (copying ctx's tune table and forced tile shape), two threads, its streams
+ * and the staging memory; ctx stays free for other use.  On failure *srv is
+ * NULL. */
+tfn_status tfn_server_create(tfn_ctx *ctx, const tfn_server_opts *opts, tfn_server **srv);
+
+/* Queues one frame; on success *ticket identifies it for tfn_wait.  The
+ * frame is validated here (as tfn_normals_batch does; host-buffer requests
+ * need no alignment).  TFN_ERR_BUSY: the queue is full (nothing queued);
+ * TFN_ERR_OUT_OF_MEMORY: the frame's staging is larger than the whole budget.
+ * The server runs on streams of its own: a device-buffer input must be
+ * complete (the work that produced it synchronised) before the call, and the
+ * caller's buffers must stay valid until the request completes. */
+tfn_status tfn_submit(tfn_server *srv, const tfn_frame *frame, int flags, uint64_t *ticket);
+
+/* Waits at most timeout_ms (>= 0; 0 polls) for the request.  TFN_OK: it
+ * finished and *result holds its status (TFN_OK: outputs written;
+ * TFN_ERR_CANCELLED: the server was destroyed before it was admitted;
+ * TFN_ERR_DEVICE: a kernel of its batch gave up a bounded wait, after which
+ * the server's later batches fail too; TFN_ERR_CUDA); the ticket is then
+ * released.  TFN_ERR_TIMEOUT: not finished yet (wait again).
+ * TFN_ERR_INVALID_ARG: unknown or already released ticket.  Never blocks
+ * longer than the limit. */
+tfn_status tfn_wait(tfn_server *srv, uint64_t ticket, int32_t timeout_ms, tfn_status *result);
+
+/* Counters and latency percentiles; reset != 0 restarts them after reading. */
+tfn_status tfn_server_stats(tfn_server *srv, tfn_serving_stats *stats, int reset);
+
+/* Stops admitting, cancels queued requests, waits for the batches in flight,
+ * joins the threads and frees everything.  No call on srv may be running or
+ * follow.  NULL is a no-op. */
+tfn_status tfn_server_destroy(tfn_server *srv);
 
 /* ---- without any allocation ------------------------------------------------- */
 

@@ -22,12 +22,13 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 # ---- enums (tfn.h) ------------------------------------------------------------------------
 TFN_OK, TFN_ERR_INVALID_ARG, TFN_ERR_UNSUPPORTED, TFN_ERR_MISALIGNED, TFN_ERR_OUT_OF_MEMORY, TFN_ERR_CUDA, \
-    TFN_ERR_TIMEOUT, TFN_ERR_CANCELLED, TFN_ERR_BUSY, TFN_ERR_DEVICE = range(10)
+    TFN_ERR_TIMEOUT, TFN_ERR_CANCELLED, TFN_ERR_BUSY, TFN_ERR_DEVICE, TFN_ERR_IO = range(11)
 TFN_DEPTH_F32, TFN_DEPTH_F16, TFN_DISP_U16, TFN_DISP_F32 = range(4)
 TFN_GRAD_FD, TFN_GRAD_SOBEL, TFN_GRAD_SCHARR, TFN_GRAD_PREWITT = range(4)
 TFN_PHI_MEAN, TFN_PHI_MEDIAN = range(2)
 TFN_OUT_F32, TFN_OUT_F16, TFN_OUT_BF16, TFN_OUT_F16X4, TFN_OUT_BF16X4 = range(5)
 TFN_FLAG_REFINE_ALL = 1
+TFN_REQ_HOST = 1
 
 GRADS = {"fd": TFN_GRAD_FD, "sobel": TFN_GRAD_SOBEL, "scharr": TFN_GRAD_SCHARR, "prewitt": TFN_GRAD_PREWITT}
 PHIS = {"mean": TFN_PHI_MEAN, "median": TFN_PHI_MEDIAN}
@@ -55,6 +56,21 @@ class tfn_method(ctypes.Structure):
                 ("flags", ctypes.c_int32)]
 
 
+class tfn_server_opts(ctypes.Structure):
+    _fields_ = [("method", tfn_method), ("mem_budget_bytes", ctypes.c_size_t), ("max_batch_frames", ctypes.c_int32),
+                ("max_queue", ctypes.c_int32), ("max_delay_us", ctypes.c_int32), ("pipelines", ctypes.c_int32)]
+
+
+class tfn_serving_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("cancelled", ctypes.c_uint64), ("rejected", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("pixels", ctypes.c_uint64), ("elapsed_s", ctypes.c_double), ("frames_per_s", ctypes.c_double),
+                ("mean_batch_frames", ctypes.c_double), ("latency_p50_us", ctypes.c_double),
+                ("latency_p99_us", ctypes.c_double), ("latency_max_us", ctypes.c_double),
+                ("latency_samples", ctypes.c_uint64), ("queued", ctypes.c_int32), ("in_flight", ctypes.c_int32),
+                ("staging_bytes_in_use", ctypes.c_size_t), ("staging_bytes_capacity", ctypes.c_size_t)]
+
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _lib.tfn_status_string.restype = ctypes.c_char_p
@@ -77,9 +93,20 @@ _lib.tfn_plan_launch.argtypes = [_P, _P]
 _lib.tfn_plan_destroy.argtypes = [_P]
 _lib.tfn_refined_pixels.argtypes = [_P, ctypes.POINTER(ctypes.c_uint64), _P]
 _lib.tfn_normals_noalloc.argtypes = [ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), _P]
+_lib.tfn_autotune.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), _I, _P,
+                              ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_float)]
+_lib.tfn_tuned_shape.argtypes = [_P, _I, ctypes.POINTER(tfn_method), ctypes.POINTER(_I)]
+_lib.tfn_tune_cache_save.argtypes = [_P, ctypes.c_char_p]
+_lib.tfn_tune_cache_load.argtypes = [_P, ctypes.c_char_p]
+_lib.tfn_server_create.argtypes = [_P, ctypes.POINTER(tfn_server_opts), ctypes.POINTER(_P)]
+_lib.tfn_submit.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(ctypes.c_uint64)]
+_lib.tfn_wait.argtypes = [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(_I)]
+_lib.tfn_server_stats.argtypes = [_P, ctypes.POINTER(tfn_serving_stats), _I]
+_lib.tfn_server_destroy.argtypes = [_P]
 for _f in ("tfn_create", "tfn_destroy", "tfn_normals", "tfn_normals_batch", "tfn_normals_batch_host",
            "tfn_device_status", "tfn_refined_pixels", "tfn_normals_noalloc", "tfn_plan_create", "tfn_plan_launch",
-           "tfn_plan_destroy"):
+           "tfn_plan_destroy", "tfn_autotune", "tfn_tuned_shape", "tfn_tune_cache_save", "tfn_tune_cache_load",
+           "tfn_server_create", "tfn_submit", "tfn_wait", "tfn_server_stats", "tfn_server_destroy"):
     getattr(_lib, _f).restype = _I
 
 # The C entry points under their own names.
@@ -99,6 +126,15 @@ tfn_set_tile_shape = _lib.tfn_set_tile_shape
 tfn_plan_create = _lib.tfn_plan_create
 tfn_plan_launch = _lib.tfn_plan_launch
 tfn_plan_destroy = _lib.tfn_plan_destroy
+tfn_autotune = _lib.tfn_autotune
+tfn_tuned_shape = _lib.tfn_tuned_shape
+tfn_tune_cache_save = _lib.tfn_tune_cache_save
+tfn_tune_cache_load = _lib.tfn_tune_cache_load
+tfn_server_create = _lib.tfn_server_create
+tfn_submit = _lib.tfn_submit
+tfn_wait = _lib.tfn_wait
+tfn_server_stats = _lib.tfn_server_stats
+tfn_server_destroy = _lib.tfn_server_destroy
 # For callers that may not allocate device memory (see include/tfn.h).
 tfn_normals_noalloc = _lib.tfn_normals_noalloc
 TFN_NOALLOC_MAX_FRAMES = 64
@@ -106,7 +142,9 @@ TFN_NOALLOC_MAX_FRAMES = 64
 EXPORTED = ["tfn_status_string", "tfn_version", "tfn_last_cuda_error", "tfn_create", "tfn_destroy", "tfn_normals",
             "tfn_normals_batch", "tfn_normals_batch_host", "tfn_device_status", "tfn_refined_pixels",
             "tfn_normals_noalloc", "tfn_plan_create", "tfn_plan_launch", "tfn_plan_destroy", "tfn_tile_shape_count",
-            "tfn_tile_shape_info", "tfn_set_tile_shape"]
+            "tfn_tile_shape_info", "tfn_set_tile_shape", "tfn_autotune", "tfn_tuned_shape", "tfn_tune_cache_save",
+            "tfn_tune_cache_load", "tfn_server_create", "tfn_submit", "tfn_wait", "tfn_server_stats",
+            "tfn_server_destroy"]
 
 
 class TfnError(RuntimeError):
@@ -299,7 +337,40 @@ class Context:
         return Plan(h, inputs, normals, masks)
 
     def set_tile_shape(self, index: int):
+        """Force tile shape `index`; -1 returns to the tune table."""
         check(tfn_set_tile_shape(self.handle, index), "tfn_set_tile_shape")
+
+    def autotune(self, inputs, cams, *, grad="fd", phi="mean", output="f32", disparity=False, disp_scale=1.0 / 16,
+                 normals=None, masks=None, reps=10, stream=None):
+        """Times every tile shape on this batch; returns (best index, [ms per run of each shape])."""
+        n = len(inputs)
+        if isinstance(cams, dict):
+            cams = [cams] * n
+        if normals is None:
+            normals = [empty_normals(x.shape[0], x.shape[1], output, x.device) for x in inputs]
+        if masks is None:
+            masks = [empty_image(tuple(x.shape), _torch().uint8, x.device) for x in inputs]
+        frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output)
+                                   for k in range(n)])
+        m = make_method(grad, phi, output)
+        best = ctypes.c_int()
+        ms = (ctypes.c_float * tfn_tile_shape_count())()
+        check(tfn_autotune(self.handle, frames, n, ctypes.byref(m), reps, _stream_handle(stream), ctypes.byref(best),
+                           ms), "tfn_autotune")
+        return best.value, list(ms)
+
+    def tuned_shape(self, input_type: int, *, grad="fd", phi="mean", output="f32") -> int:
+        """The tune table's shape for this combination, or -1."""
+        m = make_method(grad, phi, output)
+        idx = ctypes.c_int()
+        check(tfn_tuned_shape(self.handle, input_type, ctypes.byref(m), ctypes.byref(idx)), "tfn_tuned_shape")
+        return idx.value
+
+    def save_tune_cache(self, path: str):
+        check(tfn_tune_cache_save(self.handle, os.fsencode(path)), "tfn_tune_cache_save")
+
+    def load_tune_cache(self, path: str):
+        check(tfn_tune_cache_load(self.handle, os.fsencode(path)), "tfn_tune_cache_load")
 
     def refined_pixels(self, stream=None) -> int:
         """Pixels sent to the double-float path since the last call (diagnostics)."""
@@ -344,3 +415,60 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """A libtfn request server (continuous batching); see tfn_server_create in include/tfn.h.
+
+    submit() takes torch tensors on the device, or in host memory with host=True; the tensors are kept
+    alive until wait() returns for their ticket."""
+
+    def __init__(self, ctx: Context, *, grad="fd", phi="mean", output="f32", flags=0, mem_budget=0,
+                 max_batch=0, max_queue=0, max_delay_us=0, pipelines=0):
+        o = tfn_server_opts()
+        o.method = make_method(grad, phi, output, flags)
+        o.mem_budget_bytes = mem_budget
+        o.max_batch_frames, o.max_queue, o.max_delay_us, o.pipelines = max_batch, max_queue, max_delay_us, pipelines
+        h = ctypes.c_void_p()
+        check(tfn_server_create(ctx.handle, ctypes.byref(o), ctypes.byref(h)), "tfn_server_create")
+        self.handle = h
+        self.output = output
+        self._keep = {}
+
+    def submit(self, inp, cam, normals, mask, *, host=False, disparity=False, disp_scale=1.0 / 16) -> int:
+        """Queues one frame; returns its ticket (raises TfnError, e.g. TFN_ERR_BUSY)."""
+        f = make_frame(inp, normals, mask, cam, disparity, disp_scale, self.output)
+        t = ctypes.c_uint64()
+        check(tfn_submit(self.handle, ctypes.byref(f), TFN_REQ_HOST if host else 0, ctypes.byref(t)), "tfn_submit")
+        self._keep[t.value] = (inp, normals, mask)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 10000) -> int:
+        """The request's status once done; raises TfnError(TFN_ERR_TIMEOUT) if not done in time."""
+        r = ctypes.c_int()
+        check(tfn_wait(self.handle, ticket, timeout_ms, ctypes.byref(r)), "tfn_wait")
+        self._keep.pop(ticket, None)
+        return r.value
+
+    def stats(self, reset=False) -> dict:
+        st = tfn_serving_stats()
+        check(tfn_server_stats(self.handle, ctypes.byref(st), 1 if reset else 0), "tfn_server_stats")
+        return {k: getattr(st, k) for k, _ in tfn_serving_stats._fields_}
+
+    def close(self):
+        if self.handle:
+            tfn_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/tfn.h"
+#include "tfn_ctx.h"
 #include "tfn_internal.h"
 
 namespace tfn {
@@ -72,65 +73,10 @@ bool load_encode()
     return g_encode != nullptr;
 }
 
-constexpr int kSlots = 4;
-
-// One scratch slot: descriptors + tensor maps for one launch.
-struct Slot {
-    void *dev = nullptr;   // FrameDesc[cap] then CUtensorMap[cap]
-    void *host = nullptr;  // pinned mirror
-    int cap = 0;
-    size_t bytes = 0;
-    cudaEvent_t done = nullptr;  // recorded after the launch that used it
-    std::vector<unsigned char> key;
-    bool has_key = false;
-};
-
-// Staging of the host-buffer path: one set per pipeline stream.
-struct Stage {
-    cudaStream_t stream = nullptr;
-    void *in = nullptr, *out = nullptr, *mask = nullptr;
-    size_t in_bytes = 0, out_bytes = 0, mask_bytes = 0;
-};
-
 }  // namespace
 
-struct tfn_ctx {
-    int device = 0;
-    int num_sms = 0;
-    size_t budget = 0, used = 0;
-    uint32_t *status = nullptr;
-    uint32_t *status_host = nullptr;
-    Slot slots[kSlots];
-    int next_slot = 0, last_slot = -1;
-    int cfg = 0;
-    Stage stages[3];
-    std::vector<tfn_frame> chunk_frames;
-};
 
-struct tfn_plan {
-    tfn_ctx *ctx = nullptr;
-    void *dev = nullptr;  // FrameDesc[n] then CUtensorMap[n]
-    size_t bytes = 0;
-    int n = 0;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-};
-
-namespace {
-
-struct DeviceGuard {  // switches to the context's device for the call's duration
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) ok = cuda_ok(cudaSetDevice(dev), "cudaSetDevice");
-    }
-    ~DeviceGuard()
-    {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
+namespace tfn {
 
 tfn_status ctx_alloc(tfn_ctx *c, void **p, size_t bytes)
 {
@@ -154,9 +100,6 @@ void ctx_free(tfn_ctx *c, void *&p, size_t bytes)
     }
 }
 
-}  // namespace
-
-namespace tfn {
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 bool mult16(int64_t x) { return (x & 15) == 0; }
@@ -373,7 +316,7 @@ CUtensorMap *slot_maps(void *base, int cap)
 tfn_status launch_group(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method &m, cudaStream_t stream)
 {
     const int kind = frames[0].input_type;
-    const int cfg = c->cfg;
+    const int cfg = pick_cfg(c, kind, m);
     std::vector<unsigned char> key;
     key.reserve(16 + (size_t)n * 96);
     append_key(key, &m, sizeof m);
@@ -419,6 +362,10 @@ tfn_status launch_group(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_me
     return TFN_OK;
 }
 
+}  // namespace
+
+namespace tfn {
+
 tfn_status run_batch(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method &m, cudaStream_t stream)
 {
     // frames of one input kind go to one launch; keep the caller's order
@@ -433,7 +380,7 @@ tfn_status run_batch(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_metho
     return TFN_OK;
 }
 
-}  // namespace
+}  // namespace tfn
 
 extern "C" {
 
@@ -450,6 +397,7 @@ const char *tfn_status_string(tfn_status s)
     case TFN_ERR_CANCELLED: return "cancelled";
     case TFN_ERR_BUSY: return "busy";
     case TFN_ERR_DEVICE: return "a kernel reported a failed bounded wait";
+    case TFN_ERR_IO: return "file could not be opened, read or written";
     }
     return "unknown status";
 }
@@ -658,13 +606,13 @@ tfn_status tfn_plan_create(tfn_ctx *c, const tfn_frame *frames, int n, const tfn
         delete p;
         return st;
     }
-    const int cfg = c->cfg;
     std::vector<unsigned char> host(p->bytes + 128);
     void *hbase = (void *)(((uintptr_t)host.data() + 127) & ~(uintptr_t)127);
     FrameDesc *d = slot_descs(hbase);
     CUtensorMap *maps = slot_maps(hbase, n);
     for (int i = 0, tb = 0; i < n; ++i) {
         if (i > 0 && frames[i].input_type != frames[i - 1].input_type) tb = 0;
+        const int cfg = pick_cfg(c, frames[i].input_type, *m);
         d[i] = describe_frame(frames[i], cfg, m->phi, tb);
         tb += frame_tiles(frames[i], cfg);
         if ((st = encode_map(&maps[i], frames[i], cfg))) break;
@@ -680,6 +628,7 @@ tfn_status tfn_plan_create(tfn_ctx *c, const tfn_frame *frames, int n, const tfn
         for (int i = 0; i < n && lst == TFN_OK;) {
             int j = i + 1;
             while (j < n && frames[j].input_type == frames[i].input_type) ++j;
+            const int cfg = pick_cfg(c, frames[i].input_type, *m);
             int total = 0;
             for (int k = i; k < j; ++k) total += frame_tiles(frames[k], cfg);
             lst = launch_normals(frames[i].input_type, *m, cfg, slot_descs(p->dev) + i, slot_maps(p->dev, n) + i,
@@ -738,8 +687,8 @@ tfn_status tfn_tile_shape_info(int index, int *tile_w, int *tile_h, int *rows_pe
 
 tfn_status tfn_set_tile_shape(tfn_ctx *c, int index)
 {
-    if (!c || index < 0 || index >= kNumCfg) return TFN_ERR_INVALID_ARG;
-    c->cfg = index;
+    if (!c || index < -1 || index >= kNumCfg) return TFN_ERR_INVALID_ARG;
+    c->forced_cfg = index;
     c->last_slot = -1;  // descriptors depend on the tile shape
     return TFN_OK;
 }

@@ -1,0 +1,106 @@
+// tfn_ctx.h -- the context and plan objects behind the opaque handles of the
+// C ABI, shared by the host-side translation units (tfn_api.cu, tfn_tune.cu,
+// tfn_server.cu).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "tfn_internal.h"
+
+namespace tfn {
+
+constexpr int kSlots = 4;
+constexpr int kOutCount = OUT_BF16X4 + 1;
+
+// One scratch slot: descriptors + tensor maps for one launch.
+struct Slot {
+    void *dev = nullptr;   // FrameDesc[cap] then CUtensorMap[cap]
+    void *host = nullptr;  // pinned mirror
+    int cap = 0;
+    size_t bytes = 0;
+    cudaEvent_t done = nullptr;  // recorded after the launch that used it
+    std::vector<unsigned char> key;
+    bool has_key = false;
+};
+
+// Staging of the host-buffer path: one set per pipeline stream.
+struct Stage {
+    cudaStream_t stream = nullptr;
+    void *in = nullptr, *out = nullptr, *mask = nullptr;
+    size_t in_bytes = 0, out_bytes = 0, mask_bytes = 0;
+};
+
+}  // namespace tfn
+
+struct tfn_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t budget = 0, used = 0;
+    uint32_t *status = nullptr;
+    uint32_t *status_host = nullptr;
+    tfn::Slot slots[tfn::kSlots];
+    int next_slot = 0, last_slot = -1;
+    // tile shape: forced >= 0 (tfn_set_tile_shape), else the tune table's
+    // entry for (input kind, gradient, phi, output), else shape 0
+    int forced_cfg = -1;
+    signed char tuned[tfn::KIND_COUNT][tfn::GRAD_COUNT][tfn::PHI_COUNT][tfn::kOutCount];
+    float tuned_ms[tfn::KIND_COUNT][tfn::GRAD_COUNT][tfn::PHI_COUNT][tfn::kOutCount];
+    tfn::Stage stages[3];
+    tfn_ctx()
+    {
+        for (auto &a : tuned)
+            for (auto &b : a)
+                for (auto &c : b)
+                    for (auto &d : c) d = -1;
+        for (auto &a : tuned_ms)
+            for (auto &b : a)
+                for (auto &c : b)
+                    for (auto &d : c) d = 0.f;
+    }
+};
+
+struct tfn_plan {
+    tfn_ctx *ctx = nullptr;
+    void *dev = nullptr;  // FrameDesc[n] then CUtensorMap[n]
+    size_t bytes = 0;
+    int n = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace tfn {
+
+struct DeviceGuard {  // switches to the context's device for the call's duration
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cuda_ok(cudaSetDevice(dev), "cudaSetDevice");
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Device allocations counted against the context's budget.
+tfn_status ctx_alloc(tfn_ctx *c, void **p, size_t bytes);
+void ctx_free(tfn_ctx *c, void *&p, size_t bytes);
+
+// Tile shape for a launch of frames of input kind `kind` with method `m`.
+inline int pick_cfg(const tfn_ctx *c, int kind, const tfn_method &m)
+{
+    if (c->forced_cfg >= 0) return c->forced_cfg;
+    const int t = c->tuned[kind][m.grad][m.phi][m.output];
+    return t >= 0 ? t : 0;
+}
+
+// Enqueues the estimator over frames[0..n) (device pointers, already
+// validated) on `stream`: one persistent launch per run of frames of one
+// input kind.
+tfn_status run_batch(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method &m, cudaStream_t stream);
+
+}  // namespace tfn

@@ -1,0 +1,533 @@
+// tfn_server.cu -- the serving form: a thread-safe request server with
+// continuous batching and memory-budget admission.
+//
+// Clients submit single frames (any size, input type and intrinsics; one
+// method per server) from any thread and get a ticket; tfn_wait blocks, with a
+// limit, until that frame's normals are in the client's buffers.  Inside, two
+// threads run the pipeline:
+//
+//   launcher: waits until requests are queued and a pipeline is free, admits
+//             requests from the front of the queue while the batch stays within
+//             max_batch_frames and its staging bytes fit in one block of the
+//             ring arena (host-buffer requests are staged through device
+//             memory; device-buffer requests need none), then enqueues on that
+//             pipeline's stream: host-to-device copies, one persistent kernel
+//             launch per input type over the whole batch (the same launch path
+//             as tfn_normals_batch), device-to-host copies, an event;
+//   retirer:  waits for the oldest batch in flight, checks the kernels' status
+//             word, completes the batch's requests (status, latency), releases
+//             its arena block and wakes the waiters and the launcher.
+//
+// Requests that arrive while batches are in flight queue up and form the next
+// batch as soon as a pipeline frees up (continuous batching); with
+// max_delay_us > 0 the launcher also holds a partial batch for up to that long
+// while the device is busy.  Every pixel's result is independent of which
+// other frames share its launch, so a request gets the same bits alone and in
+// any mix.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/tfn.h"
+#include "tfn_ctx.h"
+#include "tfn_internal.h"
+#include "tfn_sched.h"
+
+using namespace tfn;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+constexpr int kMaxPipes = 4;
+constexpr size_t kLatencyWindow = 65536;
+
+size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int out_bytes_per_elem(int fmt) { return fmt == OUT_F32 ? 4 : (fmt == OUT_F16 || fmt == OUT_BF16) ? 2 : 8; }
+
+// Device staging layout of one host-buffer request: input, normals, mask.
+struct StageLayout {
+    size_t in_pitch, out_pitch, mask_pitch;
+    size_t in_off, out_off, mask_off, bytes;
+    int planes;
+};
+
+StageLayout stage_layout(const tfn_frame &f, int fmt)
+{
+    StageLayout L;
+    const int ob = out_bytes_per_elem(fmt);
+    L.planes = fmt <= OUT_BF16 ? 3 : 1;
+    L.in_pitch = al16((size_t)f.width * kind_elem_size(f.input_type));
+    L.out_pitch = al16((size_t)f.width * ob);
+    L.mask_pitch = al16((size_t)f.width);
+    L.in_off = 0;
+    L.out_off = al256(L.in_pitch * f.height);
+    L.mask_off = L.out_off + al256(L.out_pitch * f.height * L.planes);
+    L.bytes = L.mask_off + al256(L.mask_pitch * f.height);
+    return L;
+}
+
+struct Request {
+    uint64_t ticket;
+    tfn_frame frame;  // as submitted
+    bool host;
+    size_t stage_bytes;  // 0 for device-buffer requests
+    Clock::time_point t_submit;
+};
+
+struct Result {
+    bool done = false;
+    tfn_status status = TFN_OK;
+};
+
+struct Batch {
+    int pipe;
+    bool has_block;
+    std::vector<Request> reqs;
+    tfn_status launch_status = TFN_OK;  // failure while enqueueing
+};
+
+struct Pipe {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    uint32_t *status_host = nullptr;  // pinned copy of the kernels' status word
+    bool busy = false;
+};
+
+}  // namespace
+
+struct tfn_server {
+    tfn_ctx *ctx = nullptr;  // the server's own context (the launcher thread uses it alone)
+    tfn_method method;
+    size_t max_batch = 256, max_queue = 65536;
+    int max_delay_us = 0;
+    int npipes = 2;
+    Pipe pipes[kMaxPipes];
+    void *arena_base = nullptr;
+    size_t arena_bytes = 0;
+    RingArena arena;
+
+    std::mutex mu;
+    std::condition_variable cv_launch;  // launcher: queue or resources changed
+    std::condition_variable cv_retire;  // retirer: a batch was launched
+    std::condition_variable cv_done;    // waiters: a request completed
+    std::deque<Request> queue;
+    std::deque<Batch> inflight;
+    std::unordered_map<uint64_t, Result> results;
+    uint64_t next_ticket = 1;
+    bool stopping = false, launcher_done = false;
+    std::thread launcher, retirer;
+
+    // statistics (under mu)
+    uint64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, rejected = 0, batches = 0, batch_frames = 0;
+    uint64_t pixels = 0;
+    Clock::time_point t0;
+    std::vector<float> lat_us;  // ring of the last kLatencyWindow latencies
+    size_t lat_next = 0;
+    int inflight_reqs = 0;
+};
+
+namespace {
+
+void complete_locked(tfn_server *s, const Request &r, tfn_status st, Clock::time_point now)
+{
+    auto it = s->results.find(r.ticket);
+    if (it != s->results.end()) {
+        it->second.done = true;
+        it->second.status = st;
+    }
+    if (st == TFN_OK) {
+        ++s->completed;
+        s->pixels += (uint64_t)r.frame.height * r.frame.width;
+        const float us = std::chrono::duration<float, std::micro>(now - r.t_submit).count();
+        if (s->lat_us.size() < kLatencyWindow)
+            s->lat_us.push_back(us);
+        else
+            s->lat_us[s->lat_next] = us;
+        s->lat_next = (s->lat_next + 1) % kLatencyWindow;
+    } else if (st == TFN_ERR_CANCELLED) {
+        ++s->cancelled;
+    } else {
+        ++s->failed;
+    }
+}
+
+// Enqueues one batch on its pipeline's stream (launcher thread, no lock held).
+tfn_status enqueue_batch(tfn_server *s, Batch &b, size_t block_off)
+{
+    Pipe &p = s->pipes[b.pipe];
+    const int fmt = s->method.output;
+    const int ob = out_bytes_per_elem(fmt);
+    std::vector<tfn_frame> dev(b.reqs.size());
+    size_t off = block_off;
+    for (size_t i = 0; i < b.reqs.size(); ++i) {
+        const Request &r = b.reqs[i];
+        if (!r.host) {
+            dev[i] = r.frame;
+            continue;
+        }
+        const tfn_frame &f = r.frame;
+        const StageLayout L = stage_layout(f, fmt);
+        char *base = (char *)s->arena_base + off;
+        off += r.stage_bytes;
+        tfn_frame d = f;
+        d.input = base + L.in_off;
+        d.input_pitch = (int64_t)L.in_pitch;
+        d.normals = base + L.out_off;
+        d.normals_pitch = (int64_t)L.out_pitch;
+        d.normals_plane_stride = (int64_t)(L.out_pitch * f.height);
+        d.mask = (uint8_t *)(base + L.mask_off);
+        d.mask_pitch = (int64_t)L.mask_pitch;
+        dev[i] = d;
+        if (!cuda_ok(cudaMemcpy2DAsync((void *)d.input, L.in_pitch, f.input, (size_t)f.input_pitch,
+                                       (size_t)f.width * kind_elem_size(f.input_type), f.height, cudaMemcpyHostToDevice,
+                                       p.stream),
+                     "cudaMemcpy2DAsync(H2D)"))
+            return TFN_ERR_CUDA;
+    }
+    tfn_status st = run_batch(s->ctx, dev.data(), (int)dev.size(), s->method, p.stream);
+    if (st) return st;
+    for (size_t i = 0; i < b.reqs.size(); ++i) {
+        const Request &r = b.reqs[i];
+        if (!r.host) continue;
+        const tfn_frame &f = r.frame, &d = dev[i];
+        const int planes = fmt <= OUT_BF16 ? 3 : 1;
+        for (int q = 0; q < planes; ++q)
+            if (!cuda_ok(cudaMemcpy2DAsync((char *)f.normals + q * f.normals_plane_stride, (size_t)f.normals_pitch,
+                                           (const char *)d.normals + q * d.normals_plane_stride,
+                                           (size_t)d.normals_pitch, (size_t)f.width * ob, f.height,
+                                           cudaMemcpyDeviceToHost, p.stream),
+                         "cudaMemcpy2DAsync(D2H)"))
+                return TFN_ERR_CUDA;
+        if (!cuda_ok(cudaMemcpy2DAsync(f.mask, (size_t)f.mask_pitch, d.mask, (size_t)d.mask_pitch, f.width, f.height,
+                                       cudaMemcpyDeviceToHost, p.stream),
+                     "cudaMemcpy2DAsync(D2H)"))
+            return TFN_ERR_CUDA;
+    }
+    if (!cuda_ok(cudaMemcpyAsync(p.status_host, s->ctx->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, p.stream),
+                 "cudaMemcpyAsync(status)") ||
+        !cuda_ok(cudaEventRecord(p.done, p.stream), "cudaEventRecord"))
+        return TFN_ERR_CUDA;
+    return TFN_OK;
+}
+
+void launcher_main(tfn_server *s)
+{
+    DeviceGuard g(s->ctx->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        int pipe = -1;
+        for (;;) {
+            if (s->stopping) break;
+            pipe = -1;
+            for (int k = 0; k < s->npipes; ++k)
+                if (!s->pipes[k].busy) {
+                    pipe = k;
+                    break;
+                }
+            if (pipe >= 0 && !s->queue.empty()) {
+                // optional batching delay: hold a partial batch while the device is busy
+                bool any_busy = false;
+                for (int k = 0; k < s->npipes; ++k) any_busy |= s->pipes[k].busy;
+                if (s->max_delay_us > 0 && any_busy && s->queue.size() < s->max_batch) {
+                    const auto deadline = s->queue.front().t_submit + std::chrono::microseconds(s->max_delay_us);
+                    if (Clock::now() < deadline) {
+                        s->cv_launch.wait_until(lk, deadline);
+                        continue;
+                    }
+                }
+                size_t bytes = 0;
+                const size_t k = admit_count(s->queue, s->max_batch, s->arena.largest_fit(),
+                                             [](const Request &r) { return r.stage_bytes; }, &bytes);
+                if (k > 0) break;
+            }
+            s->cv_launch.wait(lk);
+        }
+        if (s->stopping) break;
+        // admit
+        size_t bytes = 0;
+        const size_t k = admit_count(s->queue, s->max_batch, s->arena.largest_fit(),
+                                     [](const Request &r) { return r.stage_bytes; }, &bytes);
+        Batch b;
+        b.pipe = pipe;
+        b.reqs.assign(s->queue.begin(), s->queue.begin() + k);
+        s->queue.erase(s->queue.begin(), s->queue.begin() + k);
+        size_t off = 0;
+        b.has_block = bytes > 0;
+        if (b.has_block) off = s->arena.alloc(bytes);  // fits: admit_count checked largest_fit
+        s->pipes[pipe].busy = true;
+        s->inflight_reqs += (int)k;
+        ++s->batches;
+        s->batch_frames += k;
+        lk.unlock();
+        b.launch_status = enqueue_batch(s, b, off);
+        if (b.launch_status != TFN_OK) {
+            // let the stream drain what was enqueued before the failure, so the
+            // retirer can release the block safely
+            cudaEventRecord(s->pipes[pipe].done, s->pipes[pipe].stream);
+        }
+        lk.lock();
+        s->inflight.push_back(std::move(b));
+        s->cv_retire.notify_one();
+    }
+    // cancel what was never admitted
+    const auto now = Clock::now();
+    for (const Request &r : s->queue) complete_locked(s, r, TFN_ERR_CANCELLED, now);
+    s->queue.clear();
+    s->launcher_done = true;
+    s->cv_retire.notify_one();
+    s->cv_done.notify_all();
+}
+
+void retirer_main(tfn_server *s)
+{
+    DeviceGuard g(s->ctx->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        s->cv_retire.wait(lk, [s] { return !s->inflight.empty() || s->launcher_done; });
+        if (s->inflight.empty()) break;  // launcher finished and nothing in flight
+        const int pipe = s->inflight.front().pipe;
+        Pipe &p = s->pipes[pipe];
+        lk.unlock();
+        tfn_status st = cuda_ok(cudaEventSynchronize(p.done), "cudaEventSynchronize") ? TFN_OK : TFN_ERR_CUDA;
+        const auto now = Clock::now();
+        lk.lock();
+        Batch b = std::move(s->inflight.front());
+        s->inflight.pop_front();
+        if (st == TFN_OK) st = b.launch_status;
+        if (st == TFN_OK && *p.status_host != 0) st = TFN_ERR_DEVICE;  // a kernel gave up a bounded wait
+        for (const Request &r : b.reqs) complete_locked(s, r, st, now);
+        if (b.has_block) s->arena.free_oldest();
+        p.busy = false;
+        s->inflight_reqs -= (int)b.reqs.size();
+        s->cv_done.notify_all();
+        s->cv_launch.notify_one();
+    }
+}
+
+void destroy_resources(tfn_server *s)
+{
+    for (Pipe &p : s->pipes) {
+        if (p.stream) {
+            cudaStreamSynchronize(p.stream);
+            cudaStreamDestroy(p.stream);
+        }
+        if (p.done) cudaEventDestroy(p.done);
+        if (p.status_host) cudaFreeHost(p.status_host);
+    }
+    if (s->arena_base) cudaFree(s->arena_base);
+    if (s->ctx) tfn_destroy(s->ctx);
+}
+
+// Geometry, type and intrinsics of a host-buffer request, checked on a
+// stand-in frame with the staging pointers and pitches it would get.
+tfn_status validate_host_request(const tfn_frame &f, int fmt)
+{
+    if (!f.input || !f.normals || !f.mask) return TFN_ERR_INVALID_ARG;
+    if (f.height < 1 || f.width < 1 || f.height > 32768 || f.width > 32768 || f.input_type < 0 ||
+        f.input_type >= KIND_COUNT)
+        return TFN_ERR_INVALID_ARG;
+    const int ob = out_bytes_per_elem(fmt);
+    if (f.input_pitch < (int64_t)f.width * kind_elem_size(f.input_type) || f.normals_pitch < (int64_t)f.width * ob ||
+        f.mask_pitch < f.width)
+        return TFN_ERR_INVALID_ARG;
+    if (fmt <= OUT_BF16 && f.normals_plane_stride < f.normals_pitch * (int64_t)f.height) return TFN_ERR_INVALID_ARG;
+    const StageLayout L = stage_layout(f, fmt);
+    tfn_frame d = f;
+    d.input = (const void *)(uintptr_t)256;
+    d.input_pitch = (int64_t)L.in_pitch;
+    d.normals = (void *)(uintptr_t)256;
+    d.normals_pitch = (int64_t)L.out_pitch;
+    d.normals_plane_stride = (int64_t)(L.out_pitch * f.height);
+    d.mask = (uint8_t *)(uintptr_t)256;
+    d.mask_pitch = (int64_t)L.mask_pitch;
+    return validate_frame(&d, fmt);
+}
+
+}  // namespace
+
+extern "C" {
+
+tfn_status tfn_server_create(tfn_ctx *ctx, const tfn_server_opts *o, tfn_server **out)
+{
+    if (!out) return TFN_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!ctx || !o) return TFN_ERR_INVALID_ARG;
+    tfn_status st = validate_method(&o->method);
+    if (st) return st;
+    if (o->max_batch_frames < 0 || o->max_queue < 0 || o->max_delay_us < 0 || o->pipelines < 0 ||
+        o->pipelines > kMaxPipes)
+        return TFN_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return TFN_ERR_CUDA;
+    tfn_server *s = new (std::nothrow) tfn_server();
+    if (!s) return TFN_ERR_OUT_OF_MEMORY;
+    s->method = o->method;
+    s->max_batch = o->max_batch_frames ? (size_t)o->max_batch_frames : 256;
+    s->max_queue = o->max_queue ? (size_t)o->max_queue : 65536;
+    s->max_delay_us = o->max_delay_us;
+    s->npipes = o->pipelines ? o->pipelines : 2;
+    s->arena_bytes = o->mem_budget_bytes ? o->mem_budget_bytes : ((size_t)1 << 30);
+    if ((st = tfn_create(&s->ctx, ctx->device, 0))) {
+        delete s;
+        return st;
+    }
+    // the server inherits the caller's tune table and forced shape
+    memcpy(s->ctx->tuned, ctx->tuned, sizeof ctx->tuned);
+    memcpy(s->ctx->tuned_ms, ctx->tuned_ms, sizeof ctx->tuned_ms);
+    s->ctx->forced_cfg = ctx->forced_cfg;
+    cudaError_t e = cudaMalloc(&s->arena_base, s->arena_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        s->arena_base = nullptr;
+        destroy_resources(s);
+        delete s;
+        return e == cudaErrorMemoryAllocation ? TFN_ERR_OUT_OF_MEMORY : TFN_ERR_CUDA;
+    }
+    s->arena = RingArena(s->arena_bytes, 256);
+    for (int k = 0; k < s->npipes; ++k) {
+        Pipe &p = s->pipes[k];
+        if (!cuda_ok(cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking), "cudaStreamCreate") ||
+            !cuda_ok(cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming), "cudaEventCreate") ||
+            !cuda_ok(cudaMallocHost((void **)&p.status_host, sizeof(uint32_t)), "cudaMallocHost")) {
+            destroy_resources(s);
+            delete s;
+            return TFN_ERR_CUDA;
+        }
+        *p.status_host = 0;
+    }
+    s->t0 = Clock::now();
+    s->lat_us.reserve(kLatencyWindow);
+    try {
+        s->launcher = std::thread(launcher_main, s);
+        s->retirer = std::thread(retirer_main, s);
+    } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->stopping = true;
+        }
+        s->cv_launch.notify_all();
+        if (s->launcher.joinable()) s->launcher.join();
+        if (s->retirer.joinable()) s->retirer.join();
+        destroy_resources(s);
+        delete s;
+        return TFN_ERR_OUT_OF_MEMORY;
+    }
+    *out = s;
+    return TFN_OK;
+}
+
+tfn_status tfn_submit(tfn_server *s, const tfn_frame *frame, int flags, uint64_t *ticket)
+{
+    if (!s || !frame || !ticket || (flags & ~TFN_REQ_HOST)) return TFN_ERR_INVALID_ARG;
+    const bool host = flags & TFN_REQ_HOST;
+    tfn_status st = host ? validate_host_request(*frame, s->method.output) : validate_frame(frame, s->method.output);
+    if (st) return st;
+    Request r;
+    r.frame = *frame;
+    r.host = host;
+    r.stage_bytes = host ? s->arena.round(stage_layout(*frame, s->method.output).bytes) : 0;
+    if (r.stage_bytes > s->arena.capacity()) return TFN_ERR_OUT_OF_MEMORY;  // could never be admitted
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stopping) return TFN_ERR_CANCELLED;
+    if (s->queue.size() >= s->max_queue) {
+        ++s->rejected;
+        return TFN_ERR_BUSY;
+    }
+    r.ticket = s->next_ticket++;
+    r.t_submit = Clock::now();
+    s->results.emplace(r.ticket, Result());
+    s->queue.push_back(r);
+    ++s->submitted;
+    *ticket = r.ticket;
+    s->cv_launch.notify_one();
+    return TFN_OK;
+}
+
+tfn_status tfn_wait(tfn_server *s, uint64_t ticket, int32_t timeout_ms, tfn_status *result)
+{
+    if (!s || !result || timeout_ms < 0) return TFN_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->results.find(ticket);
+    if (it == s->results.end()) return TFN_ERR_INVALID_ARG;  // unknown, or already waited for
+    const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms);
+    while (!it->second.done) {
+        if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !it->second.done)
+            return TFN_ERR_TIMEOUT;
+        it = s->results.find(ticket);
+        if (it == s->results.end()) return TFN_ERR_INVALID_ARG;  // consumed by a concurrent waiter
+    }
+    *result = it->second.status;
+    s->results.erase(it);
+    return TFN_OK;
+}
+
+tfn_status tfn_server_stats(tfn_server *s, tfn_serving_stats *o, int reset)
+{
+    if (!s || !o) return TFN_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    memset(o, 0, sizeof *o);
+    o->submitted = s->submitted;
+    o->completed = s->completed;
+    o->failed = s->failed;
+    o->cancelled = s->cancelled;
+    o->rejected = s->rejected;
+    o->batches = s->batches;
+    o->pixels = s->pixels;
+    const auto now = Clock::now();
+    o->elapsed_s = std::chrono::duration<double>(now - s->t0).count();
+    o->frames_per_s = o->elapsed_s > 0 ? (double)s->completed / o->elapsed_s : 0.0;
+    o->mean_batch_frames = s->batches ? (double)s->batch_frames / (double)s->batches : 0.0;
+    if (!s->lat_us.empty()) {
+        std::vector<float> v(s->lat_us);
+        auto at = [&v](double q) {
+            const size_t i = std::min(v.size() - 1, (size_t)(q * (double)(v.size() - 1) + 0.5));
+            std::nth_element(v.begin(), v.begin() + i, v.end());
+            return (double)v[i];
+        };
+        o->latency_p50_us = at(0.50);
+        o->latency_p99_us = at(0.99);
+        o->latency_max_us = *std::max_element(v.begin(), v.end());
+        o->latency_samples = v.size();
+    }
+    o->queued = (int32_t)s->queue.size();
+    o->in_flight = s->inflight_reqs;
+    o->staging_bytes_in_use = s->arena.in_use();
+    o->staging_bytes_capacity = s->arena.capacity();
+    if (reset) {
+        s->submitted = s->completed = s->failed = s->cancelled = s->rejected = s->batches = s->batch_frames = 0;
+        s->pixels = 0;
+        s->t0 = now;
+        s->lat_us.clear();
+        s->lat_next = 0;
+    }
+    return TFN_OK;
+}
+
+tfn_status tfn_server_destroy(tfn_server *s)
+{
+    if (!s) return TFN_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stopping = true;
+    }
+    s->cv_launch.notify_all();
+    if (s->launcher.joinable()) s->launcher.join();
+    if (s->retirer.joinable()) s->retirer.join();
+    DeviceGuard g(s->ctx->device);
+    destroy_resources(s);
+    delete s;
+    return TFN_OK;
+}
+
+}  // extern "C"

@@ -35,32 +35,33 @@ def test_every_declared_symbol_is_exported(tfn):
     assert set(names) <= set(tfn.EXPORTED) | {"tfn_stream"}
 
 
+STRUCTS = ["tfn_camera", "tfn_frame", "tfn_method", "tfn_server_opts", "tfn_serving_stats"]
+
+
 def test_struct_layouts_match_header(tfn, tmp_path):
+    # size and every field offset of every struct, as the C compiler lays them out
+    lines, want = [], []
+    for name in STRUCTS:
+        cls = getattr(tfn, name)
+        lines.append(f'  printf("%zu\\n", sizeof({name}));')
+        want.append(ctypes.sizeof(cls))
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({name}, {field}));')
+            want.append(getattr(cls, field).offset)
     src = tmp_path / "layout.c"
-    src.write_text("""
-#include <stdio.h>
-#include <stddef.h>
-#include "tfn.h"
-int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(tfn_frame), sizeof(tfn_camera), sizeof(tfn_method),
-         offsetof(tfn_frame, cam), offsetof(tfn_frame, normals), offsetof(tfn_frame, mask),
-         offsetof(tfn_frame, mask_pitch), offsetof(tfn_method, flags));
-  return 0;
-}
-""")
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"tfn.h\"\nint main(void) {\n" +
+                   "\n".join(lines) + "\n  return 0;\n}\n")
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = list(map(int, subprocess.check_output([str(exe)]).split()))
-    want = [ctypes.sizeof(tfn.tfn_frame), ctypes.sizeof(tfn.tfn_camera), ctypes.sizeof(tfn.tfn_method),
-            tfn.tfn_frame.cam.offset, tfn.tfn_frame.normals.offset, tfn.tfn_frame.mask.offset,
-            tfn.tfn_frame.mask_pitch.offset, tfn.tfn_method.flags.offset]
     assert got == want
 
 
 def test_status_strings_and_version(tfn):
     assert tfn.tfn_status_string(tfn.TFN_OK) == b"ok"
-    for s in range(10):
-        assert tfn.tfn_status_string(s)
+    for s in range(11):
+        assert tfn.tfn_status_string(s) != b"unknown status"
+    assert tfn.tfn_status_string(11) == b"unknown status"
     assert b"sm_103a" in tfn.tfn_version()
 
 
@@ -71,6 +72,29 @@ def test_null_context_is_rejected_without_touching_the_gpu(tfn):
     assert tfn.tfn_normals_batch(None, ctypes.byref(f), 1, ctypes.byref(m), None) == tfn.TFN_ERR_INVALID_ARG
     assert tfn.tfn_create(None, 0, 0) == tfn.TFN_ERR_INVALID_ARG
     assert tfn.tfn_destroy(None) == tfn.TFN_OK
+
+
+def test_null_handles_of_tuner_and_server_are_rejected(tfn, tmp_path):
+    f = tfn.tfn_frame()
+    m = tfn.make_method()
+    best = ctypes.c_int()
+    assert tfn.tfn_autotune(None, ctypes.byref(f), 1, ctypes.byref(m), 1, None, ctypes.byref(best),
+                            None) == tfn.TFN_ERR_INVALID_ARG
+    assert tfn.tfn_tuned_shape(None, 0, ctypes.byref(m), ctypes.byref(best)) == tfn.TFN_ERR_INVALID_ARG
+    path = os.fsencode(str(tmp_path / "tune.txt"))
+    assert tfn.tfn_tune_cache_save(None, path) == tfn.TFN_ERR_INVALID_ARG
+    assert tfn.tfn_tune_cache_load(None, path) == tfn.TFN_ERR_INVALID_ARG
+    o = tfn.tfn_server_opts()
+    h = ctypes.c_void_p(1)
+    assert tfn.tfn_server_create(None, ctypes.byref(o), ctypes.byref(h)) == tfn.TFN_ERR_INVALID_ARG
+    assert h.value is None  # *srv is cleared on failure
+    t = ctypes.c_uint64()
+    r = ctypes.c_int()
+    assert tfn.tfn_submit(None, ctypes.byref(f), 0, ctypes.byref(t)) == tfn.TFN_ERR_INVALID_ARG
+    assert tfn.tfn_wait(None, 1, 0, ctypes.byref(r)) == tfn.TFN_ERR_INVALID_ARG
+    st = tfn.tfn_serving_stats()
+    assert tfn.tfn_server_stats(None, ctypes.byref(st), 0) == tfn.TFN_ERR_INVALID_ARG
+    assert tfn.tfn_server_destroy(None) == tfn.TFN_OK
 
 
 def test_library_links_no_torch(tfn):

@@ -60,10 +60,11 @@ def dist_info():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the sources that define the kernels (not the host side)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2005_08165_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name in ("tfn_kernel.cuh", "tfn_internal.h") or (name.startswith("tfn_k_") and name.endswith(".cu")):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(name.encode() + f.read())
     return h.hexdigest()[:16]

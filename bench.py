@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=20000, help="requests per serving-mix run")
     return ap.parse_args()
 
 
@@ -327,6 +329,9 @@ def run_ours(args):
                         "frames_per_s": round(nf / (lm * 1e-3), 1),
                         "hbm_gbs": round(BYTES_PER_PX["f32_in_f32_out"] * px / (lm * 1e-3) / 1e9, 1)}
             variants.update(run_forms(torch, tfn, ctx, stream, dev, max(5, args.steps // 2)))
+        serving = None
+        if not args.no_serving:
+            serving = run_serving(torch, tfn, ctx, dev, d, args.serve_requests)
 
         line = {
             "metric": METRIC, "value": round(fps, 1), "unit": "frames/s", "n_gpus": world, "steps": args.steps,
@@ -347,6 +352,7 @@ def run_ours(args):
             "gpu_launches": args.steps,
             "device_status": status,
             "variants": variants,
+            "serving": serving,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
@@ -401,6 +407,133 @@ def run_forms(torch, tfn, ctx, stream, dev, steps):
         out[f"fp16_in_{fmt}_out_fd_mean"] = {"frames_per_s": round(N_FRAMES / (lm * 1e-3), 1),
                                              "hbm_gbs": round(BYTES_PER_PX[key] * px / (lm * 1e-3) / 1e9, 1)}
         del o
+    return out
+
+
+SERVE_SIZES = ((240, 320), (480, 640), (720, 1280), (1080, 1920))
+
+
+def serve_stream(tfn, srv, frames, order, flags, rate=None, seed=0):
+    """Submits requests order[i] -> frames[order[i]] (a list per pool entry of prebuilt tfn_frame slots; a
+    slot is reused only after its previous request completed), open loop with Poisson arrivals at `rate`
+    requests/s, or as fast as possible (rate None).  Returns (requests/s achieved, server stats)."""
+    import ctypes
+    import random
+    rnd = random.Random(seed)
+    submit, wait = tfn.tfn_submit, tfn.tfn_wait
+    h = srv.handle
+    t = ctypes.c_uint64()
+    res = ctypes.c_int()
+    outstanding = {}
+    used = [0] * len(frames)
+    srv.stats(reset=True)
+    start = time.perf_counter()
+    due = start
+    for p in order:
+        if rate:
+            due += rnd.expovariate(rate)
+            while time.perf_counter() < due:
+                pass
+        slots = frames[p]
+        j = used[p] % len(slots)
+        used[p] += 1
+        key = (p, j)
+        if key in outstanding:
+            tfn.check(wait(h, outstanding.pop(key), 60000, ctypes.byref(res)), "tfn_wait")
+            tfn.check(res.value, "request")
+        tfn.check(submit(h, ctypes.byref(slots[j]), flags, ctypes.byref(t)), "tfn_submit")
+        outstanding[key] = t.value
+    for tk in outstanding.values():
+        tfn.check(wait(h, tk, 60000, ctypes.byref(res)), "tfn_wait")
+        tfn.check(res.value, "request")
+    dt = time.perf_counter() - start
+    return len(order) / dt, srv.stats()
+
+
+def run_serving(torch, tfn, ctx, dev, depth_dev, n_req):
+    """Serving form: the request server on the mixed-resolution workload (host buffers, Poisson arrivals),
+    and the FP16 serving path against the plain per-frame path (device buffers)."""
+    import ctypes
+    import random
+
+    import numpy as np
+
+    import scenes
+    out = {}
+    # plain per-frame path: one non-graph launch per 480x640 FP32 frame, device-resident
+    nf = depth_dev.shape[0]
+    nrm = tfn.empty_normals(H, W, "f32", dev, lead=(nf,))
+    msk = tfn.empty_image((nf, H, W), torch.uint8, dev)
+    frames32 = [tfn.make_frame(depth_dev[k], nrm[k], msk[k], scenes.CAMERA) for k in range(nf)]
+    m32 = tfn.make_method("fd", "mean", "f32")
+    sh = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    for k in range(nf):
+        tfn.check(tfn.tfn_normals(ctx.handle, ctypes.byref(frames32[k]), ctypes.byref(m32), sh), "tfn_normals")
+    torch.cuda.synchronize()
+    reps = 4
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for k in range(nf):
+            tfn.tfn_normals(ctx.handle, ctypes.byref(frames32[k]), ctypes.byref(m32), sh)
+    torch.cuda.synchronize()
+    plain = reps * nf / (time.perf_counter() - t0)
+    out["plain_per_frame_f32"] = {"frames_per_s": round(plain, 1),
+                                  "what": "tfn_normals per 480x640 FP32 frame, device buffers, no graph"}
+    # FP16 serving path: FP16 depth in, FP16 normals out, device-resident requests through the server
+    d16 = tfn.empty_image((nf, H, W), torch.float16, dev)
+    d16.copy_(depth_dev)
+    o16 = tfn.empty_normals(H, W, "f16", dev, lead=(nf,))
+    frames16 = [[tfn.make_frame(d16[k], o16[k], msk[k], scenes.CAMERA, output="f16")] for k in range(nf)]
+    with tfn.Server(ctx, grad="fd", phi="mean", output="f16") as srv:
+        serve_stream(tfn, srv, frames16, list(range(nf)), 0)  # warm-up
+        order = [k % nf for k in range(8 * nf)]
+        fps16, st = serve_stream(tfn, srv, frames16, order, 0)
+    out["fp16_serving_device"] = {"frames_per_s": round(fps16, 1), "p50_ms": round(st["latency_p50_us"] / 1e3, 3),
+                                  "p99_ms": round(st["latency_p99_us"] / 1e3, 3),
+                                  "mean_batch": round(st["mean_batch_frames"], 1),
+                                  "vs_plain_per_frame_f32": round(fps16 / plain, 2),
+                                  "what": "480x640 FP16 in, FP16 planar out, device buffers, as fast as submitted"}
+    del nrm, d16, o16
+    # the serving mix: resolutions uniform over SERVE_SIZES, FP32/FP16 uniform, per-request intrinsics
+    # fx = fy = 481.2 W/640 x U(0.95, 1.05); host buffers (page-locked); 4 scenes per resolution and type,
+    # 2 output slots each
+    rng = np.random.default_rng(10 ** 6)
+    pool = []
+    for si, (Hh, Ww) in enumerate(SERVE_SIZES):
+        for k in range(4):
+            f = 481.2 * Ww / 640 * rng.uniform(0.95, 1.05)
+            r = scenes.Recipe(H=Hh, W=Ww, fx=f, fy=f, u0=(Ww - 1) / 2, v0=(Hh - 1) / 2, noise_k=0.0012,
+                              hole_frac=0.03)
+            img = scenes.render(10 ** 6 + 4 * si + k, r)
+            for arr in (img, img.astype(np.float16)):
+                inp = torch.from_numpy(arr).pin_memory()
+                slots = []
+                for _ in range(2):
+                    n_ = torch.empty((3, Hh, Ww), dtype=torch.float32, pin_memory=True)
+                    m_ = torch.empty((Hh, Ww), dtype=torch.uint8, pin_memory=True)
+                    slots.append((tfn.make_frame(inp, n_, m_, r.camera), n_, m_))
+                pool.append((inp, slots))
+    frames = [[s[0] for s in slots] for _, slots in pool]
+    rnd = random.Random(10 ** 6)
+    order = [rnd.randrange(len(pool)) for _ in range(n_req)]
+    mix = {"workload": f"{n_req} requests; resolution uniform over 240x320, 480x640, 720x1280, 1080x1920; "
+                       "FP32/FP16 depth uniform; per-request intrinsics; host buffers; fd, mean, FP32 out",
+           "requests": n_req}
+    with tfn.Server(ctx, grad="fd", phi="mean", output="f32") as srv:
+        serve_stream(tfn, srv, frames, order[:256], tfn.TFN_REQ_HOST)  # warm-up
+        sat, st = serve_stream(tfn, srv, frames, order, tfn.TFN_REQ_HOST)
+        mix["saturated"] = {"requests_per_s": round(sat, 1), "p50_ms": round(st["latency_p50_us"] / 1e3, 3),
+                            "p99_ms": round(st["latency_p99_us"] / 1e3, 3),
+                            "mean_batch": round(st["mean_batch_frames"], 1),
+                            "gpixels_per_s": round(st["pixels"] / st["elapsed_s"] / 1e9, 2)}
+        mix["poisson"] = []
+        for frac in (0.5, 0.8, 1.0):
+            got, st = serve_stream(tfn, srv, frames, order, tfn.TFN_REQ_HOST, rate=frac * sat, seed=int(frac * 10))
+            mix["poisson"].append({"offered_per_s": round(frac * sat, 1), "achieved_per_s": round(got, 1),
+                                   "p50_ms": round(st["latency_p50_us"] / 1e3, 3),
+                                   "p99_ms": round(st["latency_p99_us"] / 1e3, 3),
+                                   "mean_batch": round(st["mean_batch_frames"], 1)})
+    out["mix_host"] = mix
     return out
 
 

@@ -163,6 +163,40 @@ def test_reduced_precision_outputs_round_the_f32_result(torch, tfn, ctx, output)
     assert torch.equal(m16, m32)
 
 
+@pytest.mark.parametrize("output", ["f16", "bf16", "f16x4", "bf16x4"])
+def test_fp16_precision_form_angle_vs_oracle(torch, tfn, ctx, output):
+    """FP16 depth in, FP16/BF16 normals out: per-frame mean and max angle against the FP64 oracle run on
+    the same FP16-decoded depth (clean scenes rounded to FP16, 480x640).  FP16 outputs (11-bit significand)
+    must keep the mean within 0.05 deg; BF16 outputs (8-bit significand) sit at their rounding floor, a
+    mean of about 0.05 deg, and are held to that floor instead."""
+    import oracle
+    imgs = scenes.render_batch(3000, 3, scenes.Recipe()).astype(np.float16)
+    inputs = [to_dev(torch, tfn, x) for x in imgs]
+    n, m = ctx.normals_batch(inputs, scenes.CAMERA, output=output)
+    torch.cuda.synchronize()
+    rows = []
+    for k, img in enumerate(imgs):
+        got = n[k].float() if output in ("f16", "bf16") else n[k][..., :3].permute(2, 0, 1).float()
+        got = got.cpu().numpy().astype(np.float64)
+        cam = scenes.CAMERA
+        ref_n, ref_m = oracle.normals(img, cam["fx"], cam["fy"], cam["u0"], cam["v0"], grad="fd", phi="mean")
+        assert (m[k].cpu().numpy() == ref_m).all()
+        v = ref_m == 1
+        ang = oracle.angle_deg(got, ref_n)[v]
+        rows.append((float(ang.mean()), float(ang.max())))
+    print(f"\nFP16 in -> {output} out, angle vs FP64 oracle per frame (mean, max deg): "
+          + ", ".join(f"({a:.4f}, {b:.4f})" for a, b in rows))
+    # rounding each component to nearest moves it by at most 2^-11 (f16) / 2^-8 (bf16) of itself, so the
+    # unit vector turns by at most about that many radians (sqrt(3) x for safety), plus the FP32 path's 1e-3
+    half_ulp = 2.0 ** -11 if output.startswith("f16") else 2.0 ** -8
+    floor = np.degrees(np.sqrt(3) * half_ulp) + 1e-3
+    assert all(b <= floor for _, b in rows)
+    if output.startswith("f16"):
+        assert all(a <= 0.05 for a, _ in rows)
+    else:
+        assert all(a <= floor / 2 for a, _ in rows)
+
+
 def test_batch_composition_and_alone_bit_identical(torch, tfn, ctx):
     frames = depth_frames([(67, 131), (480, 640), (33, 64)], 1200)
     n_mix, m_mix = run_batch(torch, tfn, ctx, frames, grad="scharr", phi="median")

@@ -8,8 +8,10 @@ library has not been built.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
+import weakref
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtfn.so")
@@ -147,6 +149,21 @@ EXPORTED = ["tfn_status_string", "tfn_version", "tfn_last_cuda_error", "tfn_crea
             "tfn_server_destroy"]
 
 
+# Objects that own library handles, closed at interpreter exit (servers first, then plans, then contexts)
+# so that no handle outlives the CUDA runtime's own teardown.
+_LIVE = {"server": weakref.WeakSet(), "plan": weakref.WeakSet(), "ctx": weakref.WeakSet()}
+
+
+@atexit.register
+def _close_all():
+    for kind in ("server", "plan", "ctx"):
+        for obj in list(_LIVE[kind]):
+            try:
+                obj.close()
+            except Exception:
+                pass
+
+
 class TfnError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         msg = tfn_status_string(status).decode()
@@ -259,6 +276,7 @@ class Context:
         h = ctypes.c_void_p()
         check(tfn_create(ctypes.byref(h), device, mem_budget), "tfn_create")
         self.handle = h
+        _LIVE["ctx"].add(self)
 
     def close(self):
         if self.handle:
@@ -399,6 +417,7 @@ class Plan:
 
     def __init__(self, handle, inputs, normals, masks):
         self.handle = handle
+        _LIVE["plan"].add(self)
         self.inputs, self.normals, self.masks = inputs, normals, masks  # keep the buffers alive
 
     def launch(self, stream=None):
@@ -432,6 +451,7 @@ class Server:
         h = ctypes.c_void_p()
         check(tfn_server_create(ctx.handle, ctypes.byref(o), ctypes.byref(h)), "tfn_server_create")
         self.handle = h
+        _LIVE["server"].add(self)
         self.output = output
         self._keep = {}
 

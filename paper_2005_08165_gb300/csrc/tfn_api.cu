@@ -148,14 +148,17 @@ tfn_status validate_frame(const tfn_frame *f, int out_fmt)
 
 // Per-pixel refinement threshold: a pixel is recomputed in double-float when
 // its FP32 error bound, (6 + 4 cA + 32/min(fx,fy)) u + K1 u bound/|n'|, could
-// exceed 3/4 of the 1e-3 degree budget.  bound is sum |num_p|(|rho_j| +
-// |rho_-j|)/m for the mean (candidate-sum cancellation; K1 = 23 covers the
-// per-edge reciprocal, rho, numerator, product and accumulation roundings and
-// the approximate 1/m) and the larger |middle candidate| for the median
-// (K1 = 11).  cA bounds |A|/|n'|: A = (u-u0) G_u + (v-v0) G_v and
-// |n'| >= (fx |G_u|, fy |G_v|).
-float refine_threshold(const tfn_frame &f, int phi)
+// exceed 3/4 of the 1e-3 degree budget (u = 2^-24).  bound is sum_p |num_p|
+// (|rho_j| + |rho_-j|) for the mean (candidate-sum cancellation; K1 = 23
+// covers the per-edge reciprocal, rho, numerator, product and accumulation
+// roundings) and the larger |middle candidate| for the median (K1 = 11).
+// cA bounds |A|/|n'|: A = (u-u0) G_u + (v-v0) G_v and |n'| >= |(fx G_u, fy G_v)|.
+// The gradients are carried as h + l to about u^2 relative (compensated
+// reciprocals, or a residual-corrected quotient for FD).  The kernel compares
+// bound with thr |n'|.
+float refine_threshold(const tfn_frame &f, int grad, int phi)
 {
+    (void)grad;  // every filter's gradients are compensated
     const double u = std::ldexp(1.0, -24);
     const double tol_part = 0.75 * 1e-3 * M_PI / 180.0;
     const double mu = std::max(std::fabs(0.0 - f.cam.u0), std::fabs(f.width - 1.0 - f.cam.u0));
@@ -192,7 +195,7 @@ tfn_status encode_map(CUtensorMap *map, const tfn_frame &f, int cfg)
 }
 
 // Fills the device descriptor of one frame for tile shape `cfg`.
-FrameDesc describe_frame(const tfn_frame &f, int cfg, int phi, int tile_begin)
+FrameDesc describe_frame(const tfn_frame &f, int cfg, const tfn_method &m, int tile_begin)
 {
     const int tw = kCfgs[cfg].tw;
     FrameDesc fd;
@@ -202,6 +205,8 @@ FrameDesc describe_frame(const tfn_frame &f, int cfg, int phi, int tile_begin)
     fd.out_plane = f.normals_plane_stride;
     fd.mask = f.mask;
     fd.mask_pitch = f.mask_pitch;
+    fd.in = f.input;
+    fd.in_pitch = f.input_pitch;
     fd.H = f.height;
     fd.W = f.width;
     fd.tiles_x = (f.width + tw - 1) / tw;
@@ -210,7 +215,7 @@ FrameDesc describe_frame(const tfn_frame &f, int cfg, int phi, int tile_begin)
     fd.fy = f.cam.fy;
     fd.u0 = f.cam.u0;
     fd.v0 = f.cam.v0;
-    fd.thr = refine_threshold(f, phi);
+    fd.thr = refine_threshold(f, m.grad, m.phi);
     fd.kind = f.input_type;
     return fd;
 }
@@ -238,7 +243,9 @@ tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDes
                  "cudaOccupancyMaxActiveBlocksPerMultiprocessor"))
         return TFN_ERR_CUDA;
     if (per_sm < 1) per_sm = 1;
-    const int grid = std::min(total_tiles, per_sm * num_sms);
+    // one warp per work item at a time: no more CTAs than items / warps per CTA
+    const int nw = kCfgs[cfg].warps;
+    const int grid = std::min((total_tiles + nw - 1) / nw, per_sm * num_sms);
     if (grid < 1) return TFN_OK;
     LaunchArgs a;
     a.frames = d_frames;
@@ -339,7 +346,7 @@ tfn_status launch_group(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_me
         int tb = 0;
         for (int i = 0; i < n; ++i) {
             const tfn_frame &f = frames[i];
-            d[i] = describe_frame(f, cfg, m.phi, tb);
+            d[i] = describe_frame(f, cfg, m, tb);
             tb += frame_tiles(f, cfg);
             st = encode_map(&maps[i], f, cfg);
             if (st) return st;
@@ -613,7 +620,7 @@ tfn_status tfn_plan_create(tfn_ctx *c, const tfn_frame *frames, int n, const tfn
     for (int i = 0, tb = 0; i < n; ++i) {
         if (i > 0 && frames[i].input_type != frames[i - 1].input_type) tb = 0;
         const int cfg = pick_cfg(c, frames[i].input_type, *m);
-        d[i] = describe_frame(frames[i], cfg, m->phi, tb);
+        d[i] = describe_frame(frames[i], cfg, *m, tb);
         tb += frame_tiles(frames[i], cfg);
         if ((st = encode_map(&maps[i], frames[i], cfg))) break;
     }

@@ -22,13 +22,14 @@ struct alignas(16) FrameDesc {
     int64_t out_plane;   // bytes
     uint8_t *mask;
     int64_t mask_pitch;  // bytes
+    const void *in;      // the input image (read again only for the rare refined pixels)
+    int64_t in_pitch;    // bytes
     int32_t H, W;
-    int32_t tiles_x;     // tiles per row of this frame
-    int32_t tile_begin;  // global index of this frame's first tile
+    int32_t tiles_x;     // work items per row band of this frame
+    int32_t tile_begin;  // global index of this frame's first work item
     float fx, fy, u0, v0;
     float thr;           // refinement threshold (see refine_threshold in tfn_api.cu)
     int32_t kind;        // Kind of this frame (a launch holds frames of one kind)
-    int32_t pad[2];
 };
 static_assert(sizeof(FrameDesc) == 96, "FrameDesc layout");
 
@@ -43,28 +44,28 @@ struct LaunchArgs {
     int32_t flags;
 };
 
-// Tile shapes the kernels are compiled for: TW x TH pixels per tile, PR
-// pixel rows per thread (4 pixel columns per thread); every shape has 256
-// threads.
+// Work-item shapes the kernels are compiled for.  An item is a band of tw =
+// 128 pixel columns (32 lanes x 4) by th rows of one frame, computed by one
+// warp that rolls down its rows (pr = th rows per lane); the rows stream
+// through a ring of nst shared-memory stages of cr rows each (th + 2 rows per
+// item: one above, one below), per warp; a CTA has `warps` warps.
 struct TileCfg {
-    int tw, th, pr;
+    int tw, th, pr, cr, nst, warps;
 };
 constexpr int kNumCfg = 3;
-constexpr TileCfg kCfgs[kNumCfg] = {{64, 32, 2}, {128, 16, 2}, {64, 16, 1}};
-constexpr int kStages = 6;
-constexpr int kFrameTableMax = 160;  // frames whose descriptors a CTA keeps in shared memory
+constexpr TileCfg kCfgs[kNumCfg] = {{128, 18, 18, 5, 3, 4}, {128, 30, 30, 8, 3, 4}, {128, 12, 12, 7, 3, 4}};
 
-inline int cfg_threads(int) { return 256; }
+inline int cfg_threads(int c) { return 32 * kCfgs[c].warps; }
 inline int kind_elem_size(int kind) { return (kind == KIND_DEPTH_F32 || kind == KIND_DISP_F32) ? 4 : 2; }
 // Halo columns loaded on each side so that the TMA box starts on a 16-byte boundary.
 inline int kind_padx(int kind) { return 16 / kind_elem_size(kind); }
 inline int box_w(int kind, int c) { return kCfgs[c].tw + 2 * kind_padx(kind); }
-inline int box_h(int c) { return kCfgs[c].th + 2; }
+inline int box_h(int c) { return kCfgs[c].cr; }
 inline size_t stage_bytes(int kind, int c) { return (size_t)box_w(kind, c) * box_h(c) * kind_elem_size(kind); }
-inline size_t stage_stride(int kind, int c) { return (stage_bytes(kind, c) + 1023) & ~(size_t)1023; }
+inline size_t stage_stride(int kind, int c) { return (stage_bytes(kind, c) + 127) & ~(size_t)127; }
 inline size_t smem_bytes(int kind, int c)
 {
-    return kStages * stage_stride(kind, c) + kFrameTableMax * sizeof(FrameDesc) + 128;
+    return (size_t)kCfgs[c].warps * kCfgs[c].nst * stage_stride(kind, c) + 128;
 }
 
 // Kernel entry points, one per (kind, grad, phi, cfg); defined in tfn_k_*.cu.
@@ -81,9 +82,9 @@ namespace tfn {
 bool cuda_ok(cudaError_t e, const char *what);
 tfn_status validate_method(const tfn_method *m);
 tfn_status validate_frame(const tfn_frame *f, int out_fmt);
-float refine_threshold(const tfn_frame &f, int phi);
+float refine_threshold(const tfn_frame &f, int grad, int phi);
 tfn_status encode_map(CUtensorMap *map, const tfn_frame &f, int cfg);
-FrameDesc describe_frame(const tfn_frame &f, int cfg, int phi, int tile_begin);
+FrameDesc describe_frame(const tfn_frame &f, int cfg, const tfn_method &m, int tile_begin);
 int frame_tiles(const tfn_frame &f, int cfg);
 tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
                           uint32_t *d_status, int nframes, int total_tiles, int num_sms, cudaStream_t stream);

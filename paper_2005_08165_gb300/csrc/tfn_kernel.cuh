@@ -1,22 +1,25 @@
 // tfn_kernel.cuh -- the fused Three-Filters-to-Normal kernel for sm_103a.
 //
-// One persistent kernel walks a queue of TW x TH tiles spanning every frame
-// of a launch; CTA b takes every grid-th tile starting at b.  Each tile plus a halo
-// (1 row above/below, 4 or 8 columns left/right so that the box starts on a
-// 16-byte boundary) is staged into shared memory by a TMA 2D copy, through a
-// ring of kStages buffers (mbarrier for "landed", a release counter for
-// "free"); each of the 256 threads computes 4 x PR pixels from a register
-// window and writes normals and mask with vectorised streaming stores.  Out-of-image taps read the TMA
-// zero fill, which is a hole, so image borders need no special case.
+// A persistent kernel of independent warps.  A work item is a band of 128
+// pixel columns x TH rows of one frame; warp w takes items w, w + W, ... of a
+// queue spanning every frame of the launch.  A lane owns 4 adjacent columns
+// and rolls down the item's rows keeping three sample rows (above, at, below)
+// in registers, so the edges between two rows are computed once for both.
+// The rows reach shared memory through a per-warp ring of TMA 2D copies
+// (boxes of CR rows x 128 columns plus a 16-byte halo each side, one mbarrier
+// per stage); normals and mask leave through vectorised streaming stores.
+// Holes decode to 2^100 (see kHole), the TMA zero fill outside the image is a
+// hole, and rows past the bottom read as holes, so borders need no special
+// case.
 //
 // Arithmetic (Sec. III of Fan et al.):
-//   inverse depth    w = 1/Z per sample as wh + wl (hardware reciprocal plus
-//                    its FMA residual), so gradients never lose the digits a
-//                    difference of two rounded reciprocals would;
-//   filters          G = sum_k c_k (w_{k,+1} - w_{k,-1}) with the row weights of
-//                    the chosen filter (normalisation dropped: the normal's
-//                    direction is homogeneous in (G_u, G_v)); disparity: the
-//                    same on d (Eq. nx2_ny2_nz3);
+//   filters          FD on depth: G = 1/Z_{+1} - 1/Z_{-1} = (Z_{-1} - Z_{+1}) /
+//                    (Z_{-1} Z_{+1}) in one pass; Sobel, Scharr, Prewitt:
+//                    G = sum_k c_k (w_{k,+1} - w_{k,-1}) with w = 1/Z per sample
+//                    as wh + wl (hardware reciprocal plus its FMA residual) and
+//                    exact tap differences (Knuth's TwoSum); normalisation
+//                    dropped (the normal's direction is homogeneous in
+//                    (G_u, G_v)); disparity: the same on d (Eq. nx2_ny2_nz3);
 //   candidates       c_j = A + R_j, A = (u-u0) G_u + (v-v0) G_v,
 //                    R_j = (du G_u + dv G_v) rho_j, rho_j = Z_j / (Z_j - Z_i)
 //                    (Eq. nx2_ny2_nz2 with the back-projection of Eq. intrinsic
@@ -29,13 +32,12 @@
 //                    position 3 (odd count) or 3 and 4 (even count);
 //   output           n = -n'/|n'|, n' = (fx G_u, fy G_v, -(A + Phi)).
 //
-// Accuracy: the gradients are compensated (w residuals, exact tap
-// differences by Knuth's TwoSum where filter terms can cancel), so each
-// candidate carries a few units of FP32 rounding relative to itself.  What
-// remains is cancellation inside the candidate sum (mean) or between the two
-// middle candidates (even median); each pixel bounds that error and the rare
-// pixels whose bound exceeds the threshold go to refine_pixel(), which redoes
-// the pixel in double-float arithmetic.
+// Accuracy: each candidate carries a few units of FP32 rounding relative to
+// itself, and each gradient a known relative error.  What remains is
+// cancellation inside the candidate sum (mean) or between the two middle
+// candidates (even median), and the effect of the gradient error; each pixel
+// bounds both, and the rare pixels whose bound exceeds the threshold go to
+// refine_pixel(), which redoes the pixel in double-float arithmetic.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -49,6 +51,7 @@ namespace dev {
 constexpr float kValidLo = 1.52587890625e-05f;  // 2^-16
 constexpr float kValidHi = 65536.0f;            // 2^16
 constexpr long long kWaitCycles = 4000000000LL;    // ~2 s at 2 GHz
+constexpr long long kDrainCycles = 2000000LL;      // ~1 ms: the drain after a failed wait
 
 // ---------------------------------------------------------------- numerics
 
@@ -327,267 +330,307 @@ __device__ __forceinline__ EdgeR edge_recip(float delta)
     return {r, __fmul_rn(delta, r)};
 }
 
-// The register window of one thread: ROWS+2 sample rows x 6 columns around
-// its 4 x ROWS pixels.  Holes are stored as 0.
-template <int KIND, int ROWS>
-struct Win {
-    float z[ROWS + 2][6];   // holes are 0, valid samples are > 0
-    float wh[ROWS + 2][6];  // depth kinds: 1/Z ~ wh + wl (rcp + FMA residual)
-    float wl[ROWS + 2][6];
-    unsigned ok[ROWS + 2];  // bit c: column c valid
-};
+// A hole's stand-in value, 2^100.  Its difference with any valid sample
+// (<= 2^16) has a square that overflows to +inf, whose reciprocal is 0, so an
+// edge that touches a hole gets r = 0 and k = 0 with no test (two holes give
+// delta = 0: the same).  Valid samples are <= kValidHi, holes are above it.
+constexpr float kHole = 1.2676506002282294e30f;
 
 template <int KIND>
-__device__ __forceinline__ float decode(typename KindTraits<KIND>::T raw, bool &ok)
+__device__ __forceinline__ float decode(typename KindTraits<KIND>::T raw)
 {
-    float v;
-    if (KIND == KIND_DISP_U16) {
-        v = (float)(uint16_t)raw;
-        ok = v != 0.f;
+    if constexpr (KIND == KIND_DISP_U16) {
+        const float v = (float)raw;
+        return v != 0.f ? v : kHole;
     } else {
-        if (KIND == KIND_DEPTH_F16)
-            v = __half2float(*reinterpret_cast<const __half *>(&raw));
+        float v;
+        if constexpr (KIND == KIND_DEPTH_F16)
+            v = __half2float(raw);
         else
-            v = *reinterpret_cast<const float *>(&raw);
+            v = raw;
         // finite and in [2^-16, 2^16]: one unsigned compare on the bit pattern
         // (negatives, infinities and NaNs have patterns above 2^16's)
-        ok = (uint32_t)(__float_as_uint(v) - 0x37800000u) <= (0x47800000u - 0x37800000u);
-    }
-    return ok ? v : 0.f;
-}
-
-template <int KIND, int ROWS>
-__device__ __forceinline__ void load_window(const void *tile, int SW, int PADX, int row0, int col0, Win<KIND, ROWS> &W)
-{
-    typedef typename KindTraits<KIND>::T T;
-    const T *t = reinterpret_cast<const T *>(tile);
-#pragma unroll
-    for (int a = 0; a < ROWS + 2; ++a) {
-        const T *p = t + (row0 + a) * SW + PADX + col0;  // p[-1..4]
-        T raw[6];
-        raw[0] = p[-1];
-        if (sizeof(T) == 4) {
-            const uint4 q = *reinterpret_cast<const uint4 *>(p);
-            raw[1] = *reinterpret_cast<const T *>(&q.x);
-            raw[2] = *reinterpret_cast<const T *>(&q.y);
-            raw[3] = *reinterpret_cast<const T *>(&q.z);
-            raw[4] = *reinterpret_cast<const T *>(&q.w);
-        } else {
-            const uint2 q = *reinterpret_cast<const uint2 *>(p);
-            const uint16_t h[4] = {(uint16_t)(q.x & 0xffff), (uint16_t)(q.x >> 16), (uint16_t)(q.y & 0xffff),
-                                   (uint16_t)(q.y >> 16)};
-#pragma unroll
-            for (int c = 0; c < 4; ++c) raw[1 + c] = *reinterpret_cast<const T *>(&h[c]);
-        }
-        raw[5] = p[4];
-        unsigned bits = 0;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            bool ok;
-            W.z[a][c] = decode<KIND>(raw[c], ok);
-            bits |= (unsigned)ok << c;
-            if (!KindTraits<KIND>::disparity) {
-                const float wh = rcp_approx(W.z[a][c]);
-                W.wh[a][c] = wh;
-                W.wl[a][c] = __fmaf_rn(-wh, W.z[a][c], 1.f) * wh;
-            }
-        }
-        W.ok[a] = bits;
+        return (uint32_t)(__float_as_uint(v) - 0x37800000u) <= (0x47800000u - 0x37800000u) ? v : kHole;
     }
 }
 
-// Edge between samples (a1,c1) < (a2,c2) (raster order): 1/(s2 - s1); for
-// disparity, an edge touching a hole is given delta = 0 so that it drops out.
-template <int KIND, int ROWS>
-__device__ __forceinline__ EdgeR edge(const Win<KIND, ROWS> &W, int a1, int c1, int a2, int c2)
+template <class T>
+__device__ __forceinline__ T from_bits16(uint32_t b)
 {
-    float d = W.z[a2][c2] - W.z[a1][c1];
-    if (KindTraits<KIND>::disparity) d = (W.z[a1][c1] != 0.f && W.z[a2][c2] != 0.f) ? d : 0.f;
-    return edge_recip(d);
-}
-
-// rho_j = Z_j / (Z_j - Z_i) for pixel i = (a,c) and neighbour j = (a+dv, c+du);
-// disparity: d_i / (d_i - d_j).  k is the edge's candidate indicator.
-template <int KIND, int ROWS>
-__device__ __forceinline__ float rho(const Win<KIND, ROWS> &W, int a, int c, int dv, int du, float &k)
-{
-    const int a2 = a + dv, c2 = c + du;
-    const bool fwd = dv > 0 || (dv == 0 && du > 0);  // i precedes j in raster order
-    const EdgeR e = fwd ? edge<KIND, ROWS>(W, a, c, a2, c2) : edge<KIND, ROWS>(W, a2, c2, a, c);
-    k = e.k;
-    if (KindTraits<KIND>::disparity) return fwd ? -__fmul_rn(W.z[a][c], e.r) : __fmul_rn(W.z[a][c], e.r);
-    return fwd ? __fmul_rn(W.z[a2][c2], e.r) : -__fmul_rn(W.z[a2][c2], e.r);
-}
-
-// Exact difference of two taps as h + l (w-differences carry the w residuals).
-template <int KIND, int ROWS>
-__device__ __forceinline__ df tap_diff(const Win<KIND, ROWS> &W, int a1, int c1, int a2, int c2, bool exact_needed)
-{
-    if (KindTraits<KIND>::disparity) {
-        if (KindTraits<KIND>::exact_diff) return {W.z[a2][c2] - W.z[a1][c1], 0.f};
-        return two_sum(W.z[a2][c2], -W.z[a1][c1]);
-    }
-    const float lo = __fsub_rn(W.wl[a2][c2], W.wl[a1][c1]);
-    if (!exact_needed) return {__fsub_rn(W.wh[a2][c2], W.wh[a1][c1]), lo};
-    const df h = two_sum(W.wh[a2][c2], -W.wh[a1][c1]);
-    return {h.h, __fadd_rn(h.l, lo)};
-}
-
-template <int KIND, int GRAD, int ROWS>
-__device__ __forceinline__ void gradients_win(const Win<KIND, ROWS> &W, int a, int c, df &Gu, df &Gv)
-{
-    if (GRAD == GRAD_FD) {
-        // a single difference: no cancellation between terms to protect
-        Gu = tap_diff<KIND, ROWS>(W, a, c - 1, a, c + 1, false);
-        Gv = tap_diff<KIND, ROWS>(W, a - 1, c, a + 1, c, false);
+    if constexpr (sizeof(T) == 2) {
+        const uint16_t s = (uint16_t)b;
+        return *reinterpret_cast<const T *>(&s);
     } else {
-        Gu = filter_sum<GRAD>(tap_diff<KIND, ROWS>(W, a - 1, c - 1, a - 1, c + 1, true),
-                              tap_diff<KIND, ROWS>(W, a, c - 1, a, c + 1, true),
-                              tap_diff<KIND, ROWS>(W, a + 1, c - 1, a + 1, c + 1, true));
-        Gv = filter_sum<GRAD>(tap_diff<KIND, ROWS>(W, a - 1, c - 1, a + 1, c - 1, true),
-                              tap_diff<KIND, ROWS>(W, a - 1, c, a + 1, c, true),
-                              tap_diff<KIND, ROWS>(W, a - 1, c + 1, a + 1, c + 1, true));
+        return T();
     }
 }
 
-struct PixelResult {
-    float x, y, z;
-    bool valid, refine;
+// One sample row of a lane's window: image columns x0-1 .. x0+4 around the
+// lane's 4 pixel columns x0 .. x0+3.  Depth rows that feed a compensated
+// (Sobel-type) filter also carry w = 1/Z per sample as wh + wl.
+template <int KIND, int GRAD>
+struct Row {
+    static constexpr bool kW = !KindTraits<KIND>::disparity && GRAD != GRAD_FD;
+    float z[6];
+    float wh[kW ? 6 : 1], wl[kW ? 6 : 1];
 };
 
-// Main FP32 path of one pixel, branch-free: every lane runs the same
-// instructions; invalid pixels, the special case and pixels that need the
-// double-float path are resolved by selects at the end.  Every product is an
-// explicit __fmul_rn (never contracted into an FMA), so a pixel's bits do not
-// depend on which row of a thread's window it sits in or on the tile shape.
-template <int KIND, int GRAD, int PHI, int ROWS>
-__device__ __forceinline__ PixelResult pixel_normal(const Win<KIND, ROWS> &W, unsigned evmask, int a, int c, int u, int v,
-                                                    float fx, float fy, float u0, float v0, float thr, bool refine_all)
+template <int KIND, int GRAD>
+__device__ __forceinline__ void hole_row(Row<KIND, GRAD> &R)
 {
-    // evaluable: the centre and every filter tap valid (bit c of the row's mask)
-    const bool ev = (evmask >> c) & 1u;
-    df Gu, Gv;
-    gradients_win<KIND, GRAD, ROWS>(W, a, c, Gu, Gv);
-    const float gu = __fadd_rn(Gu.h, Gu.l), gv = __fadd_rn(Gv.h, Gv.l);
-    // Sec. III special case: both gradients exactly zero (the sums h + l of an
-    // exact representation vanish only when both parts do)
-    const bool flat = Gu.h == 0.f && Gu.l == 0.f && Gv.h == 0.f && Gv.l == 0.f;
-    float num[4];
-    num[0] = gu;
-    num[1] = gv;
-    num[2] = __fadd_rn(__fadd_rn(Gu.h, Gv.h), __fadd_rn(Gu.l, Gv.l));
-    num[3] = __fadd_rn(__fsub_rn(Gu.h, Gv.h), __fsub_rn(Gu.l, Gv.l));
-    // pair p: neighbour j_p and -j_p; j = right, down, down-right, up-right
-    const int du_[4] = {1, 0, 1, 1}, dv_[4] = {0, 1, 1, -1};
-    float rj[4], rm[4], kj[4], km[4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        rj[p] = rho<KIND, ROWS>(W, a, c, dv_[p], du_[p], kj[p]);
-        rm[p] = rho<KIND, ROWS>(W, a, c, -dv_[p], -du_[p], km[p]);
+    for (int c = 0; c < 6; ++c) R.z[c] = kHole;
+    if constexpr (Row<KIND, GRAD>::kW) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) R.wh[c] = R.wl[c] = 0.f;
     }
-    // The mean is carried unnormalised: n' scaled by m (> 0) has the same
-    // direction, so no 1/m is needed.
-    float mF, mbound, scale;
-    if (PHI == PHI_MEAN) {
-        float S = 0.f, Sabs = 0.f, m = 0.f;
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            S = __fmaf_rn(num[p], __fsub_rn(rj[p], rm[p]), S);
-            Sabs = __fmaf_rn(fabsf(num[p]), __fadd_rn(fabsf(rj[p]), fabsf(rm[p])), Sabs);
-            if (GRAD == GRAD_FD && !KindTraits<KIND>::disparity && p >= 2) {
-                // FD: a diagonal neighbour may be a hole (its rho is 0 already)
-                m += (W.z[a + dv_[p]][c + du_[p]] != 0.f ? kj[p] : 0.f);
-                m += (W.z[a - dv_[p]][c - du_[p]] != 0.f ? km[p] : 0.f);
-            } else {
-                m += kj[p] + km[p];
-            }
-        }
-        mF = S;
-        mbound = Sabs;
-        scale = m;
-    } else {
-        float s[8];
-        int cnt = 0;
-        unsigned sgn = 0;  // sign bit of the next sentinel: +inf, -inf, +inf, ...
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const float cand[2] = {__fmul_rn(num[p], rj[p]), -__fmul_rn(num[p], rm[p])};
-            const float rr[2] = {rj[p], rm[p]};
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const bool kept = rr[q] != 0.f;
-                cnt += kept;
-                s[2 * p + q] = kept ? cand[q] : __uint_as_float(0x7f800000u | sgn);
-                sgn ^= kept ? 0u : 0x80000000u;
-            }
-        }
-#define TFN_CE(i, j)                           \
-    {                                          \
-        const float lo_ = fminf(s[i], s[j]);   \
-        s[j] = fmaxf(s[i], s[j]);              \
-        s[i] = lo_;                            \
-    }
-        TFN_CE(0, 2) TFN_CE(1, 3) TFN_CE(4, 6) TFN_CE(5, 7)
-        TFN_CE(0, 4) TFN_CE(1, 5) TFN_CE(2, 6) TFN_CE(3, 7)
-        TFN_CE(0, 1) TFN_CE(2, 3) TFN_CE(4, 5) TFN_CE(6, 7)
-        TFN_CE(2, 4) TFN_CE(3, 5)
-        TFN_CE(1, 4) TFN_CE(3, 6)
-        TFN_CE(1, 2) TFN_CE(3, 4) TFN_CE(5, 6)
-#undef TFN_CE
-        const bool odd = cnt & 1;
-        mF = odd ? s[3] : __fmul_rn(0.5f, __fadd_rn(s[3], s[4]));
-        mbound = odd ? fabsf(s[3]) : fmaxf(fabsf(s[3]), fabsf(s[4]));
-        scale = 1.f;
-    }
-    const float A = __fmaf_rn(__fsub_rn((float)u, u0), gu, __fmul_rn(__fsub_rn((float)v, v0), gv));
-    const float nxp = __fmul_rn(__fmul_rn(scale, fx), gu), nyp = __fmul_rn(__fmul_rn(scale, fy), gv);
-    const float nzp = -__fmaf_rn(scale, A, mF);
-    const float nn = __fmaf_rn(nxp, nxp, __fmaf_rn(nyp, nyp, __fmul_rn(nzp, nzp)));
-    const float rs = rsqrt_approx(nn);
-    PixelResult res;
-    res.valid = ev;
-    res.refine = ev && !flat && (refine_all || mbound > __fmul_rn(thr, __fmul_rn(nn, rs)));
-    res.x = ev && !flat ? -__fmul_rn(nxp, rs) : 0.f;
-    res.y = ev && !flat ? -__fmul_rn(nyp, rs) : 0.f;
-    res.z = ev ? (flat ? -1.f : -__fmul_rn(nzp, rs)) : 0.f;
-    return res;
 }
 
-// Double-float recomputation of the pixel whose 3x3 window starts at
-// element `base` of the tile in shared memory (the tile is still resident:
-// its buffer is released only after the refinement).  One call site keeps
-// the rare path out of the main instruction stream.
-template <int KIND, int GRAD, int PHI>
-__device__ __noinline__ Vec3 refine_from_tile(const void *tile, int base, int SW, int u, int v, float fx, float fy,
-                                              float u0, float v0)
+// Reads row `jr` of a staged box (BOXW samples per row, the lane's pixels at
+// column PADX + 4 lane) and decodes it.
+template <int KIND, int GRAD, int BOXW, int PADX>
+__device__ __forceinline__ void load_row(const unsigned char *stage, int jr, int lane, Row<KIND, GRAD> &R)
 {
     typedef typename KindTraits<KIND>::T T;
-    const T *t = reinterpret_cast<const T *>(tile) + base;
-    float z[9];
-    unsigned okbits = 0;
+    const T *p = reinterpret_cast<const T *>(stage) + jr * BOXW + PADX + 4 * lane;
+    T raw[6];
+    raw[0] = p[-1];
+    if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        raw[1] = q.x;
+        raw[2] = q.y;
+        raw[3] = q.z;
+        raw[4] = q.w;
+    } else {
+        const uint2 q = *reinterpret_cast<const uint2 *>(p);
+        raw[1] = from_bits16<T>(q.x & 0xffffu);
+        raw[2] = from_bits16<T>(q.x >> 16);
+        raw[3] = from_bits16<T>(q.y & 0xffffu);
+        raw[4] = from_bits16<T>(q.y >> 16);
+    }
+    raw[5] = p[4];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 6; ++c) R.z[c] = decode<KIND>(raw[c]);
+    if constexpr (Row<KIND, GRAD>::kW) {
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            bool ok;
-            z[3 * a + b] = decode<KIND>(t[a * SW + b], ok);
-            okbits |= (unsigned)ok << (3 * a + b);
+        for (int c = 0; c < 6; ++c) {
+            const float wh = rcp_approx(R.z[c]);
+            R.wh[c] = wh;
+            R.wl[c] = __fmul_rn(__fmaf_rn(-wh, R.z[c], 1.f), wh);
         }
-    return refine_pixel<KIND, GRAD, PHI>(z[0], z[1], z[2], z[3], z[4], z[5], z[6], z[7], z[8], okbits, u, v, fx, fy, u0,
-                                         v0);
+    }
 }
 
-// Bit c (1..4) set iff pixel column c of window row a is evaluable: the centre
-// and every tap of both filters valid.
-template <int GRAD, int KIND, int ROWS>
-__device__ __forceinline__ unsigned evaluable_row(const Win<KIND, ROWS> &W, int a)
+// FD gradient term between taps a (the -1 side) and b (the +1 side), as
+// h + l.  Depth: 1/Z_b - 1/Z_a = d / P with d = Z_a - Z_b (exact for
+// neighbouring depths within a factor 2) and P = Z_a Z_b; h = d rcp(P), and l
+// is h's residual against the exact product P + Pe divided by P, so h + l is
+// the quotient to about u^2 relative, as a difference of compensated
+// reciprocals would be.  h is 0 exactly when the taps are equal.  Disparity:
+// d_b - d_a (exact for integer samples; TwoSum for float ones).
+template <int KIND>
+__device__ __forceinline__ df fd_term(float a, float b)
 {
-    const unsigned m = W.ok[a];
-    if (GRAD == GRAD_FD) return m & (m >> 1) & (m << 1) & W.ok[a - 1] & W.ok[a + 1];
-    const unsigned t = W.ok[a - 1] & m & W.ok[a + 1];
-    return t & (t >> 1) & (t << 1);
+    if constexpr (KindTraits<KIND>::disparity) {
+        if constexpr (KindTraits<KIND>::exact_diff) return {__fsub_rn(b, a), 0.f};
+        return two_sum(b, -a);
+    } else {
+        const float d = __fsub_rn(a, b);
+        const float P = __fmul_rn(a, b);
+        const float Pe = __fmaf_rn(a, b, -P);
+        const float r = rcp_approx(P);
+        const float q = __fmul_rn(d, r);
+        const float e = __fmaf_rn(-q, Pe, __fmaf_rn(-q, P, d));
+        return {q, __fmul_rn(e, r)};
+    }
 }
 
+// Exact difference of two compensated taps, w_b - w_a as h + l.
+template <int KIND, int GRAD>
+__device__ __forceinline__ df tap_diff(const Row<KIND, GRAD> &A, int ca, const Row<KIND, GRAD> &B, int cb)
+{
+    if constexpr (KindTraits<KIND>::disparity) {
+        if constexpr (KindTraits<KIND>::exact_diff) return {__fsub_rn(B.z[cb], A.z[ca]), 0.f};
+        return two_sum(B.z[cb], -A.z[ca]);
+    } else {
+        const float lo = __fsub_rn(B.wl[cb], A.wl[ca]);
+        const df h = two_sum(B.wh[cb], -A.wh[ca]);
+        return {h.h, __fadd_rn(h.l, lo)};
+    }
+}
+
+// rho of the two end pixels of an edge p -> q (p first in raster order),
+// r = 1/(s_q - s_p): rho_fwd is q's rho seen from p, rho_bwd is p's rho seen
+// from q.  Depth: rho_j = Z_j / (Z_j - Z_i); disparity: d_i / (d_i - d_j).
+template <int KIND>
+__device__ __forceinline__ float rho_fwd(float sp, float sq, float r)
+{
+    if constexpr (KindTraits<KIND>::disparity)
+        return -__fmul_rn(sp, r);
+    else
+        return __fmul_rn(sq, r);
+}
+template <int KIND>
+__device__ __forceinline__ float rho_bwd(float sp, float sq, float r)
+{
+    if constexpr (KindTraits<KIND>::disparity)
+        return __fmul_rn(sq, r);
+    else
+        return -__fmul_rn(sp, r);
+}
+
+// rho of the neighbours above a row's 4 pixels, known from the previous row
+// pair: up, up-left, up-right, and how many of the three are kept.
+struct UpCarry {
+    float ru[4], rul[4], rur[4], ku[4];
+};
+
+// Edges between sample rows C (above) and N (below) as seen from N's pixels:
+// the carry for the row of N.
+template <int KIND, int GRAD>
+__device__ __forceinline__ void carry_down(const Row<KIND, GRAD> &C, const Row<KIND, GRAD> &N, UpCarry &cy)
+{
+#pragma unroll
+    for (int c = 1; c <= 4; ++c) {
+        const EdgeR v = edge_recip(__fsub_rn(N.z[c], C.z[c]));          // (y, c)   -> (y+1, c)
+        const EdgeR d = edge_recip(__fsub_rn(N.z[c], C.z[c - 1]));      // (y, c-1) -> (y+1, c)
+        const EdgeR a = edge_recip(__fsub_rn(N.z[c], C.z[c + 1]));      // (y, c+1) -> (y+1, c)
+        cy.ru[c - 1] = rho_bwd<KIND>(C.z[c], N.z[c], v.r);
+        cy.rul[c - 1] = rho_bwd<KIND>(C.z[c - 1], N.z[c], d.r);
+        cy.rur[c - 1] = rho_bwd<KIND>(C.z[c + 1], N.z[c], a.r);
+        cy.ku[c - 1] = __fadd_rn(__fadd_rn(v.k, d.k), a.k);
+    }
+}
+
+// One row of a lane's 4 pixels (Sec. III end to end), given the sample rows
+// above (P), at (C) and below (N) and the carry from the row above; leaves
+// the carry for the next row in `cy`.  Outputs the normal components, the
+// mask bits and the bits of the pixels whose FP32 error bound is too loose.
+// Every product is an explicit __fmul_rn and every fused multiply-add an
+// explicit __fmaf_rn (never a contraction), so a pixel's bits do not depend
+// on how the compiler schedules this code in a given instantiation.
+template <int KIND, int GRAD, int PHI>
+__device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIND, GRAD> &C, const Row<KIND, GRAD> &N,
+                                         UpCarry &cy, const float (&uc)[4], float vc, float fx, float fy, float thr,
+                                         bool refine_all, float (&ox)[4], float (&oy)[4], float (&oz)[4],
+                                         unsigned &evbits, unsigned &rbits)
+{
+    // edges of this row (c -> c+1) and to the row below
+    EdgeR h[5], ed[5], ea[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        h[c] = edge_recip(__fsub_rn(C.z[c + 1], C.z[c]));
+        ed[c] = edge_recip(__fsub_rn(N.z[c + 1], C.z[c]));  // (y, c)   -> (y+1, c+1)
+        ea[c] = edge_recip(__fsub_rn(N.z[c], C.z[c + 1]));  // (y, c+1) -> (y+1, c)
+    }
+    evbits = 0;
+    rbits = 0;
+#pragma unroll
+    for (int c = 1; c <= 4; ++c) {
+        const int k = c - 1;
+        const EdgeR ev = edge_recip(__fsub_rn(N.z[c], C.z[c]));  // (y, c) -> (y+1, c)
+        const float zi = C.z[c];
+        const float rr = rho_fwd<KIND>(zi, C.z[c + 1], h[c].r);
+        const float rl = rho_bwd<KIND>(C.z[c - 1], zi, h[c - 1].r);
+        const float rd = rho_fwd<KIND>(zi, N.z[c], ev.r);
+        const float rdr = rho_fwd<KIND>(zi, N.z[c + 1], ed[c].r);
+        const float rdl = rho_fwd<KIND>(zi, N.z[c - 1], ea[c - 1].r);
+        const float ru = cy.ru[k], rul = cy.rul[k], rur = cy.rur[k];
+        const float m = __fadd_rn(__fadd_rn(__fadd_rn(h[c].k, h[c - 1].k), __fadd_rn(ev.k, ed[c].k)),
+                                  __fadd_rn(ea[c - 1].k, cy.ku[k]));
+
+        // gradients (as h + l), the special case and evaluability
+        df Gu, Gv;
+        bool ev_ok;
+        if constexpr (GRAD == GRAD_FD) {
+            Gu = fd_term<KIND>(C.z[c - 1], C.z[c + 1]);
+            Gv = fd_term<KIND>(P.z[c], N.z[c]);
+            ev_ok = fmaxf(fmaxf(fmaxf(C.z[c - 1], zi), C.z[c + 1]), fmaxf(P.z[c], N.z[c])) <= kValidHi;
+        } else {
+            Gu = filter_sum<GRAD>(tap_diff(P, c - 1, P, c + 1), tap_diff(C, c - 1, C, c + 1),
+                                  tap_diff(N, c - 1, N, c + 1));
+            Gv = filter_sum<GRAD>(tap_diff(P, c - 1, N, c - 1), tap_diff(P, c, N, c), tap_diff(P, c + 1, N, c + 1));
+            const float mp = fmaxf(fmaxf(P.z[c - 1], P.z[c]), P.z[c + 1]);
+            const float mc = fmaxf(fmaxf(C.z[c - 1], zi), C.z[c + 1]);
+            const float mn = fmaxf(fmaxf(N.z[c - 1], N.z[c]), N.z[c + 1]);
+            ev_ok = fmaxf(fmaxf(mp, mc), mn) <= kValidHi;
+        }
+        // Sec. III special case: both gradients exactly zero (an h + l pair
+        // vanishes only when both parts do)
+        const bool flat = Gu.h == 0.f && Gu.l == 0.f && Gv.h == 0.f && Gv.l == 0.f;
+        // (a non-evaluable pixel's gradient may be NaN, from two hole taps: keep n' finite)
+        const float gu = ev_ok ? __fadd_rn(Gu.h, Gu.l) : 0.f, gv = ev_ok ? __fadd_rn(Gv.h, Gv.l) : 0.f;
+        // numerators of the diagonal pairs from the parts (they can cancel)
+        const float n2 = __fadd_rn(__fadd_rn(Gu.h, Gv.h), __fadd_rn(Gu.l, Gv.l));
+        const float n3 = __fadd_rn(__fsub_rn(Gu.h, Gv.h), __fsub_rn(Gu.l, Gv.l));
+
+        float mF, mbound, scale;
+        if constexpr (PHI == PHI_MEAN) {
+            // sum over the pairs (j, -j) of num_p (rho_j - rho_-j), carried
+            // unnormalised: n' scaled by m > 0 keeps its direction
+            const float S = __fmaf_rn(gu, __fsub_rn(rr, rl),
+                                      __fmaf_rn(gv, __fsub_rn(rd, ru),
+                                                __fmaf_rn(n2, __fsub_rn(rdr, rul), __fmul_rn(n3, __fsub_rn(rur, rdl)))));
+            // bound of the candidate sum's rounding: sum_p |num_p| (|rho_j| + |rho_-j|)
+            mbound = __fmaf_rn(fabsf(gu), __fadd_rn(fabsf(rr), fabsf(rl)),
+                               __fmaf_rn(fabsf(gv), __fadd_rn(fabsf(rd), fabsf(ru)),
+                                         __fmaf_rn(fabsf(n2), __fadd_rn(fabsf(rdr), fabsf(rul)),
+                                                   __fmul_rn(fabsf(n3), __fadd_rn(fabsf(rur), fabsf(rdl))))));
+            mF = S;
+            scale = m;
+        } else {
+            const float rho8[8] = {rr, rl, rd, ru, rdr, rul, rur, rdl};
+            const float num8[8] = {gu, -gu, gv, -gv, n2, -n2, n3, -n3};
+            float s[8];
+            unsigned sgn = 0;  // sign bit of the next sentinel: +inf, -inf, +inf, ...
+            int cnt = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const bool kept = rho8[q] != 0.f;
+                cnt += kept;
+                s[q] = kept ? __fmul_rn(num8[q], rho8[q]) : __uint_as_float(0x7f800000u | sgn);
+                sgn ^= kept ? 0u : 0x80000000u;
+            }
+#define TFN_CE(i, j)                         \
+    {                                        \
+        const float lo_ = fminf(s[i], s[j]); \
+        s[j] = fmaxf(s[i], s[j]);            \
+        s[i] = lo_;                          \
+    }
+            TFN_CE(0, 2) TFN_CE(1, 3) TFN_CE(4, 6) TFN_CE(5, 7)
+            TFN_CE(0, 4) TFN_CE(1, 5) TFN_CE(2, 6) TFN_CE(3, 7)
+            TFN_CE(0, 1) TFN_CE(2, 3) TFN_CE(4, 5) TFN_CE(6, 7)
+            TFN_CE(2, 4) TFN_CE(3, 5)
+            TFN_CE(1, 4) TFN_CE(3, 6)
+            TFN_CE(1, 2) TFN_CE(3, 4) TFN_CE(5, 6)
+#undef TFN_CE
+            const bool odd = cnt & 1;
+            mF = odd ? s[3] : __fmul_rn(0.5f, __fadd_rn(s[3], s[4]));
+            mbound = odd ? fabsf(s[3]) : fmaxf(fabsf(s[3]), fabsf(s[4]));
+            scale = 1.f;
+        }
+        const float A = __fmaf_rn(uc[k], gu, __fmul_rn(vc, gv));
+        const float nxp = __fmul_rn(__fmul_rn(scale, fx), gu), nyp = __fmul_rn(__fmul_rn(scale, fy), gv);
+        // (a non-evaluable pixel's median may be a +-inf sentinel: keep n' finite so that rs = 0 zeroes it)
+        const float nzp = (flat || !ev_ok) ? 1.f : -__fmaf_rn(scale, A, mF);
+        const float nn = __fmaf_rn(nxp, nxp, __fmaf_rn(nyp, nyp, __fmul_rn(nzp, nzp)));
+        const float rs = ev_ok ? rsqrt_approx(nn) : 0.f;
+        const bool refine = ev_ok && !flat &&
+                            (refine_all || mbound > __fmul_rn(thr, __fmul_rn(nn, rs)) || !(nn <= 1e38f));
+        // -n'/|n'|, with +0 (not -0) for zero components and for non-evaluable pixels
+        ox[k] = __fmaf_rn(-nxp, rs, 0.f);
+        oy[k] = __fmaf_rn(-nyp, rs, 0.f);
+        oz[k] = __fmaf_rn(-nzp, rs, 0.f);
+        evbits |= ev_ok ? 1u << k : 0u;
+        rbits |= refine ? 1u << k : 0u;
+
+        // the carry for the pixel below: its up, up-left and up-right neighbours
+        cy.ru[k] = rho_bwd<KIND>(zi, N.z[c], ev.r);
+        cy.rul[k] = rho_bwd<KIND>(C.z[c - 1], N.z[c], ed[c - 1].r);
+        cy.rur[k] = rho_bwd<KIND>(C.z[c + 1], N.z[c], ea[c].r);
+        cy.ku[k] = __fadd_rn(__fadd_rn(ev.k, ed[c - 1].k), ea[c].k);
+    }
+}
 
 // ------------------------------------------------------------ TMA / mbarrier
 
@@ -596,6 +639,11 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
@@ -619,7 +667,7 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase)
 
 // Bounded wait for the phase with parity `phase`; false if it did not
 // complete within kWaitCycles (the clock is read every 16 polls).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long limit = kWaitCycles)
 {
     if (mbar_try(bar, phase)) return true;
     const long long t0 = clock64();
@@ -627,7 +675,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase)
 #pragma unroll 1
         for (int k = 0; k < 16; ++k)
             if (mbar_try(bar, phase)) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -734,175 +782,224 @@ __device__ __forceinline__ void store1(const OutDesc &fd, int fmt, int u, int v,
     }
 }
 
-// ------------------------------------------------------------ the kernel
-
-// Persistent kernel, 8 warps.  CTA b takes tiles b, b + grid, b + 2 grid, ...
-// of the queue (interleaving spreads every CTA over all of memory).  Tile
-// buffers form a kStages-deep ring.  Whoever fills a buffer also writes the
-// tile's frame descriptor and origin into the buffer's info slot in shared
-// memory, then arrives on the buffer's "full" mbarrier with the TMA byte
-// count; consumers wait on it and read the slot, never global memory.  Every
-// warp bumps the buffer's release counter when done with it, and the warp
-// that completes the count refills it with the tile kStages ahead.  No warp
-// ever waits for another except for data.
-constexpr int kWarps = 8;
-constexpr int kThreads = kWarps * 32;
-
-struct StageInfo {
-    FrameDesc fd;
-    int x0, y0, tile;
-    int pad;
-};
-
-template <int KIND, int GRAD, int PHI, int CFG>
-__global__ void __launch_bounds__(kThreads, 2) normals_kernel(const __grid_constant__ LaunchArgs args)
+// The double-float path for pixel (x, y), reading its 3x3 window again from
+// the input image (taps outside the image and holes are invalid).  Called
+// for the rare refined pixels after a work item's rows are done, so that the
+// main loop never waits on it.
+template <int KIND, int GRAD, int PHI>
+__device__ __noinline__ Vec3 refine_from_input(const void *in, int64_t pitch, int H, int W, int x, int y, float fx,
+                                               float fy, float u0, float v0)
 {
     typedef typename KindTraits<KIND>::T T;
-    constexpr int TW = kCfgs[CFG].tw, TH = kCfgs[CFG].th, PR = kCfgs[CFG].pr;
+    float z[9];
+    unsigned okb = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int yy = y - 1 + a, xx = x - 1 + b;
+            float v = kHole;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                v = decode<KIND>(reinterpret_cast<const T *>(static_cast<const char *>(in) + (int64_t)yy * pitch)[xx]);
+            z[3 * a + b] = v;
+            okb |= (v <= kValidHi ? 1u : 0u) << (3 * a + b);
+        }
+    return refine_pixel<KIND, GRAD, PHI>(z[0], z[1], z[2], z[3], z[4], z[5], z[6], z[7], z[8], okb, x, y, fx, fy, u0,
+                                         v0);
+}
+
+// ------------------------------------------------------------ the kernel
+
+// Persistent kernel of independent warps.  The work item is a band of 128
+// pixel columns x TH rows of one frame (items are numbered frame by frame,
+// row band by row band, left to right); warp w of the grid takes items w,
+// w + W, w + 2W, ... (W warps in the grid).  A lane owns 4 adjacent columns
+// and rolls down the item's rows with three sample rows in registers, so the
+// edges between two rows are computed once for both.  Each warp streams its
+// items' rows through a ring of NST shared-memory stages of CR rows each
+// (box: 128 columns plus a 16-byte halo on each side), filled by TMA 2D
+// copies that lane 0 issues and completed on one mbarrier per stage; a stage
+// is refilled with the chunk NST ahead as soon as the warp has read its last
+// row.  No warp ever waits for another.  Rows at or below the frame's last
+// row read as holes, and so does the TMA zero fill above the first row and
+// beyond the right edge, so borders need no special case.
+template <int KIND, int GRAD, int PHI, int CFG>
+__global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __grid_constant__ LaunchArgs args)
+{
+    typedef typename KindTraits<KIND>::T T;
+    typedef Row<KIND, GRAD> R;
+    constexpr int TH = kCfgs[CFG].th, CR = kCfgs[CFG].cr, NST = kCfgs[CFG].nst, NW = kCfgs[CFG].warps;
+    constexpr int NCH = (TH + 2) / CR;  // chunks per item: rows y0-1 .. y0+TH
+    static_assert((TH + 2) % CR == 0 && NCH >= 1, "chunks must tile an item's rows");
+    static_assert(kCfgs[CFG].tw == 128, "a band is 32 lanes x 4 columns");
+    static_assert(TH <= 32, "pending-refinement bits hold 32 rows");
     constexpr int PADX = 16 / (int)sizeof(T);
-    constexpr int SW = TW + 2 * PADX, SH = TH + 2;
-    constexpr uint32_t BOX_BYTES = SW * SH * sizeof(T);
-    constexpr uint32_t STRIDE = (BOX_BYTES + 1023) & ~1023u;
-    constexpr int TPR = TW / 4;
-    static_assert(TPR * (TH / PR) == kThreads, "tile shape must match the block");
+    constexpr int BOXW = 128 + 2 * PADX;
+    constexpr uint32_t BOX_BYTES = BOXW * CR * sizeof(T);
+    constexpr uint32_t STRIDE = (BOX_BYTES + 127) & ~127u;
 
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long full[kStages];
-    __shared__ int released[kStages];
-    __shared__ __align__(16) StageInfo info[kStages];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-    // The launch's frame table, copied once into shared memory when it fits,
-    // so that refilling a buffer never waits on global memory.
-    FrameDesc *ftab = reinterpret_cast<FrameDesc *>(smem + kStages * STRIDE);
-    const bool ftab_smem = args.nframes <= kFrameTableMax;
-    const FrameDesc *frames = ftab_smem ? ftab : args.frames;
-
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int total = args.total_tiles, first = blockIdx.x, step = gridDim.x;
-
-    if (ftab_smem) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(args.frames);
-        uint4 *dst = reinterpret_cast<uint4 *>(ftab);
-        const int words = args.nframes * (int)(sizeof(FrameDesc) / 16);
-        for (int k = tid; k < words; k += kThreads) dst[k] = __ldg(src + k);
-    }
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(smem_addr(&full[s]), 1);
-            released[s] = 0;
-        }
+    __shared__ __align__(8) unsigned long long full[NW][NST];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // (an offset from smem_raw keeps the compiler's knowledge that this is shared memory)
+    unsigned char *ring = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u) + warp * NST * STRIDE;
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < NST; ++s) mbar_init(smem_addr(&full[warp][s]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_async_shared();
     }
-    __syncthreads();
+    __syncwarp();
 
-    // Filling side (whichever lane fills a buffer): frame cursor, last fenced map.
+    const int gw = blockIdx.x * NW + warp, nw = gridDim.x * NW, total = args.total_tiles;
+
+    // Producer (lane 0): chunk number cc of this warp's sequence is chunk
+    // cc % NCH of its (cc / NCH)-th item and goes to stage cc % NST.
     int pf = 0, fenced = -1;
-    auto fill = [&](int t, int s) {
-        while (pf + 1 < args.nframes && frames[pf + 1].tile_begin <= t) ++pf;
-        const CUtensorMap *map = args.maps + pf;
-        if (pf != fenced) {
-            fence_tensormap_acquire(map);
-            fenced = pf;
+    auto issue = [&](int cc) {
+        const int t = gw + (cc / NCH) * nw;
+        if (t >= total) return;
+        while (pf + 1 < args.nframes && __ldg(&args.frames[pf + 1].tile_begin) <= t) ++pf;
+        const FrameDesc *f = args.frames + pf;
+        const int lt = t - __ldg(&f->tile_begin), txs = __ldg(&f->tiles_x);
+        const int x = (lt % txs) * 128 - PADX;
+        const int y = (lt / txs) * TH - 1 + (cc % NCH) * CR;
+        const uint32_t bar = smem_addr(&full[warp][cc % NST]);
+        if (y < __ldg(&f->H)) {
+            const CUtensorMap *map = args.maps + pf;
+            if (pf != fenced) {
+                fence_tensormap_acquire(map);
+                fenced = pf;
+            }
+            mbar_expect_tx(bar, BOX_BYTES);
+            tma_load_2d(smem_addr(ring + (cc % NST) * STRIDE), map, x, y, bar);
+        } else {
+            mbar_arrive(bar);  // every row of this chunk is past the bottom: nothing to copy
         }
-        StageInfo &si = info[s];
-        const uint4 *src = reinterpret_cast<const uint4 *>(frames + pf);
-        uint4 *dst = reinterpret_cast<uint4 *>(&si.fd);
-#pragma unroll
-        for (int k = 0; k < (int)(sizeof(FrameDesc) / 16); ++k) dst[k] = src[k];
-        const int lt = t - si.fd.tile_begin;
-        const int txs = si.fd.tiles_x;
-        si.x0 = (lt % txs) * TW;
-        si.y0 = (lt / txs) * TH;
-        si.tile = t;
-        const uint32_t bar = smem_addr(&full[s]);
-        mbar_expect_tx(bar, BOX_BYTES);  // release: the info slot is visible with the phase
-        tma_load_2d(smem_addr(smem + s * STRIDE), map, si.x0 - PADX, si.y0 - 1, bar);
     };
-    if (tid == 0)
-        for (int s = 0; s < kStages; ++s)
-            if (first + s * step < total) fill(first + s * step, s);
+    if (lane == 0)
+#pragma unroll
+        for (int cc = 0; cc < NST; ++cc) issue(cc);
 
-    const int tx = tid % TPR, ty = tid / TPR;
-    const bool refine_all = args.flags & 1;
-    for (int i = 0;; ++i) {
-        const int t = first + i * step;
+    const bool refine_all = args.flags & TFN_FLAG_REFINE_ALL;
+    int cf = 0, fail_cc = 0;
+    unsigned nref = 0;
+    bool failed = false;
+    for (int i = 0; !failed; ++i) {
+        const int t = gw + i * nw;
         if (t >= total) break;
-        const int s = i % kStages;
-        const bool arrived = __all_sync(0xffffffffu, mbar_wait(smem_addr(&full[s]), (uint32_t)((i / kStages) & 1)));
-        if (!arrived) {
-            if (lane == 0) atomicOr(args.status, DEVERR_TMA_WAIT);
-            return;
-        }
-        unsigned pending = 0;  // pixels (pr * 4 + c) that need the double-float path
-        const StageInfo &si = info[s];
-        const FrameDesc &fd = si.fd;
-        const int W = fd.W, H = fd.H;
+        while (cf + 1 < args.nframes && __ldg(&args.frames[cf + 1].tile_begin) <= t) ++cf;
+        const FrameDesc *f = args.frames + cf;
         OutDesc out;
-        out.out = fd.out;
-        out.out_pitch = fd.out_pitch;
-        out.out_plane = fd.out_plane;
-        out.mask = fd.mask;
-        out.mask_pitch = fd.mask_pitch;
-        const int x0 = si.x0 + 4 * tx;
-        const int y0 = si.y0 + PR * ty;
-        if (x0 < W && y0 < H) {
-            const float fx = fd.fx, fy = fd.fy, u0 = fd.u0, v0 = fd.v0, thr = fd.thr;
-            Win<KIND, PR> win;
-            load_window<KIND, PR>(smem + s * STRIDE, SW, PADX, PR * ty, 4 * tx, win);
-            const int nvalid = min(4, W - x0);
+        out.out = (char *)__ldg((const unsigned long long *)&f->out);
+        out.out_pitch = __ldg(&f->out_pitch);
+        out.out_plane = __ldg(&f->out_plane);
+        out.mask = (uint8_t *)__ldg((const unsigned long long *)&f->mask);
+        out.mask_pitch = __ldg(&f->mask_pitch);
+        const int H = __ldg(&f->H), W = __ldg(&f->W), txs = __ldg(&f->tiles_x);
+        const float fx = __ldg(&f->fx), fy = __ldg(&f->fy), u0 = __ldg(&f->u0), v0 = __ldg(&f->v0);
+        const float thr = __ldg(&f->thr);
+        const void *in = (const void *)__ldg((const unsigned long long *)&f->in);
+        const int64_t in_pitch = __ldg(&f->in_pitch);
+        const int lt = t - __ldg(&f->tile_begin);
+        const int x0 = (lt % txs) * 128 + 4 * lane, y0 = (lt / txs) * TH;
+        const int nvalid = min(4, W - x0);  // pixels of this lane inside the frame (may be <= 0)
+        float uc[4];
 #pragma unroll
-            for (int pr = 0; pr < PR; ++pr) {
-                const int v = y0 + pr;
-                const unsigned evm = evaluable_row<GRAD, KIND, PR>(win, pr + 1);
-                float ox[4], oy[4], oz[4];
-                uint8_t mk[4];
-                unsigned rbits = 0;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const PixelResult r = pixel_normal<KIND, GRAD, PHI, PR>(win, evm, pr + 1, c + 1, x0 + c, v, fx, fy,
-                                                                            u0, v0, thr, refine_all);
-                    ox[c] = r.x;
-                    oy[c] = r.y;
-                    oz[c] = r.z;
-                    mk[c] = r.valid ? 1 : 0;
-                    rbits |= r.refine ? 1u << c : 0u;
-                }
-                if (v < H) {
-                    store4(out, args.out_fmt, x0, v, nvalid, ox, oy, oz, mk);
-                    pending |= (rbits & ((1u << nvalid) - 1u)) << (pr * 4);
-                }
+        for (int k = 0; k < 4; ++k) uc[k] = __fsub_rn((float)(x0 + k), u0);
+
+        // sample row j (0 .. TH+1) of the item is image row y0 - 1 + j
+        auto fetch = [&](int j, R &row) -> bool {
+            const int q = j / CR, jr = j - q * CR;
+            const int cc = i * NCH + q;
+            const unsigned char *stage = ring + (cc % NST) * STRIDE;
+            if (jr == 0 && !__all_sync(0xffffffffu, mbar_wait(smem_addr(&full[warp][cc % NST]), (uint32_t)((cc / NST) & 1)))) {
+                fail_cc = cc;
+                return false;
             }
-            // Deferred refinement: rare, so it runs after the stores and off the
-            // main instruction stream; a later store to the same pixel wins.
-            unsigned todo = pending;
-            while (todo) {
-                const int b = __ffs(todo) - 1;
-                todo &= todo - 1;
-                const int pr = b >> 2, c = b & 3;
-                const Vec3 n = refine_from_tile<KIND, GRAD, PHI>(smem + s * STRIDE, (PR * ty + pr) * SW + PADX + 4 * tx + c - 1,
-                                                                 SW, x0 + c, y0 + pr, fx, fy, u0, v0);
-                store1(out, args.out_fmt, x0 + c, y0 + pr, n);
-            }
-        }
-        // count of refined pixels (diagnostics): one atomic per warp, only if any
-        const unsigned nref = __reduce_add_sync(0xffffffffu, (unsigned)__popc(pending));
-        if (lane == 0 && nref) atomicAdd(args.status + 1, nref);
-        // release the buffer; the last warp out refills it
-        __syncwarp();
-        if (lane == 0) {
-            __threadfence_block();
-            if (atomicAdd(&released[s], 1) == kWarps - 1) {
-                released[s] = 0;
-                __threadfence_block();
-                const int tn = t + kStages * step;
-                if (tn < total) {
+            if (y0 - 1 + j < H)
+                load_row<KIND, GRAD, BOXW, PADX>(stage, jr, lane, row);
+            else
+                hole_row(row);
+            if (jr == CR - 1) {  // the stage's last row is in registers: refill it
+                __syncwarp();
+                if (lane == 0) {
                     fence_async_shared();
-                    fill(tn, s);
+                    issue(cc + NST);
                 }
             }
+            return true;
+        };
+
+        unsigned long long pend_a = 0, pend_b = 0;  // bit 4 s + k: row y0 + s, column x0 + k
+        R P, C, N;
+        if (!fetch(0, C) || !fetch(1, N)) {
+            failed = true;
+            break;
+        }
+        UpCarry cy;
+        carry_down(C, N, cy);
+        P = C;
+        C = N;
+        for (int s = 0; s < TH; ++s) {
+            if (!fetch(s + 2, N)) {
+                failed = true;
+                break;
+            }
+            const int y = y0 + s;
+            float ox[4], oy[4], oz[4];
+            unsigned evb, rb;
+            row_step<KIND, GRAD, PHI>(P, C, N, cy, uc, __fsub_rn((float)y, v0), fx, fy, thr, refine_all, ox, oy, oz,
+                                      evb, rb);
+            if (y < H && nvalid > 0) {
+                const uint8_t mk[4] = {(uint8_t)(evb & 1u), (uint8_t)((evb >> 1) & 1u), (uint8_t)((evb >> 2) & 1u),
+                                       (uint8_t)((evb >> 3) & 1u)};
+                store4(out, args.out_fmt, x0, y, nvalid, ox, oy, oz, mk);
+                rb &= (1u << min(nvalid, 4)) - 1u;
+            } else {
+                rb = 0;
+            }
+            // pixels whose FP32 error bound is too loose: redone after the item
+            if (s < 16)
+                pend_a |= (unsigned long long)rb << (4 * s);
+            else
+                pend_b |= (unsigned long long)rb << (4 * (s - 16));
+            P = C;
+            C = N;
+        }
+        if (failed) break;
+        // Rare: the double-float path for this item's flagged pixels (lanes in
+        // parallel); the later store to the same pixel wins.
+        while (pend_a | pend_b) {
+            int b;
+            if (pend_a) {
+                b = __ffsll((long long)pend_a) - 1;
+                pend_a &= pend_a - 1;
+            } else {
+                b = 64 + __ffsll((long long)pend_b) - 1;
+                pend_b &= pend_b - 1;
+            }
+            const int x = x0 + (b & 3), y = y0 + (b >> 2);
+            store1(out, args.out_fmt, x, y,
+                   refine_from_input<KIND, GRAD, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0));
+            ++nref;
         }
     }
+    if (failed) {
+        // a copy did not land in time: flag it, then give the copies this warp
+        // may still have in flight a short bounded wait before leaving
+        if (lane == 0) {
+            atomicOr(args.status, DEVERR_TMA_WAIT);
+            for (int cc = fail_cc; cc < fail_cc + NST; ++cc)
+                if (gw + (cc / NCH) * nw < total)
+                    mbar_wait(smem_addr(&full[warp][cc % NST]), (uint32_t)((cc / NST) & 1), kDrainCycles);
+        }
+        __syncwarp();
+        return;
+    }
+    // count of refined pixels (diagnostics): one atomic per warp, only if any
+    const unsigned tot = __reduce_add_sync(0xffffffffu, nref);
+    if (lane == 0 && tot) atomicAdd(args.status + 1, tot);
 }
 
 template <int KIND>

@@ -88,7 +88,7 @@ extern "C" tfn_status tfn_normals_noalloc(const tfn_frame *frames, int n, const 
     for (int i = 0; i < n; ++i) {
         if (i > 0 && frames[i].input_type != frames[i - 1].input_type)
             tb = 0;  // a new launch (input kind) starts its own tile queue
-        h.desc[i] = describe_frame(frames[i], cfg, method->phi, tb);
+        h.desc[i] = describe_frame(frames[i], cfg, *method, tb);
         tb += frame_tiles(frames[i], cfg);
         if ((st = encode_map(&h.maps[i], frames[i], cfg))) return st;
     }

@@ -512,8 +512,8 @@ __device__ __forceinline__ void carry_down(const Row<KIND, GRAD> &C, const Row<K
 template <int KIND, int GRAD, int PHI>
 __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIND, GRAD> &C, const Row<KIND, GRAD> &N,
                                          UpCarry &cy, const float (&uc)[4], float vc, float fx, float fy, float thr,
-                                         bool refine_all, float (&ox)[4], float (&oy)[4], float (&oz)[4],
-                                         unsigned &evbits, unsigned &rbits)
+                                         float (&ox)[4], float (&oy)[4], float (&oz)[4], uint32_t &mword,
+                                         unsigned &rbits)
 {
     // edges of this row (c -> c+1) and to the row below
     EdgeR h[5], ed[5], ea[5];
@@ -523,7 +523,7 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
         ed[c] = edge_recip(__fsub_rn(N.z[c + 1], C.z[c]));  // (y, c)   -> (y+1, c+1)
         ea[c] = edge_recip(__fsub_rn(N.z[c], C.z[c + 1]));  // (y, c+1) -> (y+1, c)
     }
-    evbits = 0;
+    mword = 0;
     rbits = 0;
 #pragma unroll
     for (int c = 1; c <= 4; ++c) {
@@ -557,7 +557,11 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
         }
         // Sec. III special case: both gradients exactly zero (an h + l pair
         // vanishes only when both parts do)
-        const bool flat = Gu.h == 0.f && Gu.l == 0.f && Gv.h == 0.f && Gv.l == 0.f;
+        bool flat;
+        if constexpr (GRAD == GRAD_FD)
+            flat = Gu.h == 0.f && Gv.h == 0.f;  // an FD term's low part is 0 whenever its high part is
+        else
+            flat = Gu.h == 0.f && Gu.l == 0.f && Gv.h == 0.f && Gv.l == 0.f;
         // (a non-evaluable pixel's gradient may be NaN, from two hole taps: keep n' finite)
         const float gu = ev_ok ? __fadd_rn(Gu.h, Gu.l) : 0.f, gv = ev_ok ? __fadd_rn(Gv.h, Gv.l) : 0.f;
         // numerators of the diagonal pairs from the parts (they can cancel)
@@ -615,13 +619,14 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
         const float nzp = (flat || !ev_ok) ? 1.f : -__fmaf_rn(scale, A, mF);
         const float nn = __fmaf_rn(nxp, nxp, __fmaf_rn(nyp, nyp, __fmul_rn(nzp, nzp)));
         const float rs = ev_ok ? rsqrt_approx(nn) : 0.f;
-        const bool refine = ev_ok && !flat &&
-                            (refine_all || mbound > __fmul_rn(thr, __fmul_rn(nn, rs)) || !(nn <= 1e38f));
+        // refine unless bound <= thr |n'|; written so that a NaN (|n'|
+        // overflowed) also refines, and thr < 0 refines every pixel
+        const bool refine = ev_ok && !flat && !(mbound <= __fmul_rn(thr, __fmul_rn(nn, rs)));
         // -n'/|n'|, with +0 (not -0) for zero components and for non-evaluable pixels
         ox[k] = __fmaf_rn(-nxp, rs, 0.f);
         oy[k] = __fmaf_rn(-nyp, rs, 0.f);
         oz[k] = __fmaf_rn(-nzp, rs, 0.f);
-        evbits |= ev_ok ? 1u << k : 0u;
+        mword |= ev_ok ? 1u << (8 * k) : 0u;
         rbits |= refine ? 1u << k : 0u;
 
         // the carry for the pixel below: its up, up-left and up-right neighbours
@@ -717,7 +722,7 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, int fmt)
 
 // Stores 4 consecutive pixels (n valid of them, starting at column u).
 __device__ __forceinline__ void store4(const OutDesc &fd, int fmt, int u, int v, int n, const float (&x)[4],
-                                       const float (&y)[4], const float (&zz)[4], const uint8_t (&mk)[4])
+                                       const float (&y)[4], const float (&zz)[4], uint32_t mw)
 {
     char *row = fd.out + (int64_t)v * fd.out_pitch;
     uint8_t *mrow = fd.mask + (int64_t)v * fd.mask_pitch;
@@ -741,7 +746,6 @@ __device__ __forceinline__ void store4(const OutDesc &fd, int fmt, int u, int v,
             __stcs(reinterpret_cast<uint4 *>(row + (int64_t)u * 8), a);
             __stcs(reinterpret_cast<uint4 *>(row + (int64_t)u * 8 + 16), b);
         }
-        const uint32_t mw = (uint32_t)mk[0] | ((uint32_t)mk[1] << 8) | ((uint32_t)mk[2] << 16) | ((uint32_t)mk[3] << 24);
         __stcs(reinterpret_cast<unsigned int *>(mrow + u), mw);
         return;
     }
@@ -759,7 +763,7 @@ __device__ __forceinline__ void store4(const OutDesc &fd, int fmt, int u, int v,
         } else {
             reinterpret_cast<uint2 *>(row)[uu] = make_uint2(pack2(x[k], y[k], fmt), pack2(zz[k], 0.f, fmt));
         }
-        mrow[uu] = mk[k];
+        mrow[uu] = (uint8_t)(mw >> (8 * k));
     }
 }
 
@@ -881,7 +885,7 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
 #pragma unroll
         for (int cc = 0; cc < NST; ++cc) issue(cc);
 
-    const bool refine_all = args.flags & TFN_FLAG_REFINE_ALL;
+    const bool refine_all = args.flags & TFN_FLAG_REFINE_ALL;  // a negative threshold refines every pixel
     int cf = 0, fail_cc = 0;
     unsigned nref = 0;
     bool failed = false;
@@ -898,7 +902,7 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
         out.mask_pitch = __ldg(&f->mask_pitch);
         const int H = __ldg(&f->H), W = __ldg(&f->W), txs = __ldg(&f->tiles_x);
         const float fx = __ldg(&f->fx), fy = __ldg(&f->fy), u0 = __ldg(&f->u0), v0 = __ldg(&f->v0);
-        const float thr = __ldg(&f->thr);
+        const float thr = refine_all ? -1.f : __ldg(&f->thr);
         const void *in = (const void *)__ldg((const unsigned long long *)&f->in);
         const int64_t in_pitch = __ldg(&f->in_pitch);
         const int lt = t - __ldg(&f->tile_begin);
@@ -908,53 +912,49 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
 #pragma unroll
         for (int k = 0; k < 4; ++k) uc[k] = __fsub_rn((float)(x0 + k), u0);
 
-        // sample row j (0 .. TH+1) of the item is image row y0 - 1 + j
-        auto fetch = [&](int j, R &row) -> bool {
-            const int q = j / CR, jr = j - q * CR;
-            const int cc = i * NCH + q;
-            const unsigned char *stage = ring + (cc % NST) * STRIDE;
-            if (jr == 0 && !__all_sync(0xffffffffu, mbar_wait(smem_addr(&full[warp][cc % NST]), (uint32_t)((cc / NST) & 1)))) {
-                fail_cc = cc;
-                return false;
+        // Sample row j (0 .. TH+1) of the item is image row y0 - 1 + j; rows
+        // at or past the bottom read as holes.  The rows arrive in order, so
+        // the chunk state advances incrementally: row jr of chunk cc.
+        const int rows_in = H - (y0 - 1);
+        int jr = 0, cc = i * NCH;
+        const unsigned char *stage = ring;
+        auto fetch = [&](R &row, int j) -> bool {
+            if (jr == 0) {
+                const int st = cc % NST;
+                stage = ring + st * STRIDE;
+                if (!__all_sync(0xffffffffu, mbar_wait(smem_addr(&full[warp][st]), (uint32_t)((cc / NST) & 1)))) {
+                    fail_cc = cc;
+                    return false;
+                }
             }
-            if (y0 - 1 + j < H)
+            if (j < rows_in)
                 load_row<KIND, GRAD, BOXW, PADX>(stage, jr, lane, row);
             else
                 hole_row(row);
-            if (jr == CR - 1) {  // the stage's last row is in registers: refill it
+            if (++jr == CR) {  // the stage's last row is in registers: refill it
                 __syncwarp();
                 if (lane == 0) {
                     fence_async_shared();
                     issue(cc + NST);
                 }
+                jr = 0;
+                ++cc;
             }
             return true;
         };
 
         unsigned long long pend_a = 0, pend_b = 0;  // bit 4 s + k: row y0 + s, column x0 + k
-        R P, C, N;
-        if (!fetch(0, C) || !fetch(1, N)) {
-            failed = true;
-            break;
-        }
         UpCarry cy;
-        carry_down(C, N, cy);
-        P = C;
-        C = N;
-        for (int s = 0; s < TH; ++s) {
-            if (!fetch(s + 2, N)) {
-                failed = true;
-                break;
-            }
+        // output row y0 + s from sample rows P (above), C and N (below, fetched here)
+        auto step = [&](const R &P, const R &C, R &N, int s) -> bool {
+            if (!fetch(N, s + 2)) return false;
             const int y = y0 + s;
             float ox[4], oy[4], oz[4];
-            unsigned evb, rb;
-            row_step<KIND, GRAD, PHI>(P, C, N, cy, uc, __fsub_rn((float)y, v0), fx, fy, thr, refine_all, ox, oy, oz,
-                                      evb, rb);
+            uint32_t mw;
+            unsigned rb;
+            row_step<KIND, GRAD, PHI>(P, C, N, cy, uc, __fsub_rn((float)y, v0), fx, fy, thr, ox, oy, oz, mw, rb);
             if (y < H && nvalid > 0) {
-                const uint8_t mk[4] = {(uint8_t)(evb & 1u), (uint8_t)((evb >> 1) & 1u), (uint8_t)((evb >> 2) & 1u),
-                                       (uint8_t)((evb >> 3) & 1u)};
-                store4(out, args.out_fmt, x0, y, nvalid, ox, oy, oz, mk);
+                store4(out, args.out_fmt, x0, y, nvalid, ox, oy, oz, mw);
                 rb &= (1u << min(nvalid, 4)) - 1u;
             } else {
                 rb = 0;
@@ -964,6 +964,23 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
                 pend_a |= (unsigned long long)rb << (4 * s);
             else
                 pend_b |= (unsigned long long)rb << (4 * (s - 16));
+            return true;
+        };
+        R P, C, N;
+        if (!fetch(C, 0) || !fetch(N, 1)) {
+            failed = true;
+            break;
+        }
+        carry_down(C, N, cy);
+        P = C;
+        C = N;
+        // (a rolled loop: unrolling it to rotate the roles of P, C, N costs
+        // more in instruction fetch than the row copies it saves)
+        for (int s = 0; s < TH; ++s) {
+            if (!step(P, C, N, s)) {
+                failed = true;
+                break;
+            }
             P = C;
             C = N;
         }

@@ -515,19 +515,20 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
                                          float (&ox)[4], float (&oy)[4], float (&oz)[4], uint32_t &mword,
                                          unsigned &rbits)
 {
-    // edges of this row (c -> c+1) and to the row below
+    // edges of this row (c -> c+1) and to the row below, computed pixel by
+    // pixel: pixel c needs those of columns c-1 and c only
     EdgeR h[5], ed[5], ea[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-        h[c] = edge_recip(__fsub_rn(C.z[c + 1], C.z[c]));
-        ed[c] = edge_recip(__fsub_rn(N.z[c + 1], C.z[c]));  // (y, c)   -> (y+1, c+1)
-        ea[c] = edge_recip(__fsub_rn(N.z[c], C.z[c + 1]));  // (y, c+1) -> (y+1, c)
-    }
+    h[0] = edge_recip(__fsub_rn(C.z[1], C.z[0]));
+    ed[0] = edge_recip(__fsub_rn(N.z[1], C.z[0]));  // (y, 0) -> (y+1, 1)
+    ea[0] = edge_recip(__fsub_rn(N.z[0], C.z[1]));  // (y, 1) -> (y+1, 0)
     mword = 0;
     rbits = 0;
 #pragma unroll
     for (int c = 1; c <= 4; ++c) {
         const int k = c - 1;
+        h[c] = edge_recip(__fsub_rn(C.z[c + 1], C.z[c]));
+        ed[c] = edge_recip(__fsub_rn(N.z[c + 1], C.z[c]));  // (y, c)   -> (y+1, c+1)
+        ea[c] = edge_recip(__fsub_rn(N.z[c], C.z[c + 1]));  // (y, c+1) -> (y+1, c)
         const EdgeR ev = edge_recip(__fsub_rn(N.z[c], C.z[c]));  // (y, c) -> (y+1, c)
         const float zi = C.z[c];
         const float rr = rho_fwd<KIND>(zi, C.z[c + 1], h[c].r);

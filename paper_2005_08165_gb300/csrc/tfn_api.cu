@@ -389,6 +389,57 @@ tfn_status run_batch(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_metho
 
 }  // namespace tfn
 
+namespace {
+
+// Queues the copies of one direction on one stream, merging a copy into the
+// previous one when both of its ends start exactly where the previous one's
+// full extent ends.  A batch of same-size frames laid out back to back on
+// both sides then costs one large copy per direction and chunk instead of one
+// per frame and plane, which is what bounds the host path otherwise (each
+// call costs microseconds of CPU).  The padding after the last row of the
+// last merged copy is left out, so no copy reads or writes past a buffer.
+// When the destination is the caller's memory (`exact_rows`), only rows
+// without padding merge: a pitched view's padding may belong to other data.
+struct CopyQueue {
+    cudaMemcpyKind kind;
+    cudaStream_t stream;
+    bool exact_rows;
+    char *dst = nullptr;
+    const char *src = nullptr;
+    size_t extent = 0, trim = 0;
+    bool ok = true;
+
+    CopyQueue(cudaMemcpyKind k, cudaStream_t s, bool exact) : kind(k), stream(s), exact_rows(exact) {}
+
+    // rows x width bytes, at dpitch / spitch bytes per row
+    void add(void *d, size_t dpitch, const void *sp, size_t spitch, size_t width, size_t rows)
+    {
+        if (!ok || rows == 0 || width == 0) return;
+        if (dpitch != spitch || (exact_rows && dpitch != width)) {  // a 2D copy of its own
+            flush();
+            ok = cuda_ok(cudaMemcpy2DAsync(d, dpitch, sp, spitch, width, rows, kind, stream), "cudaMemcpy2DAsync");
+            return;
+        }
+        const size_t ext = dpitch * rows;
+        if (extent && (char *)d == dst + extent && (const char *)sp == src + extent) {
+            extent += ext;
+        } else {
+            flush();
+            dst = (char *)d;
+            src = (const char *)sp;
+            extent = ext;
+        }
+        trim = dpitch - width;
+    }
+    void flush()
+    {
+        if (extent && ok) ok = cuda_ok(cudaMemcpyAsync(dst, src, extent - trim, kind, stream), "cudaMemcpyAsync");
+        extent = 0;
+    }
+};
+
+}  // namespace
+
 extern "C" {
 
 const char *tfn_status_string(tfn_status s)
@@ -505,12 +556,20 @@ tfn_status tfn_normals_batch_host(tfn_ctx *c, const tfn_frame *frames, int n, co
     const bool planar = fmt <= OUT_BF16;
     const int ob = out_elem_bytes(fmt);
     // chunk size: about 64 MB of input per chunk, at least one frame
+    // Device rows use the host's pitch when it suits the kernel (a multiple of
+    // 16 bytes), so that host and device layouts match and copies merge.
+    auto dev_pitch = [](int64_t host_pitch, size_t row_bytes) -> size_t {
+        const size_t a = (row_bytes + 15) & ~(size_t)15;
+        return (host_pitch > 0 && (host_pitch & 15) == 0 && (size_t)host_pitch >= a && (size_t)host_pitch <= 4 * a)
+                   ? (size_t)host_pitch
+                   : a;
+    };
     size_t max_in = 0, max_out = 0, max_mask = 0;
     for (int i = 0; i < n; ++i) {
         const tfn_frame &f = frames[i];
-        const size_t ip = ((size_t)f.width * kind_elem_size(f.input_type) + 15) & ~(size_t)15;
-        const size_t op = ((size_t)f.width * ob + 15) & ~(size_t)15;
-        const size_t mp = ((size_t)f.width + 15) & ~(size_t)15;
+        const size_t ip = dev_pitch(f.input_pitch, (size_t)f.width * kind_elem_size(f.input_type));
+        const size_t op = dev_pitch(f.normals_pitch, (size_t)f.width * ob);
+        const size_t mp = dev_pitch(f.mask_pitch, (size_t)f.width);
         max_in = std::max(max_in, ip * f.height);
         max_out = std::max(max_out, op * f.height * (planar ? 3 : 1));
         max_mask = std::max(max_mask, mp * f.height);
@@ -546,12 +605,14 @@ tfn_status tfn_normals_batch_host(tfn_ctx *c, const tfn_frame *frames, int n, co
         Stage &s = c->stages[ci % nst];
         const int cnt = std::min(chunk, n - base);
         dframes.resize(cnt);
+        CopyQueue h2d(cudaMemcpyHostToDevice, s.stream, false);
         for (int i = 0; i < cnt; ++i) {
             const tfn_frame &f = frames[base + i];
             tfn_frame d = f;
-            const size_t ip = ((size_t)f.width * kind_elem_size(f.input_type) + 15) & ~(size_t)15;
-            const size_t op = ((size_t)f.width * ob + 15) & ~(size_t)15;
-            const size_t mp = ((size_t)f.width + 15) & ~(size_t)15;
+            const size_t row_in = (size_t)f.width * kind_elem_size(f.input_type);
+            const size_t ip = dev_pitch(f.input_pitch, row_in);
+            const size_t op = dev_pitch(f.normals_pitch, (size_t)f.width * ob);
+            const size_t mp = dev_pitch(f.mask_pitch, (size_t)f.width);
             d.input = (char *)s.in + max_in * i;
             d.input_pitch = ip;
             d.normals = (char *)s.out + max_out * i;
@@ -560,32 +621,26 @@ tfn_status tfn_normals_batch_host(tfn_ctx *c, const tfn_frame *frames, int n, co
             d.mask = (uint8_t *)s.mask + max_mask * i;
             d.mask_pitch = mp;
             if ((st = validate_frame(&d, fmt))) break;
-            if (!cuda_ok(cudaMemcpy2DAsync((void *)d.input, ip, f.input, f.input_pitch,
-                                           (size_t)f.width * kind_elem_size(f.input_type), f.height,
-                                           cudaMemcpyHostToDevice, s.stream),
-                         "cudaMemcpy2DAsync(H2D)")) {
-                st = TFN_ERR_CUDA;
-                break;
-            }
+            h2d.add((void *)d.input, ip, f.input, f.input_pitch, row_in, f.height);
             dframes[i] = d;
         }
+        h2d.flush();
+        if (!st && !h2d.ok) st = TFN_ERR_CUDA;
         if (st) break;
         if ((st = run_batch(c, dframes.data(), cnt, *m, s.stream))) break;
-        for (int i = 0; i < cnt && st == TFN_OK; ++i) {
+        CopyQueue d2h(cudaMemcpyDeviceToHost, s.stream, true), d2h_mask(cudaMemcpyDeviceToHost, s.stream, true);
+        for (int i = 0; i < cnt; ++i) {
             const tfn_frame &f = frames[base + i];
             const tfn_frame &d = dframes[i];
             for (int p = 0; p < (planar ? 3 : 1); ++p)
-                if (!cuda_ok(cudaMemcpy2DAsync((char *)f.normals + p * f.normals_plane_stride, f.normals_pitch,
-                                               (char *)d.normals + p * d.normals_plane_stride, d.normals_pitch,
-                                               (size_t)f.width * ob, f.height, cudaMemcpyDeviceToHost, s.stream),
-                             "cudaMemcpy2DAsync(D2H)"))
-                    st = TFN_ERR_CUDA;
-            if (st == TFN_OK &&
-                !cuda_ok(cudaMemcpy2DAsync(f.mask, f.mask_pitch, d.mask, d.mask_pitch, f.width, f.height,
-                                           cudaMemcpyDeviceToHost, s.stream),
-                         "cudaMemcpy2DAsync(D2H)"))
-                st = TFN_ERR_CUDA;
+                d2h.add((char *)f.normals + p * f.normals_plane_stride, f.normals_pitch,
+                        (char *)d.normals + p * d.normals_plane_stride, d.normals_pitch, (size_t)f.width * ob,
+                        f.height);
+            d2h_mask.add(f.mask, f.mask_pitch, d.mask, d.mask_pitch, f.width, f.height);
         }
+        d2h.flush();
+        d2h_mask.flush();
+        if (!d2h.ok || !d2h_mask.ok) st = TFN_ERR_CUDA;
     }
     for (int k = 0; k < nst; ++k)
         if (!cuda_ok(cudaStreamSynchronize(c->stages[k].stream), "cudaStreamSynchronize") && st == TFN_OK)

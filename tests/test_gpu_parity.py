@@ -282,6 +282,29 @@ def test_host_buffer_path_matches_device_path(torch, tfn, ctx):
         assert np.array_equal(normals[k].numpy(), n_dev[k]) and np.array_equal(masks[k].numpy(), m_dev[k])
 
 
+def test_host_path_contiguous_batch_and_padded_views(torch, tfn, ctx):
+    # a contiguous batch (copies merge into a few large ones) gives the device path's bits
+    imgs = [img for img, _ in depth_frames([(96, 128)] * 6, 1450)]
+    cam = small_recipe(96, 128).camera
+    stack = torch.from_numpy(np.stack(imgs)).pin_memory()
+    n_all = torch.empty((6, 3, 96, 128), dtype=torch.float32).pin_memory()
+    m_all = torch.empty((6, 96, 128), dtype=torch.uint8).pin_memory()
+    ctx.normals_batch_host([stack[k] for k in range(6)], cam, [n_all[k] for k in range(6)],
+                           [m_all[k] for k in range(6)])
+    n_dev, m_dev = run_batch(torch, tfn, ctx, [(x, cam) for x in imgs], grad="fd", phi="mean")
+    for k in range(6):
+        assert np.array_equal(n_all[k].numpy(), n_dev[k]) and np.array_equal(m_all[k].numpy(), m_dev[k])
+    # outputs that are views with padding between rows: the padding keeps its bytes
+    big_n = torch.full((6, 3, 96, 160), 7.0, dtype=torch.float32).pin_memory()
+    big_m = torch.full((6, 96, 144), 9, dtype=torch.uint8).pin_memory()
+    ctx.normals_batch_host([stack[k] for k in range(6)], cam, [big_n[k, :, :, :128] for k in range(6)],
+                           [big_m[k, :, :128] for k in range(6)])
+    assert (big_n[..., 128:] == 7.0).all() and (big_m[..., 128:] == 9).all()
+    for k in range(6):
+        assert np.array_equal(big_n[k, :, :, :128].numpy(), n_dev[k])
+        assert np.array_equal(big_m[k, :, :128].numpy(), m_dev[k])
+
+
 def test_full_batch_256_sampled_against_oracle(torch, tfn, ctx):
     # the benchmark's launch: 256 noisy 480x640 frames in one call; three
     # frames are compared with the oracle pixel by pixel, all frames for

@@ -323,7 +323,7 @@ CUtensorMap *slot_maps(void *base, int cap)
 tfn_status launch_group(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method &m, cudaStream_t stream)
 {
     const int kind = frames[0].input_type;
-    const int cfg = pick_cfg(c, kind, m);
+    const int cfg = choose_cfg(c, frames, n, m);
     std::vector<unsigned char> key;
     key.reserve(16 + (size_t)n * 96);
     append_key(key, &m, sizeof m);
@@ -672,9 +672,18 @@ tfn_status tfn_plan_create(tfn_ctx *c, const tfn_frame *frames, int n, const tfn
     void *hbase = (void *)(((uintptr_t)host.data() + 127) & ~(uintptr_t)127);
     FrameDesc *d = slot_descs(hbase);
     CUtensorMap *maps = slot_maps(hbase, n);
+    // one launch per run of frames of the same input kind, each with its shape
+    std::vector<int> run_cfg(n);
+    for (int i = 0; i < n;) {
+        int j = i + 1;
+        while (j < n && frames[j].input_type == frames[i].input_type) ++j;
+        const int cfg = choose_cfg(c, frames + i, j - i, *m);
+        for (int k = i; k < j; ++k) run_cfg[k] = cfg;
+        i = j;
+    }
     for (int i = 0, tb = 0; i < n; ++i) {
         if (i > 0 && frames[i].input_type != frames[i - 1].input_type) tb = 0;
-        const int cfg = pick_cfg(c, frames[i].input_type, *m);
+        const int cfg = run_cfg[i];
         d[i] = describe_frame(frames[i], cfg, *m, tb);
         tb += frame_tiles(frames[i], cfg);
         if ((st = encode_map(&maps[i], frames[i], cfg))) break;
@@ -690,7 +699,7 @@ tfn_status tfn_plan_create(tfn_ctx *c, const tfn_frame *frames, int n, const tfn
         for (int i = 0; i < n && lst == TFN_OK;) {
             int j = i + 1;
             while (j < n && frames[j].input_type == frames[i].input_type) ++j;
-            const int cfg = pick_cfg(c, frames[i].input_type, *m);
+            const int cfg = run_cfg[i];
             int total = 0;
             for (int k = i; k < j; ++k) total += frame_tiles(frames[k], cfg);
             lst = launch_normals(frames[i].input_type, *m, cfg, slot_descs(p->dev) + i, slot_maps(p->dev, n) + i,

@@ -90,12 +90,24 @@ struct DeviceGuard {  // switches to the context's device for the call's duratio
 tfn_status ctx_alloc(tfn_ctx *c, void **p, size_t bytes);
 void ctx_free(tfn_ctx *c, void *&p, size_t bytes);
 
-// Tile shape for a launch of frames of input kind `kind` with method `m`.
-inline int pick_cfg(const tfn_ctx *c, int kind, const tfn_method &m)
+// True when a launch over frames[0..n) has fewer than two work items per
+// resident warp with the default shape (one or a few small frames).
+inline bool small_launch(const tfn_frame *frames, int n, int num_sms)
+{
+    long long items = 0;
+    for (int i = 0; i < n; ++i) items += frame_tiles(frames[i], 0);
+    return items < (long long)num_sms * 32;
+}
+
+// Tile shape for a launch over frames[0..n) (one input kind) with method m:
+// forced (tfn_set_tile_shape), else the tune table's, else the short-item
+// shape for a small launch, else shape 0.
+inline int choose_cfg(const tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method &m)
 {
     if (c->forced_cfg >= 0) return c->forced_cfg;
-    const int t = c->tuned[kind][m.grad][m.phi][m.output];
-    return t >= 0 ? t : 0;
+    const int t = c->tuned[frames[0].input_type][m.grad][m.phi][m.output];
+    if (t >= 0) return t;
+    return small_launch(frames, n, c->num_sms) ? kSmallCfg : 0;
 }
 
 // Enqueues the estimator over frames[0..n) (device pointers, already

@@ -52,8 +52,11 @@ struct LaunchArgs {
 struct TileCfg {
     int tw, th, pr, cr, nst, warps;
 };
-constexpr int kNumCfg = 3;
-constexpr TileCfg kCfgs[kNumCfg] = {{128, 18, 18, 5, 3, 4}, {128, 30, 30, 8, 3, 4}, {128, 12, 12, 7, 3, 4}};
+constexpr int kNumCfg = 4;
+constexpr TileCfg kCfgs[kNumCfg] = {
+    {128, 18, 18, 5, 3, 4}, {128, 30, 30, 8, 3, 4}, {128, 12, 12, 7, 3, 4}, {128, 6, 6, 4, 2, 4}};
+// the default shape for launches with few items (short items spread one frame over many warps)
+constexpr int kSmallCfg = 3;
 
 inline int cfg_threads(int c) { return 32 * kCfgs[c].warps; }
 inline int kind_elem_size(int kind) { return (kind == KIND_DEPTH_F32 || kind == KIND_DISP_F32) ? 4 : 2; }

@@ -20,6 +20,7 @@
 #include <mutex>
 
 #include "../../include/tfn.h"
+#include "tfn_ctx.h"
 #include "tfn_internal.h"
 
 namespace {
@@ -83,14 +84,22 @@ extern "C" tfn_status tfn_normals_noalloc(const tfn_frame *frames, int n, const 
     // pageable-memory copy returns once the source has been consumed, so the
     // staging is free for the next call as soon as this one returns.
     thread_local Scratch h;
-    const int cfg = 0;
+    // one launch per run of frames of one input kind; a small run takes the short-item shape
+    int run_cfg[kMax];
+    for (int i = 0; i < n;) {
+        int j = i + 1;
+        while (j < n && frames[j].input_type == frames[i].input_type) ++j;
+        const int cfg = small_launch(frames + i, j - i, sms) ? kSmallCfg : 0;
+        for (int k = i; k < j; ++k) run_cfg[k] = cfg;
+        i = j;
+    }
     int tb = 0;
     for (int i = 0; i < n; ++i) {
         if (i > 0 && frames[i].input_type != frames[i - 1].input_type)
             tb = 0;  // a new launch (input kind) starts its own tile queue
-        h.desc[i] = describe_frame(frames[i], cfg, *method, tb);
-        tb += frame_tiles(frames[i], cfg);
-        if ((st = encode_map(&h.maps[i], frames[i], cfg))) return st;
+        h.desc[i] = describe_frame(frames[i], run_cfg[i], *method, tb);
+        tb += frame_tiles(frames[i], run_cfg[i]);
+        if ((st = encode_map(&h.maps[i], frames[i], run_cfg[i]))) return st;
     }
     cudaStream_t s = (cudaStream_t)stream;
     if (!cuda_ok(cudaMemcpyAsync(d->maps, h.maps, (size_t)n * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s),
@@ -104,9 +113,9 @@ extern "C" tfn_status tfn_normals_noalloc(const tfn_frame *frames, int n, const 
         int j = i + 1;
         while (j < n && frames[j].input_type == frames[i].input_type) ++j;
         int total = 0;
-        for (int k = i; k < j; ++k) total += frame_tiles(frames[k], cfg);
-        st = launch_normals(frames[i].input_type, *method, cfg, d->desc + i, d->maps + i, d->status, j - i, total, sms,
-                            s);
+        for (int k = i; k < j; ++k) total += frame_tiles(frames[k], run_cfg[i]);
+        st = launch_normals(frames[i].input_type, *method, run_cfg[i], d->desc + i, d->maps + i, d->status, j - i, total,
+                            sms, s);
         if (st) return st;
         i = j;
     }

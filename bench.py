@@ -191,6 +191,20 @@ def run_reference(args):
 # --------------------------------------------------------------------------------------------
 # our arm
 
+def job_throughput(local_ms: float, frames_per_rank: int, world: int, device="cpu"):
+    """Replicas: every rank times its own batch; the job's time is the slowest rank's (a MAX
+    all-reduce over the default process group, a tensor on `device`) and its throughput is all
+    ranks' frames over that time.  Returns (job_ms, frames/s)."""
+    job_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([job_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        job_ms = float(t.item())
+    return job_ms, world * frames_per_rank / (job_ms * 1e-3)
+
+
 def cpu_baseline(seconds_target=12.0):
     import oracle
     import scenes
@@ -279,13 +293,9 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
     torch.cuda.synchronize()
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, fps = job_throughput(total_ms, nf * args.steps, world, dev)
     status = ctx.device_status()
     ms_step = total_ms / args.steps
-    fps = world * nf * args.steps / (total_ms * 1e-3)
     launch_ms = statistics.mean(per)
     px = nf * H * W
     achieved = BYTES_PER_PX["f32_in_f32_out"] * px / (launch_ms * 1e-3) / 1e9

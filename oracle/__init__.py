@@ -54,6 +54,8 @@ def open_library(path: str):
     lib.tfn_oracle_normals.restype = i
     lib.tfn_oracle_normals_batch.argtypes = [p, i64, i, i, i, i, d, d, d, d, d, d, i, i, i, p, p, i]
     lib.tfn_oracle_normals_batch.restype = i
+    lib.tfn_oracle_points.argtypes = [p, i64, i, i, i, d, d, d, d, d, d, p]
+    lib.tfn_oracle_points.restype = i
     return lib
 
 
@@ -126,6 +128,59 @@ def normals_batch(imgs, fx, fy, u0, v0, *, grad="fd", phi="mean", disparity=Fals
     if st:
         raise ValueError(f"oracle rejected its arguments (status {st})")
     return n, m
+
+
+def points(img, fx, fy, u0, v0, *, disparity=False, baseline=1.0, disp_scale=1.0 / 16, lib=None):
+    """Back-projected points of every valid sample of one H x W image, (3, H, W) float64 (X, Y, Z);
+    holes give (0, 0, 0).  Sec. III, Eq. (intrinsic matrix); disparity input through Eq. (z_d)."""
+    img = np.ascontiguousarray(img)
+    H, W = img.shape
+    out = np.empty((3, H, W), np.float64)
+    st = (lib or _load()).tfn_oracle_points(img.ctypes.data, img.strides[0], H, W, _input_type(img, disparity),
+                                            disp_scale, fx, fy, u0, v0, baseline, out.ctypes.data)
+    if st:
+        raise ValueError(f"oracle rejected its arguments (status {st})")
+    return out
+
+
+def oct_encode(n):
+    """Octahedral map of vectors (3, ...) onto the square [-1, 1]^2 (Cigolle et al., "A Survey of
+    Efficient Representations for Independent Unit Vectors", JCGT 3(2), 2014, the "oct" mapping):
+    p = (x, y) / (|x| + |y| + |z|), and for z < 0 the lower hemisphere is folded over the square's
+    corners, p <- ((1 - |p_y|) sgn p_x, (1 - |p_x|) sgn p_y) with sgn(0) = +1.  Zero vectors map to
+    (0, 0)."""
+    n = np.asarray(n, np.float64)
+    s = np.abs(n[0]) + np.abs(n[1]) + np.abs(n[2])
+    safe = np.where(s > 0, s, 1.0)
+    px = np.where(s > 0, n[0] / safe, 0.0)
+    py = np.where(s > 0, n[1] / safe, 0.0)
+    sx = np.where(px >= 0, 1.0, -1.0)
+    sy = np.where(py >= 0, 1.0, -1.0)
+    low = n[2] < 0
+    qx = np.where(low, (1 - np.abs(py)) * sx, px)
+    qy = np.where(low, (1 - np.abs(px)) * sy, py)
+    return np.stack([qx, qy])
+
+
+def oct_quantize(p):
+    """Signed 16-bit code of an octahedral point: round-to-nearest-even of p * 32767."""
+    return np.rint(np.clip(np.asarray(p, np.float64), -1.0, 1.0) * 32767.0).astype(np.int16)
+
+
+def oct_decode(q):
+    """Unit vectors (3, ...) of octahedral points (2, ...) (floats in [-1, 1], or int16 codes / 32767):
+    v = (p_x, p_y, 1 - |p_x| - |p_y|), unfolded where v_z < 0, normalised."""
+    q = np.asarray(q)
+    p = q.astype(np.float64) / 32767.0 if q.dtype == np.int16 else q.astype(np.float64)
+    vx, vy = p[0], p[1]
+    vz = 1.0 - np.abs(vx) - np.abs(vy)
+    sx = np.where(vx >= 0, 1.0, -1.0)
+    sy = np.where(vy >= 0, 1.0, -1.0)
+    low = vz < 0
+    ux = np.where(low, (1 - np.abs(vy)) * sx, vx)
+    uy = np.where(low, (1 - np.abs(vx)) * sy, vy)
+    v = np.stack([ux, uy, vz])
+    return v / np.sqrt((v * v).sum(0))
 
 
 def angle_deg(a, b):

@@ -333,6 +333,37 @@ int tfn_oracle_normals_batch(const void *in, int64_t pitch, int n, int H, int W,
     return OR_OK;
 }
 
+/*
+ * Back-projected point cloud of one frame, every valid sample (Sec. III, Eq.
+ * intrinsic matrix: p = (Z (u - u0)/fx, Z (v - v0)/fy, Z); disparity input:
+ * Z = f t_c / d, Eq. z_d, with f = fx = fy).  `points` receives 3 planes of
+ * H*W doubles (X, Y, Z); holes (reading R1) give (0, 0, 0).
+ */
+int tfn_oracle_points(const void *in, int64_t pitch, int H, int W, int type, double disp_scale, double fx,
+                      double fy, double u0, double v0, double tc, double *points)
+{
+    int st = check_args(in, pitch, H, W, type, OR_FD, OR_MEAN, OR_LITERAL, fx, fy, tc, disp_scale);
+    if (st || !points) return st ? st : OR_BAD_ARG;
+    const int disparity = (type == OR_DISP_U16 || type == OR_DISP_F32);
+    const int64_t HW = (int64_t)H * W;
+    for (int v = 0; v < H; ++v)
+        for (int u = 0; u < W; ++u) {
+            const int64_t idx = (int64_t)v * W + u;
+            const double s = read_sample(in, pitch, type, disp_scale, u, v);
+            const int ok = type == OR_DISP_U16 ? s > 0 : is_valid(s);
+            double X = 0, Y = 0, Z = 0;
+            if (ok) {
+                Z = disparity ? fx * tc / s : s;
+                X = Z * (u - u0) / fx;
+                Y = Z * (v - v0) / fy;
+            }
+            points[idx] = X;
+            points[HW + idx] = Y;
+            points[2 * HW + idx] = Z;
+        }
+    return OR_OK;
+}
+
 /* Angle in degrees between two 3-vectors, atan2(|a x b|, a.b) (Sec. IV-A, Eq.
  * ea_ep defines psi = arccos of the normalised dot product; atan2 gives the
  * same angle without the loss of accuracy of arccos near 0). */

@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_pins as pins
+from tests import test_oracle_points as point_pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "tfn_oracle.c")
 
@@ -48,11 +49,18 @@ MUTANTS = {
     "prewitt_weights": ("default: w[0] = 1; w[1] = 1; w[2] = 1; *norm = 6;",
                         "default: w[0] = 1; w[1] = 2; w[2] = 1; *norm = 6;"),
     "nx_without_focal": ("else { nx = J->fx * gu; ny = J->fy * gv; }", "else { nx = gu; ny = J->fy * gv; }"),
+    # the back-projected point cloud
+    "points_wrong_focal": ("Y = Z * (v - v0) / fy;", "Y = Z * (v - v0) / fx;"),
+    "points_swapped_principal_point": ("X = Z * (u - u0) / fx;", "X = Z * (u - v0) / fx;"),
+    "points_disparity_without_baseline": ("Z = disparity ? fx * tc / s : s;", "Z = disparity ? fx / s : s;"),
+    "points_keep_holes": ("double X = 0, Y = 0, Z = 0;\n            if (ok) {", "double X = 0, Y = 0, Z = 0;\n            if (1) {"),
 }
 
 
 def _pins_fail(lib):
     if pins.check_golden(lib):
+        return True
+    if point_pins.check_points(lib):
         return True
     for grad in pins.GRADS:
         for phi in pins.PHIS:

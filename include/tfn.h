@@ -92,8 +92,19 @@ typedef enum tfn_output {
     TFN_OUT_F16 = 1,
     TFN_OUT_BF16 = 2,
     TFN_OUT_F16X4 = 3,
-    TFN_OUT_BF16X4 = 4
+    TFN_OUT_BF16X4 = 4,
+    TFN_OUT_OCT16 = 5 /* one plane of 2 x int16 per pixel: the octahedral code of the unit
+                         normal (see below) */
 } tfn_output;
+
+/* TFN_OUT_OCT16: the octahedral map of Cigolle et al. ("A Survey of Efficient
+ * Representations for Independent Unit Vectors", JCGT 3(2), 2014): for the
+ * unit normal (x, y, z), p = (x, y) / (|x| + |y| + |z|), and where z < 0,
+ * p = ((1 - |p_y|) s(p_x), (1 - |p_x|) s(p_y)) with s(t) = +1 for t >= 0, else
+ * -1; each component is stored as round-to-nearest-even(p * 32767).  Decode:
+ * v = (p_x, p_y, 1 - |p_x| - |p_y|), unfold where v_z < 0 the same way,
+ * normalise.  Non-evaluable pixels store (0, 0).  16-bit codes keep every
+ * direction within 0.005 degrees. */
 
 /* Pinhole intrinsics (Sec. III, Eq. intrinsic matrix), in pixels.  For
  * disparity input fx must equal fy (= f of Eq. z_d) and `baseline` is the
@@ -116,6 +127,14 @@ typedef struct tfn_frame {
     int64_t normals_plane_stride; /* bytes between planes (planar layouts), multiple of 16 */
     uint8_t *mask;                /* height rows of mask_pitch bytes: 1 = evaluable, 0 = not */
     int64_t mask_pitch;           /* bytes, multiple of 16 */
+    /* Optional point cloud written in the same pass (NULL: none): three float32
+     * planes (X, Y, Z) at points + c * points_plane_stride, height rows of
+     * points_pitch bytes; every valid sample's back-projection p = (Z (u -
+     * u0)/fx, Z (v - v0)/fy, Z) (Sec. III, Eq. intrinsic matrix; disparity
+     * input: Z = f t_c / d, Eq. z_d), holes (0, 0, 0). */
+    void *points;
+    int64_t points_pitch;         /* bytes, multiple of 16, >= width * 4 */
+    int64_t points_plane_stride;  /* bytes, multiple of 16, >= points_pitch * height */
 } tfn_frame;
 
 /* Method selection. */
@@ -332,7 +351,7 @@ tfn_status tfn_server_destroy(tfn_server *srv);
  * is an interface concern of this library.)
  *
  * It takes no context.  The scratch the kernel needs (frame descriptors, TMA
- * tensor maps, a status word; about 14 KB) lives in one fixed array compiled
+ * tensor maps, a status word; about 17 KB) lives in one fixed array compiled
  * into the library, which every device that loads the library keeps until the
  * process exits.  Limits and behaviour:
  *   - n > TFN_NOALLOC_MAX_FRAMES returns TFN_ERR_INVALID_ARG before anything

@@ -28,14 +28,14 @@ TFN_OK, TFN_ERR_INVALID_ARG, TFN_ERR_UNSUPPORTED, TFN_ERR_MISALIGNED, TFN_ERR_OU
 TFN_DEPTH_F32, TFN_DEPTH_F16, TFN_DISP_U16, TFN_DISP_F32 = range(4)
 TFN_GRAD_FD, TFN_GRAD_SOBEL, TFN_GRAD_SCHARR, TFN_GRAD_PREWITT = range(4)
 TFN_PHI_MEAN, TFN_PHI_MEDIAN = range(2)
-TFN_OUT_F32, TFN_OUT_F16, TFN_OUT_BF16, TFN_OUT_F16X4, TFN_OUT_BF16X4 = range(5)
+TFN_OUT_F32, TFN_OUT_F16, TFN_OUT_BF16, TFN_OUT_F16X4, TFN_OUT_BF16X4, TFN_OUT_OCT16 = range(6)
 TFN_FLAG_REFINE_ALL = 1
 TFN_REQ_HOST = 1
 
 GRADS = {"fd": TFN_GRAD_FD, "sobel": TFN_GRAD_SOBEL, "scharr": TFN_GRAD_SCHARR, "prewitt": TFN_GRAD_PREWITT}
 PHIS = {"mean": TFN_PHI_MEAN, "median": TFN_PHI_MEDIAN}
 OUTPUTS = {"f32": TFN_OUT_F32, "f16": TFN_OUT_F16, "bf16": TFN_OUT_BF16, "f16x4": TFN_OUT_F16X4,
-           "bf16x4": TFN_OUT_BF16X4}
+           "bf16x4": TFN_OUT_BF16X4, "oct16": TFN_OUT_OCT16}
 
 
 class tfn_camera(ctypes.Structure):
@@ -50,7 +50,9 @@ class tfn_frame(ctypes.Structure):
                 ("cam", tfn_camera),
                 ("normals", ctypes.c_void_p), ("normals_pitch", ctypes.c_int64),
                 ("normals_plane_stride", ctypes.c_int64),
-                ("mask", ctypes.c_void_p), ("mask_pitch", ctypes.c_int64)]
+                ("mask", ctypes.c_void_p), ("mask_pitch", ctypes.c_int64),
+                ("points", ctypes.c_void_p), ("points_pitch", ctypes.c_int64),
+                ("points_plane_stride", ctypes.c_int64)]
 
 
 class tfn_method(ctypes.Structure):
@@ -217,9 +219,13 @@ def empty_image(shape, dtype, device="cuda"):
 
 
 def empty_normals(H, W, output="f32", device="cuda", lead=()):
-    """Output buffer for one layout: planar (..., 3, H, W) or packed (..., H, W, 4)."""
+    """Output buffer for one layout: planar (..., 3, H, W), packed (..., H, W, 4), or octahedral
+    codes (..., H, W, 2) int16."""
     torch = _torch()
     fmt = OUTPUTS[output] if isinstance(output, str) else output
+    if fmt == TFN_OUT_OCT16:
+        buf = torch.empty((*lead, H, padded_width(W, 4), 2), dtype=torch.int16, device=device)
+        return buf[..., :W, :]
     if fmt in (TFN_OUT_F32, TFN_OUT_F16, TFN_OUT_BF16):
         dt = {TFN_OUT_F32: torch.float32, TFN_OUT_F16: torch.float16, TFN_OUT_BF16: torch.bfloat16}[fmt]
         return empty_image((*lead, 3, H, W), dt, device)
@@ -230,8 +236,15 @@ def empty_normals(H, W, output="f32", device="cuda", lead=()):
     return buf[..., :W, :]
 
 
-def make_frame(inp, normals, mask, cam, disparity=False, disp_scale=1.0 / 16, output="f32") -> tfn_frame:
-    """tfn_frame describing torch tensors `inp` (H, W), `normals`, `mask` (H, W)."""
+def empty_points(H, W, device="cuda", lead=()):
+    """Point-cloud buffer: three float32 planes (..., 3, H, W) of X, Y, Z."""
+    return empty_image((*lead, 3, H, W), _torch().float32, device)
+
+
+def make_frame(inp, normals, mask, cam, disparity=False, disp_scale=1.0 / 16, output="f32",
+               points=None) -> tfn_frame:
+    """tfn_frame describing torch tensors `inp` (H, W), `normals`, `mask` (H, W) and optional `points`
+    (3, H, W)."""
     fmt = OUTPUTS[output] if isinstance(output, str) else output
     H, W = inp.shape
     f = tfn_frame()
@@ -250,6 +263,10 @@ def make_frame(inp, normals, mask, cam, disparity=False, disp_scale=1.0 / 16, ou
         f.normals_plane_stride = 0
     f.mask = mask.data_ptr()
     f.mask_pitch = mask.stride(0) * mask.element_size()
+    if points is not None:
+        f.points = points.data_ptr()
+        f.points_pitch = points.stride(1) * points.element_size()
+        f.points_plane_stride = points.stride(0) * points.element_size()
     return f
 
 
@@ -296,20 +313,21 @@ class Context:
         self.close()
 
     def normals(self, inp, cam, *, grad="fd", phi="mean", output="f32", disparity=False, disp_scale=1.0 / 16,
-                normals=None, mask=None, stream=None, flags=0):
-        """Normals of one (H, W) device image -> (normals, mask)."""
+                normals=None, mask=None, points=None, stream=None, flags=0):
+        """Normals of one (H, W) device image -> (normals, mask); `points` (3, H, W) also receives the
+        back-projected point cloud."""
         H, W = inp.shape
         if normals is None:
             normals = empty_normals(H, W, output, inp.device)
         if mask is None:
             mask = empty_image((H, W), _torch().uint8, inp.device)
-        f = make_frame(inp, normals, mask, cam, disparity, disp_scale, output)
+        f = make_frame(inp, normals, mask, cam, disparity, disp_scale, output, points)
         m = make_method(grad, phi, output, flags)
         check(tfn_normals(self.handle, ctypes.byref(f), ctypes.byref(m), _stream_handle(stream)), "tfn_normals")
         return normals, mask
 
     def normals_batch(self, inputs, cams, *, grad="fd", phi="mean", output="f32", disparity=False,
-                      disp_scale=1.0 / 16, normals=None, masks=None, stream=None, flags=0):
+                      disp_scale=1.0 / 16, normals=None, masks=None, points=None, stream=None, flags=0):
         """Normals of a list of (H_i, W_i) device images (or an (N, H, W) stack) in one launch."""
         n = len(inputs)
         if isinstance(cams, dict):
@@ -318,27 +336,27 @@ class Context:
             normals = [empty_normals(x.shape[0], x.shape[1], output, x.device) for x in inputs]
         if masks is None:
             masks = [empty_image(tuple(x.shape), _torch().uint8, x.device) for x in inputs]
-        frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output)
-                                   for k in range(n)])
+        frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output,
+                                              points[k] if points is not None else None) for k in range(n)])
         m = make_method(grad, phi, output, flags)
         check(tfn_normals_batch(self.handle, frames, n, ctypes.byref(m), _stream_handle(stream)), "tfn_normals_batch")
         return normals, masks
 
     def normals_batch_host(self, inputs, cams, normals, masks, *, grad="fd", phi="mean", output="f32",
-                           disparity=False, disp_scale=1.0 / 16, stream=None, flags=0):
+                           disparity=False, disp_scale=1.0 / 16, points=None, stream=None, flags=0):
         """Like normals_batch, with every tensor in host memory (pinned is fastest); synchronous."""
         n = len(inputs)
         if isinstance(cams, dict):
             cams = [cams] * n
-        frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output)
-                                   for k in range(n)])
+        frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output,
+                                              points[k] if points is not None else None) for k in range(n)])
         m = make_method(grad, phi, output, flags)
         check(tfn_normals_batch_host(self.handle, frames, n, ctypes.byref(m), _stream_handle(stream)),
               "tfn_normals_batch_host")
         return normals, masks
 
     def plan(self, inputs, cams, *, grad="fd", phi="mean", output="f32", disparity=False, disp_scale=1.0 / 16,
-             normals=None, masks=None, flags=0):
+             normals=None, masks=None, points=None, flags=0):
         """Freezes a batch into a Plan (descriptors uploaded once, launches captured in a CUDA graph)."""
         n = len(inputs)
         if isinstance(cams, dict):
@@ -347,8 +365,8 @@ class Context:
             normals = [empty_normals(x.shape[0], x.shape[1], output, x.device) for x in inputs]
         if masks is None:
             masks = [empty_image(tuple(x.shape), _torch().uint8, x.device) for x in inputs]
-        frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output)
-                                   for k in range(n)])
+        frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output,
+                                              points[k] if points is not None else None) for k in range(n)])
         m = make_method(grad, phi, output, flags)
         h = ctypes.c_void_p()
         check(tfn_plan_create(self.handle, frames, n, ctypes.byref(m), ctypes.byref(h)), "tfn_plan_create")
@@ -455,12 +473,13 @@ class Server:
         self.output = output
         self._keep = {}
 
-    def submit(self, inp, cam, normals, mask, *, host=False, disparity=False, disp_scale=1.0 / 16) -> int:
+    def submit(self, inp, cam, normals, mask, *, host=False, disparity=False, disp_scale=1.0 / 16,
+               points=None) -> int:
         """Queues one frame; returns its ticket (raises TfnError, e.g. TFN_ERR_BUSY)."""
-        f = make_frame(inp, normals, mask, cam, disparity, disp_scale, self.output)
+        f = make_frame(inp, normals, mask, cam, disparity, disp_scale, self.output, points)
         t = ctypes.c_uint64()
         check(tfn_submit(self.handle, ctypes.byref(f), TFN_REQ_HOST if host else 0, ctypes.byref(t)), "tfn_submit")
-        self._keep[t.value] = (inp, normals, mask)
+        self._keep[t.value] = (inp, normals, mask, points)
         return t.value
 
     def wait(self, ticket: int, timeout_ms: int = 10000) -> int:

@@ -104,13 +104,16 @@ void ctx_free(tfn_ctx *c, void *&p, size_t bytes)
 bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
 bool mult16(int64_t x) { return (x & 15) == 0; }
 
-int out_elem_bytes(int fmt) { return fmt == OUT_F32 ? 4 : (fmt == OUT_F16 || fmt == OUT_BF16) ? 2 : 8; }
+int out_elem_bytes(int fmt)
+{
+    return fmt == OUT_F32 || fmt == OUT_OCT16 ? 4 : (fmt == OUT_F16 || fmt == OUT_BF16) ? 2 : 8;
+}
 
 tfn_status validate_method(const tfn_method *m)
 {
     if (!m) return TFN_ERR_INVALID_ARG;
     if (m->grad < 0 || m->grad >= GRAD_COUNT || m->phi < 0 || m->phi >= PHI_COUNT || m->output < 0 ||
-        m->output > OUT_BF16X4 || (m->flags & ~TFN_FLAG_REFINE_ALL))
+        m->output > OUT_OCT16 || (m->flags & ~TFN_FLAG_REFINE_ALL))
         return TFN_ERR_INVALID_ARG;
     return TFN_OK;
 }
@@ -143,6 +146,12 @@ tfn_status validate_frame(const tfn_frame *f, int out_fmt)
     if (!aligned16(f->input) || !aligned16(f->normals) || !aligned16(f->mask) || !mult16(f->input_pitch) ||
         !mult16(f->normals_pitch) || !mult16(f->mask_pitch) || (planar && !mult16(f->normals_plane_stride)))
         return TFN_ERR_MISALIGNED;
+    if (f->points) {
+        if (f->points_pitch < (int64_t)f->width * 4 || f->points_plane_stride < f->points_pitch * (int64_t)f->height)
+            return TFN_ERR_INVALID_ARG;
+        if (!aligned16(f->points) || !mult16(f->points_pitch) || !mult16(f->points_plane_stride))
+            return TFN_ERR_MISALIGNED;
+    }
     return TFN_OK;
 }
 
@@ -207,6 +216,14 @@ FrameDesc describe_frame(const tfn_frame &f, int cfg, const tfn_method &m, int t
     fd.mask_pitch = f.mask_pitch;
     fd.in = f.input;
     fd.in_pitch = f.input_pitch;
+    fd.pts = (char *)f.points;
+    fd.pts_pitch = f.points ? f.points_pitch : 0;
+    fd.pts_plane = f.points ? f.points_plane_stride : 0;
+    // Z = f t_c / d with d = raw * disp_scale for 16-bit disparity (Eq. z_d)
+    if (f.input_type == KIND_DISP_U16)
+        fd.ztc = (float)((double)f.cam.fx * f.cam.baseline / f.disp_scale);
+    else if (f.input_type == KIND_DISP_F32)
+        fd.ztc = (float)((double)f.cam.fx * f.cam.baseline);
     fd.H = f.height;
     fd.W = f.width;
     fd.tiles_x = (f.width + tw - 1) / tw;
@@ -286,6 +303,9 @@ void frame_key(std::vector<unsigned char> &k, const tfn_frame &f)
     append_key(k, &f.normals_plane_stride, sizeof f.normals_plane_stride);
     append_key(k, &f.mask, sizeof f.mask);
     append_key(k, &f.mask_pitch, sizeof f.mask_pitch);
+    append_key(k, &f.points, sizeof f.points);
+    append_key(k, &f.points_pitch, sizeof f.points_pitch);
+    append_key(k, &f.points_plane_stride, sizeof f.points_plane_stride);
 }
 
 size_t slot_bytes(int cap) { return (size_t)cap * sizeof(FrameDesc) + 128 + (size_t)cap * sizeof(CUtensorMap); }
@@ -512,6 +532,7 @@ tfn_status tfn_destroy(tfn_ctx *c)
         ctx_free(c, s.in, s.in_bytes);
         ctx_free(c, s.out, s.out_bytes);
         ctx_free(c, s.mask, s.mask_bytes);
+        ctx_free(c, s.pts, s.pts_bytes);
     }
     void *st = c->status;
     ctx_free(c, st, 256);
@@ -548,6 +569,8 @@ tfn_status tfn_normals_batch_host(tfn_ctx *c, const tfn_frame *frames, int n, co
         if (!f.input || !f.normals || !f.mask || f.height < 1 || f.width < 1 || f.height > 32768 || f.width > 32768 ||
             f.input_type < 0 || f.input_type >= KIND_COUNT)
             return TFN_ERR_INVALID_ARG;
+        if (f.points && (f.points_pitch < (int64_t)f.width * 4 || f.points_plane_stride < f.points_pitch * f.height))
+            return TFN_ERR_INVALID_ARG;
     }
     if (n == 0) return TFN_OK;
     DeviceGuard g(c->device);
@@ -564,7 +587,7 @@ tfn_status tfn_normals_batch_host(tfn_ctx *c, const tfn_frame *frames, int n, co
                    ? (size_t)host_pitch
                    : a;
     };
-    size_t max_in = 0, max_out = 0, max_mask = 0;
+    size_t max_in = 0, max_out = 0, max_mask = 0, max_pts = 0;
     for (int i = 0; i < n; ++i) {
         const tfn_frame &f = frames[i];
         const size_t ip = dev_pitch(f.input_pitch, (size_t)f.width * kind_elem_size(f.input_type));
@@ -573,6 +596,7 @@ tfn_status tfn_normals_batch_host(tfn_ctx *c, const tfn_frame *frames, int n, co
         max_in = std::max(max_in, ip * f.height);
         max_out = std::max(max_out, op * f.height * (planar ? 3 : 1));
         max_mask = std::max(max_mask, mp * f.height);
+        if (f.points) max_pts = std::max(max_pts, dev_pitch(f.points_pitch, (size_t)f.width * 4) * f.height * 3);
     }
     const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, (64u << 20) / std::max<size_t>(max_in, 1)));
     const int nst = 3;
@@ -580,18 +604,21 @@ tfn_status tfn_normals_batch_host(tfn_ctx *c, const tfn_frame *frames, int n, co
         Stage &s = c->stages[k];
         if (!s.stream) TFN_CUDA(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
         const size_t need_in = max_in * chunk, need_out = max_out * chunk, need_mask = max_mask * chunk;
-        if (s.in_bytes < need_in || s.out_bytes < need_out || s.mask_bytes < need_mask) {
+        const size_t need_pts = max_pts * chunk;
+        if (s.in_bytes < need_in || s.out_bytes < need_out || s.mask_bytes < need_mask || s.pts_bytes < need_pts) {
             TFN_CUDA(cudaStreamSynchronize(s.stream));
             ctx_free(c, s.in, s.in_bytes);
             ctx_free(c, s.out, s.out_bytes);
             ctx_free(c, s.mask, s.mask_bytes);
-            s.in_bytes = s.out_bytes = s.mask_bytes = 0;
+            ctx_free(c, s.pts, s.pts_bytes);
+            s.in_bytes = s.out_bytes = s.mask_bytes = s.pts_bytes = 0;
             if ((st = ctx_alloc(c, &s.in, need_in)) || (st = ctx_alloc(c, &s.out, need_out)) ||
-                (st = ctx_alloc(c, &s.mask, need_mask)))
+                (st = ctx_alloc(c, &s.mask, need_mask)) || (need_pts && (st = ctx_alloc(c, &s.pts, need_pts))))
                 return st;
             s.in_bytes = need_in;
             s.out_bytes = need_out;
             s.mask_bytes = need_mask;
+            s.pts_bytes = need_pts;
             for (Slot &sl : c->slots) sl.has_key = false;  // device pointers changed
         }
     }
@@ -620,6 +647,12 @@ tfn_status tfn_normals_batch_host(tfn_ctx *c, const tfn_frame *frames, int n, co
             d.normals_plane_stride = op * f.height;
             d.mask = (uint8_t *)s.mask + max_mask * i;
             d.mask_pitch = mp;
+            if (f.points) {
+                const size_t pp = dev_pitch(f.points_pitch, (size_t)f.width * 4);
+                d.points = (char *)s.pts + max_pts * i;
+                d.points_pitch = pp;
+                d.points_plane_stride = pp * f.height;
+            }
             if ((st = validate_frame(&d, fmt))) break;
             h2d.add((void *)d.input, ip, f.input, f.input_pitch, row_in, f.height);
             dframes[i] = d;
@@ -629,6 +662,7 @@ tfn_status tfn_normals_batch_host(tfn_ctx *c, const tfn_frame *frames, int n, co
         if (st) break;
         if ((st = run_batch(c, dframes.data(), cnt, *m, s.stream))) break;
         CopyQueue d2h(cudaMemcpyDeviceToHost, s.stream, true), d2h_mask(cudaMemcpyDeviceToHost, s.stream, true);
+        CopyQueue d2h_pts(cudaMemcpyDeviceToHost, s.stream, true);
         for (int i = 0; i < cnt; ++i) {
             const tfn_frame &f = frames[base + i];
             const tfn_frame &d = dframes[i];
@@ -637,10 +671,16 @@ tfn_status tfn_normals_batch_host(tfn_ctx *c, const tfn_frame *frames, int n, co
                         (char *)d.normals + p * d.normals_plane_stride, d.normals_pitch, (size_t)f.width * ob,
                         f.height);
             d2h_mask.add(f.mask, f.mask_pitch, d.mask, d.mask_pitch, f.width, f.height);
+            if (f.points)
+                for (int p = 0; p < 3; ++p)
+                    d2h_pts.add((char *)f.points + p * f.points_plane_stride, f.points_pitch,
+                                (char *)d.points + p * d.points_plane_stride, d.points_pitch, (size_t)f.width * 4,
+                                f.height);
         }
         d2h.flush();
         d2h_mask.flush();
-        if (!d2h.ok || !d2h_mask.ok) st = TFN_ERR_CUDA;
+        d2h_pts.flush();
+        if (!d2h.ok || !d2h_mask.ok || !d2h_pts.ok) st = TFN_ERR_CUDA;
     }
     for (int k = 0; k < nst; ++k)
         if (!cuda_ok(cudaStreamSynchronize(c->stages[k].stream), "cudaStreamSynchronize") && st == TFN_OK)

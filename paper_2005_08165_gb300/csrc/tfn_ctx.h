@@ -28,8 +28,8 @@ struct Slot {
 // Staging of the host-buffer path: one set per pipeline stream.
 struct Stage {
     cudaStream_t stream = nullptr;
-    void *in = nullptr, *out = nullptr, *mask = nullptr;
-    size_t in_bytes = 0, out_bytes = 0, mask_bytes = 0;
+    void *in = nullptr, *out = nullptr, *mask = nullptr, *pts = nullptr;
+    size_t in_bytes = 0, out_bytes = 0, mask_bytes = 0, pts_bytes = 0;
 };
 
 }  // namespace tfn

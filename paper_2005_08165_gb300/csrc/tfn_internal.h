@@ -10,7 +10,7 @@ namespace tfn {
 enum Kind { KIND_DEPTH_F32 = 0, KIND_DEPTH_F16 = 1, KIND_DISP_U16 = 2, KIND_DISP_F32 = 3, KIND_COUNT = 4 };
 enum Grad { GRAD_FD = 0, GRAD_SOBEL = 1, GRAD_SCHARR = 2, GRAD_PREWITT = 3, GRAD_COUNT = 4 };
 enum Phi { PHI_MEAN = 0, PHI_MEDIAN = 1, PHI_COUNT = 2 };
-enum OutFmt { OUT_F32 = 0, OUT_F16 = 1, OUT_BF16 = 2, OUT_F16X4 = 3, OUT_BF16X4 = 4 };
+enum OutFmt { OUT_F32 = 0, OUT_F16 = 1, OUT_BF16 = 2, OUT_F16X4 = 3, OUT_BF16X4 = 4, OUT_OCT16 = 5 };
 
 // Device status bits written by kernels.
 enum : uint32_t { DEVERR_TMA_WAIT = 1u };
@@ -30,8 +30,13 @@ struct alignas(16) FrameDesc {
     float fx, fy, u0, v0;
     float thr;           // refinement threshold (see refine_threshold in tfn_api.cu)
     int32_t kind;        // Kind of this frame (a launch holds frames of one kind)
+    char *pts;           // optional point cloud: plane c at pts + c * pts_plane (nullptr: none)
+    int64_t pts_pitch;   // bytes
+    int64_t pts_plane;   // bytes
+    float ztc;           // disparity input: Z = ztc / raw sample (f t_c / disp_scale)
+    int32_t pad;
 };
-static_assert(sizeof(FrameDesc) == 96, "FrameDesc layout");
+static_assert(sizeof(FrameDesc) == 128, "FrameDesc layout");
 
 // Kernel arguments (passed by value as a __grid_constant__).
 struct LaunchArgs {

@@ -721,6 +721,64 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, int fmt)
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
+// Octahedral code of a unit normal (Cigolle et al., JCGT 2014, the "oct"
+// map): p = (x, y) / (|x| + |y| + |z|), folded over the square's corners where
+// z < 0 (sign +1 for 0), each component as round-to-nearest-even(p * 32767),
+// packed as two int16 (x in the low half).  The zero vector of a
+// non-evaluable pixel gives (0, 0).
+__device__ __forceinline__ uint32_t oct16(float x, float y, float z)
+{
+    const float s = __fadd_rn(__fadd_rn(fabsf(x), fabsf(y)), fabsf(z));
+    const float is = s > 0.f ? rcp_approx(s) : 0.f;
+    const float px = __fmul_rn(x, is), py = __fmul_rn(y, is);
+    float qx = px, qy = py;
+    if (z < 0.f) {
+        qx = px >= 0.f ? __fsub_rn(1.f, fabsf(py)) : -__fsub_rn(1.f, fabsf(py));
+        qy = py >= 0.f ? __fsub_rn(1.f, fabsf(px)) : -__fsub_rn(1.f, fabsf(px));
+    }
+    const int cx = __float2int_rn(__fmul_rn(fminf(fmaxf(qx, -1.f), 1.f), 32767.f));
+    const int cy = __float2int_rn(__fmul_rn(fminf(fmaxf(qy, -1.f), 1.f), 32767.f));
+    return ((uint32_t)cx & 0xffffu) | ((uint32_t)cy << 16);
+}
+
+// Where an item's optional point cloud goes.
+struct PtsDesc {
+    char *pts;
+    int64_t pitch, plane;
+};
+
+// Back-projected points of 4 consecutive pixels of row v (n of them inside
+// the frame): Z = the sample (disparity: ztc / sample), X = Z (u - u0)/fx,
+// Y = Z (v - v0)/fy with ucf = (u - u0)/fx per column and vcf = (v - v0)/fy;
+// holes give (0, 0, 0).
+template <int KIND>
+__device__ __forceinline__ void store_points4(const PtsDesc &p, int u, int v, int n, const float (&z)[6],
+                                              const float (&ucf)[4], float vcf, float ztc)
+{
+    float X[4], Y[4], Z[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float s = z[k + 1];
+        const bool ok = s <= kValidHi;
+        const float Zk = KindTraits<KIND>::disparity ? __fdiv_rn(ztc, s) : s;
+        X[k] = ok ? __fmul_rn(Zk, ucf[k]) : 0.f;
+        Y[k] = ok ? __fmul_rn(Zk, vcf) : 0.f;
+        Z[k] = ok ? Zk : 0.f;
+    }
+    char *row = p.pts + (int64_t)v * p.pitch;
+    if (n == 4) {
+        __stcs(reinterpret_cast<float4 *>(row + (int64_t)u * 4), make_float4(X[0], X[1], X[2], X[3]));
+        __stcs(reinterpret_cast<float4 *>(row + p.plane + (int64_t)u * 4), make_float4(Y[0], Y[1], Y[2], Y[3]));
+        __stcs(reinterpret_cast<float4 *>(row + 2 * p.plane + (int64_t)u * 4), make_float4(Z[0], Z[1], Z[2], Z[3]));
+        return;
+    }
+    for (int k = 0; k < n; ++k) {
+        reinterpret_cast<float *>(row)[u + k] = X[k];
+        reinterpret_cast<float *>(row + p.plane)[u + k] = Y[k];
+        reinterpret_cast<float *>(row + 2 * p.plane)[u + k] = Z[k];
+    }
+}
+
 // Stores 4 consecutive pixels (n valid of them, starting at column u).
 __device__ __forceinline__ void store4(const OutDesc &fd, int fmt, int u, int v, int n, const float (&x)[4],
                                        const float (&y)[4], const float (&zz)[4], uint32_t mw)
@@ -733,6 +791,10 @@ __device__ __forceinline__ void store4(const OutDesc &fd, int fmt, int u, int v,
             __stcs(reinterpret_cast<float4 *>(row + fd.out_plane + (int64_t)u * 4), make_float4(y[0], y[1], y[2], y[3]));
             __stcs(reinterpret_cast<float4 *>(row + 2 * fd.out_plane + (int64_t)u * 4),
                    make_float4(zz[0], zz[1], zz[2], zz[3]));
+        } else if (fmt == OUT_OCT16) {
+            __stcs(reinterpret_cast<uint4 *>(row + (int64_t)u * 4),
+                   make_uint4(oct16(x[0], y[0], zz[0]), oct16(x[1], y[1], zz[1]), oct16(x[2], y[2], zz[2]),
+                              oct16(x[3], y[3], zz[3])));
         } else if (fmt == OUT_F16 || fmt == OUT_BF16) {
             __stcs(reinterpret_cast<uint2 *>(row + (int64_t)u * 2), make_uint2(pack2(x[0], x[1], fmt), pack2(x[2], x[3], fmt)));
             __stcs(reinterpret_cast<uint2 *>(row + fd.out_plane + (int64_t)u * 2),
@@ -756,6 +818,8 @@ __device__ __forceinline__ void store4(const OutDesc &fd, int fmt, int u, int v,
             reinterpret_cast<float *>(row)[uu] = x[k];
             reinterpret_cast<float *>(row + fd.out_plane)[uu] = y[k];
             reinterpret_cast<float *>(row + 2 * fd.out_plane)[uu] = zz[k];
+        } else if (fmt == OUT_OCT16) {
+            reinterpret_cast<uint32_t *>(row)[uu] = oct16(x[k], y[k], zz[k]);
         } else if (fmt == OUT_F16 || fmt == OUT_BF16) {
             const uint32_t px = pack2(x[k], y[k], fmt), pz = pack2(zz[k], 0.f, fmt);
             reinterpret_cast<uint16_t *>(row)[uu] = (uint16_t)(px & 0xffff);
@@ -777,6 +841,8 @@ __device__ __forceinline__ void store1(const OutDesc &fd, int fmt, int u, int v,
         reinterpret_cast<float *>(row)[u] = n.x;
         reinterpret_cast<float *>(row + fd.out_plane)[u] = n.y;
         reinterpret_cast<float *>(row + 2 * fd.out_plane)[u] = n.z;
+    } else if (fmt == OUT_OCT16) {
+        reinterpret_cast<uint32_t *>(row)[u] = oct16(n.x, n.y, n.z);
     } else if (fmt == OUT_F16 || fmt == OUT_BF16) {
         const uint32_t px = pack2(n.x, n.y, fmt), pz = pack2(n.z, 0.f, fmt);
         reinterpret_cast<uint16_t *>(row)[u] = (uint16_t)(px & 0xffff);
@@ -906,12 +972,20 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
         const float thr = refine_all ? -1.f : __ldg(&f->thr);
         const void *in = (const void *)__ldg((const unsigned long long *)&f->in);
         const int64_t in_pitch = __ldg(&f->in_pitch);
+        PtsDesc pts;
+        pts.pts = (char *)__ldg((const unsigned long long *)&f->pts);
+        pts.pitch = __ldg(&f->pts_pitch);
+        pts.plane = __ldg(&f->pts_plane);
+        const float ztc = __ldg(&f->ztc);
         const int lt = t - __ldg(&f->tile_begin);
         const int x0 = (lt % txs) * 128 + 4 * lane, y0 = (lt / txs) * TH;
         const int nvalid = min(4, W - x0);  // pixels of this lane inside the frame (may be <= 0)
-        float uc[4];
+        float uc[4], ucf[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) uc[k] = __fsub_rn((float)(x0 + k), u0);
+        for (int k = 0; k < 4; ++k) {
+            uc[k] = __fsub_rn((float)(x0 + k), u0);
+            ucf[k] = __fdiv_rn(uc[k], fx);
+        }
 
         // Sample row j (0 .. TH+1) of the item is image row y0 - 1 + j; rows
         // at or past the bottom read as holes.  The rows arrive in order, so
@@ -956,6 +1030,8 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
             row_step<KIND, GRAD, PHI>(P, C, N, cy, uc, __fsub_rn((float)y, v0), fx, fy, thr, ox, oy, oz, mw, rb);
             if (y < H && nvalid > 0) {
                 store4(out, args.out_fmt, x0, y, nvalid, ox, oy, oz, mw);
+                if (pts.pts)  // the fused point cloud of this row
+                    store_points4<KIND>(pts, x0, y, nvalid, C.z, ucf, __fdiv_rn(__fsub_rn((float)y, v0), fy), ztc);
                 rb &= (1u << min(nvalid, 4)) - 1u;
             } else {
                 rb = 0;

@@ -53,12 +53,15 @@ constexpr size_t kLatencyWindow = 65536;
 size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int out_bytes_per_elem(int fmt) { return fmt == OUT_F32 ? 4 : (fmt == OUT_F16 || fmt == OUT_BF16) ? 2 : 8; }
+int out_bytes_per_elem(int fmt)
+{
+    return fmt == OUT_F32 || fmt == OUT_OCT16 ? 4 : (fmt == OUT_F16 || fmt == OUT_BF16) ? 2 : 8;
+}
 
 // Device staging layout of one host-buffer request: input, normals, mask.
 struct StageLayout {
-    size_t in_pitch, out_pitch, mask_pitch;
-    size_t in_off, out_off, mask_off, bytes;
+    size_t in_pitch, out_pitch, mask_pitch, pts_pitch;
+    size_t in_off, out_off, mask_off, pts_off, bytes;
     int planes;
 };
 
@@ -73,7 +76,9 @@ StageLayout stage_layout(const tfn_frame &f, int fmt)
     L.in_off = 0;
     L.out_off = al256(L.in_pitch * f.height);
     L.mask_off = L.out_off + al256(L.out_pitch * f.height * L.planes);
-    L.bytes = L.mask_off + al256(L.mask_pitch * f.height);
+    L.pts_pitch = al16((size_t)f.width * 4);
+    L.pts_off = L.mask_off + al256(L.mask_pitch * f.height);
+    L.bytes = L.pts_off + (f.points ? al256(L.pts_pitch * f.height * 3) : 0);
     return L;
 }
 
@@ -188,6 +193,11 @@ tfn_status enqueue_batch(tfn_server *s, Batch &b, size_t block_off)
         d.normals_plane_stride = (int64_t)(L.out_pitch * f.height);
         d.mask = (uint8_t *)(base + L.mask_off);
         d.mask_pitch = (int64_t)L.mask_pitch;
+        if (f.points) {
+            d.points = base + L.pts_off;
+            d.points_pitch = (int64_t)L.pts_pitch;
+            d.points_plane_stride = (int64_t)(L.pts_pitch * f.height);
+        }
         dev[i] = d;
         if (!cuda_ok(cudaMemcpy2DAsync((void *)d.input, L.in_pitch, f.input, (size_t)f.input_pitch,
                                        (size_t)f.width * kind_elem_size(f.input_type), f.height, cudaMemcpyHostToDevice,
@@ -213,6 +223,14 @@ tfn_status enqueue_batch(tfn_server *s, Batch &b, size_t block_off)
                                        cudaMemcpyDeviceToHost, p.stream),
                      "cudaMemcpy2DAsync(D2H)"))
             return TFN_ERR_CUDA;
+        if (f.points)
+            for (int q = 0; q < 3; ++q)
+                if (!cuda_ok(cudaMemcpy2DAsync((char *)f.points + q * f.points_plane_stride, (size_t)f.points_pitch,
+                                               (const char *)d.points + q * d.points_plane_stride,
+                                               (size_t)d.points_pitch, (size_t)f.width * 4, f.height,
+                                               cudaMemcpyDeviceToHost, p.stream),
+                             "cudaMemcpy2DAsync(D2H)"))
+                    return TFN_ERR_CUDA;
     }
     if (!cuda_ok(cudaMemcpyAsync(p.status_host, s->ctx->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, p.stream),
                  "cudaMemcpyAsync(status)") ||
@@ -342,6 +360,8 @@ tfn_status validate_host_request(const tfn_frame &f, int fmt)
         f.mask_pitch < f.width)
         return TFN_ERR_INVALID_ARG;
     if (fmt <= OUT_BF16 && f.normals_plane_stride < f.normals_pitch * (int64_t)f.height) return TFN_ERR_INVALID_ARG;
+    if (f.points && (f.points_pitch < (int64_t)f.width * 4 || f.points_plane_stride < f.points_pitch * f.height))
+        return TFN_ERR_INVALID_ARG;
     const StageLayout L = stage_layout(f, fmt);
     tfn_frame d = f;
     d.input = (const void *)(uintptr_t)256;
@@ -351,6 +371,11 @@ tfn_status validate_host_request(const tfn_frame &f, int fmt)
     d.normals_plane_stride = (int64_t)(L.out_pitch * f.height);
     d.mask = (uint8_t *)(uintptr_t)256;
     d.mask_pitch = (int64_t)L.mask_pitch;
+    if (f.points) {
+        d.points = (void *)(uintptr_t)256;
+        d.points_pitch = (int64_t)L.pts_pitch;
+        d.points_plane_stride = (int64_t)(L.pts_pitch * f.height);
+    }
     return validate_frame(&d, fmt);
 }
 

@@ -34,7 +34,7 @@ METRIC = "frames/s and % of HBM-roofline at 480×640 (batched, FP32 vs FP16 I/O)
 N_FRAMES = 256
 H, W = 480, 640
 BYTES_PER_PX = {"f32_in_f32_out": 4 + 12 + 1, "u16_in_f32_out": 2 + 12 + 1, "f16_in_f16_out": 2 + 6 + 1,
-                "f16_in_f16x4_out": 2 + 8 + 1}
+                "f16_in_f16x4_out": 2 + 8 + 1, "f32_in_oct16_out": 4 + 4 + 1, "f32_in_f32_out_points": 4 + 12 + 1 + 12}
 
 
 def parse():
@@ -340,6 +340,19 @@ def run_ours(args):
                         "frames_per_s": round(nf / (lm * 1e-3), 1),
                         "hbm_gbs": round(BYTES_PER_PX["f32_in_f32_out"] * px / (lm * 1e-3) / 1e9, 1)}
             variants.update(run_forms(torch, tfn, ctx, stream, dev, max(5, args.steps // 2)))
+            # fused outputs on the same batch: octahedral normals; normals plus the point cloud
+            oct_out = tfn.empty_normals(H, W, "oct16", dev, lead=(nf,))
+            pts = tfn.empty_points(H, W, dev, lead=(nf,))
+            for key, kw in (("fd_mean_f32_in_oct16_out", dict(output="oct16", normals=[oct_out[k] for k in range(nf)])),
+                            ("fd_mean_f32_normals_and_points", dict(normals=outs, points=[pts[k] for k in range(nf)]))):
+                fplan = ctx.plan(ins, cam, grad="fd", phi="mean", masks=mks, **kw)
+                tot, pv = time_launches(torch, lambda: fplan.launch(stream), max(5, args.steps // 2), 3, stream)
+                fplan.close()
+                lm = statistics.mean(pv)
+                bkey = "f32_in_oct16_out" if "oct16" in key else "f32_in_f32_out_points"
+                variants[key] = {"frames_per_s": round(nf / (lm * 1e-3), 1),
+                                 "hbm_gbs": round(BYTES_PER_PX[bkey] * px / (lm * 1e-3) / 1e9, 1)}
+            del oct_out, pts
         serving = None
         if not args.no_serving:
             serving = run_serving(torch, tfn, ctx, dev, d, args.serve_requests)

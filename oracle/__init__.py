@@ -23,11 +23,11 @@ _SRC = os.path.join(_HERE, "tfn_oracle.c")
 _LIB = os.path.join(_HERE, "libtfn_oracle.so")
 
 DEPTH_F32, DEPTH_F16, DISP_U16, DISP_F32, DEPTH_F64 = 0, 1, 2, 3, 100
-FD, SOBEL, SCHARR, PREWITT = 0, 1, 2, 3
+FD, SOBEL, SCHARR, PREWITT, WEIGHTED = 0, 1, 2, 3, 4
 MEAN, MEDIAN = 0, 1
 LITERAL, ALGEBRAIC = 0, 1
 
-_GRADS = {"fd": FD, "sobel": SOBEL, "scharr": SCHARR, "prewitt": PREWITT}
+_GRADS = {"fd": FD, "sobel": SOBEL, "scharr": SCHARR, "prewitt": PREWITT, "weighted": WEIGHTED}
 _PHIS = {"mean": MEAN, "median": MEDIAN}
 
 
@@ -55,6 +55,8 @@ def open_library(path: str):
     lib.tfn_oracle_normals_batch.argtypes = [p, i64, i, i, i, i, d, d, d, d, d, d, i, i, i, p, p, i]
     lib.tfn_oracle_normals_batch.restype = i
     lib.tfn_oracle_points.argtypes = [p, i64, i, i, i, d, d, d, d, d, d, p]
+    lib.tfn_oracle_normals_weighted.argtypes = [p, i64, i, i, i, d, d, d, d, d, d, i, p, i, i, p, p, p, p]
+    lib.tfn_oracle_normals_weighted.restype = i
     lib.tfn_oracle_points.restype = i
     return lib
 
@@ -90,13 +92,14 @@ def _code(table, v):
 
 
 def normals(img, fx, fy, u0, v0, *, grad="fd", phi="mean", disparity=False, baseline=1.0,
-            disp_scale=1.0 / 16, form=LITERAL, diagnostics=False, lib=None):
+            disp_scale=1.0 / 16, form=LITERAL, diagnostics=False, weights=None, lib=None):
     """Normals of one H x W image.
 
     Returns ``(n, mask)`` with ``n`` of shape (3, H, W) float64 and ``mask``
     (H, W) uint8; with ``diagnostics=True`` also ``cands`` (8, H, W; NaN where
     a neighbour gives no candidate, neighbour raster order) and ``nprime``
     (3, H, W), the unnormalised (nx, ny, n_z) of Eq. (nx2_ny2_nz2).
+    ``grad="weighted"`` takes the row weights (w0, w1, w2) in ``weights``.
     """
     img = np.ascontiguousarray(img)
     H, W = img.shape
@@ -105,9 +108,10 @@ def normals(img, fx, fy, u0, v0, *, grad="fd", phi="mean", disparity=False, base
     m = np.empty((H, W), np.uint8)
     cands = np.empty((8, H, W), np.float64) if diagnostics else None
     npr = np.empty((3, H, W), np.float64) if diagnostics else None
-    st = (lib or _load()).tfn_oracle_normals(
+    w = (ctypes.c_double * 3)(*weights) if weights is not None else None
+    st = (lib or _load()).tfn_oracle_normals_weighted(
         img.ctypes.data, img.strides[0], H, W, t, disp_scale, fx, fy, u0, v0, baseline,
-        _code(_GRADS, grad), _code(_PHIS, phi), form, n.ctypes.data, m.ctypes.data,
+        _code(_GRADS, grad), w, _code(_PHIS, phi), form, n.ctypes.data, m.ctypes.data,
         cands.ctypes.data if diagnostics else None, npr.ctypes.data if diagnostics else None)
     if st:
         raise ValueError(f"oracle rejected its arguments (status {st})")

@@ -23,7 +23,9 @@
  *      weight in either gradient filter is inside the image and valid.
  *   R3 gradients are correlations with [-1 0 1] (horizontal) and its transpose,
  *      row/column weights FD (0 1 0)/2, Sobel (1 2 1)/8, Scharr (3 10 3)/32,
- *      Prewitt (1 1 1)/6.
+ *      Prewitt (1 1 1)/6; the weighted family (the 3x3 kernels of the
+ *      brute-force search, Sec. IV) takes any row weights (w0 w1 w2) /
+ *      (2 (|w0| + |w1| + |w2|)).
  *   R4 candidates come from valid neighbours with dz != 0 only.
  *   R5 Phi = median of an even count is the mean of the two middle values.
  *   R6 if both gradients are exactly zero the normal is [0, 0, -1] (this holds
@@ -38,7 +40,7 @@
 #include <string.h>
 
 enum { OR_DEPTH_F32 = 0, OR_DEPTH_F16 = 1, OR_DISP_U16 = 2, OR_DISP_F32 = 3, OR_DEPTH_F64 = 100 };
-enum { OR_FD = 0, OR_SOBEL = 1, OR_SCHARR = 2, OR_PREWITT = 3 };
+enum { OR_FD = 0, OR_SOBEL = 1, OR_SCHARR = 2, OR_PREWITT = 3, OR_WEIGHTED = 4 };
 enum { OR_MEAN = 0, OR_MEDIAN = 1 };
 enum { OR_LITERAL = 0, OR_ALGEBRAIC = 1 };
 
@@ -85,9 +87,13 @@ static int is_valid(double s) { return isfinite(s) && s >= VALID_LO && s <= VALI
 
 /* Row weights of the 3x3 gradient filters (reading R3); the horizontal filter
  * is weight[dv] * [-1 0 1][du] / norm, the vertical one its transpose. */
-static void filter_weights(int grad, double w[3], double *norm)
+static void filter_weights(int grad, const double *custom, double w[3], double *norm)
 {
     switch (grad) {
+    case OR_WEIGHTED:
+        w[0] = custom[0]; w[1] = custom[1]; w[2] = custom[2];
+        *norm = 2 * (fabs(w[0]) + fabs(w[1]) + fabs(w[2]));
+        break;
     case OR_FD: w[0] = 0; w[1] = 1; w[2] = 0; *norm = 2; break;
     case OR_SOBEL: w[0] = 1; w[1] = 2; w[2] = 1; *norm = 8; break;
     case OR_SCHARR: w[0] = 3; w[1] = 10; w[2] = 3; *norm = 32; break;
@@ -106,6 +112,7 @@ typedef struct {
     int64_t pitch;
     int H, W, type, grad, phi, form;
     double disp_scale, fx, fy, u0, v0, tc;
+    double cw[3];          /* row weights of the weighted filter family (grad == OR_WEIGHTED) */
     double *normals;       /* 3 planes of H*W doubles */
     uint8_t *mask;         /* H*W */
     double *cands;         /* optional: 8 planes of H*W candidates (NAN = excluded) */
@@ -136,7 +143,7 @@ static void pixel(const job_t *J, int u, int v)
 
     /* Reading R2: evaluable pixels. */
     double wt[3], norm;
-    filter_weights(J->grad, wt, &norm);
+    filter_weights(J->grad, J->cw, wt, &norm);
     int evaluable = ok[1][1];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
@@ -250,7 +257,7 @@ static int check_args(const void *in, int64_t pitch, int H, int W, int type, int
     if (type != OR_DEPTH_F32 && type != OR_DEPTH_F16 && type != OR_DISP_U16 && type != OR_DISP_F32 &&
         type != OR_DEPTH_F64)
         return OR_BAD_ARG;
-    if (grad < 0 || grad > 3 || phi < 0 || phi > 1 || form < 0 || form > 1) return OR_BAD_ARG;
+    if (grad < 0 || grad > 4 || phi < 0 || phi > 1 || form < 0 || form > 1) return OR_BAD_ARG;
     if (!(fx > 0) || !(fy > 0)) return OR_BAD_ARG;
     int esz = type == OR_DEPTH_F64 ? 8 : (type == OR_DEPTH_F32 || type == OR_DISP_F32) ? 4 : 2;
     if (pitch < (int64_t)W * esz) return OR_BAD_ARG;
@@ -266,16 +273,34 @@ static int check_args(const void *in, int64_t pitch, int H, int W, int type, int
  * `mask` H*W bytes.  `cands` (8*H*W, neighbour raster order) and `nprime`
  * (3*H*W) are optional diagnostics, NULL to skip.
  */
+int tfn_oracle_normals_weighted(const void *in, int64_t pitch, int H, int W, int type, double disp_scale,
+                                double fx, double fy, double u0, double v0, double tc, int grad,
+                                const double *weights, int phi, int form, double *normals, uint8_t *mask,
+                                double *cands, double *nprime)
+{
+    int st = check_args(in, pitch, H, W, type, grad, phi, form, fx, fy, tc, disp_scale);
+    if (st || !normals || !mask) return st ? st : OR_BAD_ARG;
+    if (grad == OR_WEIGHTED) {
+        if (!weights) return OR_BAD_ARG;
+        for (int k = 0; k < 3; ++k)
+            if (!isfinite(weights[k])) return OR_BAD_ARG;
+        if (weights[0] == 0 && weights[1] == 0 && weights[2] == 0) return OR_BAD_ARG;
+    }
+    job_t J = {in, pitch, H, W, type, grad, phi, form, disp_scale, fx, fy, u0, v0, tc, {0, 0, 0},
+               normals, mask, cands, nprime};
+    if (grad == OR_WEIGHTED)
+        for (int k = 0; k < 3; ++k) J.cw[k] = weights[k];
+    run_rows(&J, 0, H);
+    return OR_OK;
+}
+
 int tfn_oracle_normals(const void *in, int64_t pitch, int H, int W, int type, double disp_scale,
                        double fx, double fy, double u0, double v0, double tc, int grad, int phi,
                        int form, double *normals, uint8_t *mask, double *cands, double *nprime)
 {
-    int st = check_args(in, pitch, H, W, type, grad, phi, form, fx, fy, tc, disp_scale);
-    if (st || !normals || !mask) return st ? st : OR_BAD_ARG;
-    job_t J = {in, pitch, H, W, type, grad, phi, form, disp_scale, fx, fy, u0, v0, tc,
-               normals, mask, cands, nprime};
-    run_rows(&J, 0, H);
-    return OR_OK;
+    if (grad == OR_WEIGHTED) return OR_BAD_ARG; /* needs its weights: tfn_oracle_normals_weighted */
+    return tfn_oracle_normals_weighted(in, pitch, H, W, type, disp_scale, fx, fy, u0, v0, tc, grad, NULL, phi, form,
+                                       normals, mask, cands, nprime);
 }
 
 typedef struct {
@@ -307,14 +332,14 @@ int tfn_oracle_normals_batch(const void *in, int64_t pitch, int n, int H, int W,
                              uint8_t *mask, int threads)
 {
     int st = check_args(in, pitch, H, W, type, grad, phi, form, fx, fy, tc, disp_scale);
-    if (st || !normals || !mask || n < 0) return st ? st : OR_BAD_ARG;
+    if (st || !normals || !mask || n < 0 || grad == OR_WEIGHTED) return st ? st : OR_BAD_ARG;
     if (threads < 1) threads = 1;
     job_t *jobs = (job_t *)calloc(n > 0 ? n : 1, sizeof(job_t));
     if (!jobs) return OR_BAD_ARG;
     const int64_t HW = (int64_t)H * W;
     for (int k = 0; k < n; ++k) {
         job_t J = {(const char *)in + (int64_t)k * H * pitch, pitch, H, W, type, grad, phi, form,
-                   disp_scale, fx, fy, u0, v0, tc, normals + 3 * HW * k, mask + HW * k, NULL, NULL};
+                   disp_scale, fx, fy, u0, v0, tc, {0, 0, 0}, normals + 3 * HW * k, mask + HW * k, NULL, NULL};
         jobs[k] = J;
     }
     pool_t P = {jobs, n, 0, PTHREAD_MUTEX_INITIALIZER};

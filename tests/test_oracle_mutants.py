@@ -13,6 +13,7 @@ import pytest
 import oracle
 from tests import test_oracle_pins as pins
 from tests import test_oracle_points as point_pins
+from tests import test_oracle_weighted as weighted_pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "tfn_oracle.c")
 
@@ -53,6 +54,11 @@ MUTANTS = {
     "points_wrong_focal": ("Y = Z * (v - v0) / fy;", "Y = Z * (v - v0) / fx;"),
     "points_swapped_principal_point": ("X = Z * (u - u0) / fx;", "X = Z * (u - v0) / fx;"),
     "points_disparity_without_baseline": ("Z = disparity ? fx * tc / s : s;", "Z = disparity ? fx / s : s;"),
+    # the weighted filter family
+    "weighted_reversed": ("w[0] = custom[0]; w[1] = custom[1]; w[2] = custom[2];",
+                          "w[0] = custom[2]; w[1] = custom[1]; w[2] = custom[0];"),
+    "weighted_ignores_weights": ("w[0] = custom[0]; w[1] = custom[1]; w[2] = custom[2];",
+                                 "w[0] = 1; w[1] = 2; w[2] = 1;"),
     "points_keep_holes": ("double X = 0, Y = 0, Z = 0;\n            if (ok) {", "double X = 0, Y = 0, Z = 0;\n            if (1) {"),
 }
 
@@ -61,6 +67,8 @@ def _pins_fail(lib):
     if pins.check_golden(lib):
         return True
     if point_pins.check_points(lib):
+        return True
+    if weighted_pins.check_weighted(lib):
         return True
     for grad in pins.GRADS:
         for phi in pins.PHIS:

@@ -353,6 +353,13 @@ def run_ours(args):
                 variants[key] = {"frames_per_s": round(nf / (lm * 1e-3), 1),
                                  "hbm_gbs": round(BYTES_PER_PX[bkey] * px / (lm * 1e-3) / 1e9, 1)}
             del oct_out, pts
+            # the weighted gradient family (the kernel search space), weights (1 3 1)
+            wplan = ctx.plan(ins, cam, grad="weighted", phi="mean", weights=(1.0, 3.0, 1.0), normals=outs, masks=mks)
+            tot, pv = time_launches(torch, lambda: wplan.launch(stream), max(5, args.steps // 2), 3, stream)
+            wplan.close()
+            lm = statistics.mean(pv)
+            variants["weighted_131_mean_f32"] = {"frames_per_s": round(nf / (lm * 1e-3), 1),
+                                                 "hbm_gbs": round(BYTES_PER_PX["f32_in_f32_out"] * px / (lm * 1e-3) / 1e9, 1)}
         serving = None
         if not args.no_serving:
             serving = run_serving(torch, tfn, ctx, dev, d, args.serve_requests)

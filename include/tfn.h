@@ -78,8 +78,18 @@ typedef enum tfn_input {
 
 /* Gradient filters (Sec. III; Sec. IV-B compares them): correlation with
  * [-1 0 1] horizontally (its transpose vertically), row weights
- * FD (0 1 0), Sobel (1 2 1), Scharr (3 10 3), Prewitt (1 1 1). */
-typedef enum tfn_grad { TFN_GRAD_FD = 0, TFN_GRAD_SOBEL = 1, TFN_GRAD_SCHARR = 2, TFN_GRAD_PREWITT = 3 } tfn_grad;
+ * FD (0 1 0), Sobel (1 2 1), Scharr (3 10 3), Prewitt (1 1 1), or any row
+ * weights (w0 w1 w2) given in tfn_method.weights (TFN_GRAD_WEIGHTED: the 3x3
+ * kernels of the paper's brute-force kernel search, Sec. IV-B).  A pixel is
+ * evaluable when it and every tap with a non-zero weight in either filter are
+ * valid. */
+typedef enum tfn_grad {
+    TFN_GRAD_FD = 0,
+    TFN_GRAD_SOBEL = 1,
+    TFN_GRAD_SCHARR = 2,
+    TFN_GRAD_PREWITT = 3,
+    TFN_GRAD_WEIGHTED = 4
+} tfn_grad;
 
 /* Phi of Eq. (nx2_ny2_nz2). */
 typedef enum tfn_phi { TFN_PHI_MEAN = 0, TFN_PHI_MEDIAN = 1 } tfn_phi;
@@ -139,10 +149,12 @@ typedef struct tfn_frame {
 
 /* Method selection. */
 typedef struct tfn_method {
-    int32_t grad;   /* tfn_grad */
-    int32_t phi;    /* tfn_phi */
-    int32_t output; /* tfn_output */
-    int32_t flags;  /* TFN_FLAG_* */
+    int32_t grad;     /* tfn_grad */
+    int32_t phi;      /* tfn_phi */
+    int32_t output;   /* tfn_output */
+    int32_t flags;    /* TFN_FLAG_* */
+    float weights[3]; /* TFN_GRAD_WEIGHTED: row weights (w0 w1 w2), finite, not all 0; else ignored */
+    int32_t reserved; /* 0 */
 } tfn_method;
 
 /* Compute every pixel on the compensated (double-float) path instead of only

@@ -26,13 +26,14 @@ _lib = ctypes.CDLL(LIB_PATH)
 TFN_OK, TFN_ERR_INVALID_ARG, TFN_ERR_UNSUPPORTED, TFN_ERR_MISALIGNED, TFN_ERR_OUT_OF_MEMORY, TFN_ERR_CUDA, \
     TFN_ERR_TIMEOUT, TFN_ERR_CANCELLED, TFN_ERR_BUSY, TFN_ERR_DEVICE, TFN_ERR_IO = range(11)
 TFN_DEPTH_F32, TFN_DEPTH_F16, TFN_DISP_U16, TFN_DISP_F32 = range(4)
-TFN_GRAD_FD, TFN_GRAD_SOBEL, TFN_GRAD_SCHARR, TFN_GRAD_PREWITT = range(4)
+TFN_GRAD_FD, TFN_GRAD_SOBEL, TFN_GRAD_SCHARR, TFN_GRAD_PREWITT, TFN_GRAD_WEIGHTED = range(5)
 TFN_PHI_MEAN, TFN_PHI_MEDIAN = range(2)
 TFN_OUT_F32, TFN_OUT_F16, TFN_OUT_BF16, TFN_OUT_F16X4, TFN_OUT_BF16X4, TFN_OUT_OCT16 = range(6)
 TFN_FLAG_REFINE_ALL = 1
 TFN_REQ_HOST = 1
 
-GRADS = {"fd": TFN_GRAD_FD, "sobel": TFN_GRAD_SOBEL, "scharr": TFN_GRAD_SCHARR, "prewitt": TFN_GRAD_PREWITT}
+GRADS = {"fd": TFN_GRAD_FD, "sobel": TFN_GRAD_SOBEL, "scharr": TFN_GRAD_SCHARR, "prewitt": TFN_GRAD_PREWITT,
+         "weighted": TFN_GRAD_WEIGHTED}
 PHIS = {"mean": TFN_PHI_MEAN, "median": TFN_PHI_MEDIAN}
 OUTPUTS = {"f32": TFN_OUT_F32, "f16": TFN_OUT_F16, "bf16": TFN_OUT_BF16, "f16x4": TFN_OUT_F16X4,
            "bf16x4": TFN_OUT_BF16X4, "oct16": TFN_OUT_OCT16}
@@ -57,7 +58,7 @@ class tfn_frame(ctypes.Structure):
 
 class tfn_method(ctypes.Structure):
     _fields_ = [("grad", ctypes.c_int32), ("phi", ctypes.c_int32), ("output", ctypes.c_int32),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("weights", ctypes.c_float * 3), ("reserved", ctypes.c_int32)]
 
 
 class tfn_server_opts(ctypes.Structure):
@@ -270,12 +271,15 @@ def make_frame(inp, normals, mask, cam, disparity=False, disp_scale=1.0 / 16, ou
     return f
 
 
-def make_method(grad="fd", phi="mean", output="f32", flags=0) -> tfn_method:
+def make_method(grad="fd", phi="mean", output="f32", flags=0, weights=None) -> tfn_method:
+    """grad="weighted" takes the row weights (w0, w1, w2) of the gradient filter in `weights`."""
     m = tfn_method()
     m.grad = GRADS[grad] if isinstance(grad, str) else grad
     m.phi = PHIS[phi] if isinstance(phi, str) else phi
     m.output = OUTPUTS[output] if isinstance(output, str) else output
     m.flags = flags
+    if weights is not None:
+        m.weights = (ctypes.c_float * 3)(*weights)
     return m
 
 
@@ -313,7 +317,7 @@ class Context:
         self.close()
 
     def normals(self, inp, cam, *, grad="fd", phi="mean", output="f32", disparity=False, disp_scale=1.0 / 16,
-                normals=None, mask=None, points=None, stream=None, flags=0):
+                normals=None, mask=None, points=None, stream=None, flags=0, weights=None):
         """Normals of one (H, W) device image -> (normals, mask); `points` (3, H, W) also receives the
         back-projected point cloud."""
         H, W = inp.shape
@@ -322,12 +326,12 @@ class Context:
         if mask is None:
             mask = empty_image((H, W), _torch().uint8, inp.device)
         f = make_frame(inp, normals, mask, cam, disparity, disp_scale, output, points)
-        m = make_method(grad, phi, output, flags)
+        m = make_method(grad, phi, output, flags, weights)
         check(tfn_normals(self.handle, ctypes.byref(f), ctypes.byref(m), _stream_handle(stream)), "tfn_normals")
         return normals, mask
 
     def normals_batch(self, inputs, cams, *, grad="fd", phi="mean", output="f32", disparity=False,
-                      disp_scale=1.0 / 16, normals=None, masks=None, points=None, stream=None, flags=0):
+                      disp_scale=1.0 / 16, normals=None, masks=None, points=None, stream=None, flags=0, weights=None):
         """Normals of a list of (H_i, W_i) device images (or an (N, H, W) stack) in one launch."""
         n = len(inputs)
         if isinstance(cams, dict):
@@ -338,25 +342,25 @@ class Context:
             masks = [empty_image(tuple(x.shape), _torch().uint8, x.device) for x in inputs]
         frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output,
                                               points[k] if points is not None else None) for k in range(n)])
-        m = make_method(grad, phi, output, flags)
+        m = make_method(grad, phi, output, flags, weights)
         check(tfn_normals_batch(self.handle, frames, n, ctypes.byref(m), _stream_handle(stream)), "tfn_normals_batch")
         return normals, masks
 
     def normals_batch_host(self, inputs, cams, normals, masks, *, grad="fd", phi="mean", output="f32",
-                           disparity=False, disp_scale=1.0 / 16, points=None, stream=None, flags=0):
+                           disparity=False, disp_scale=1.0 / 16, points=None, stream=None, flags=0, weights=None):
         """Like normals_batch, with every tensor in host memory (pinned is fastest); synchronous."""
         n = len(inputs)
         if isinstance(cams, dict):
             cams = [cams] * n
         frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output,
                                               points[k] if points is not None else None) for k in range(n)])
-        m = make_method(grad, phi, output, flags)
+        m = make_method(grad, phi, output, flags, weights)
         check(tfn_normals_batch_host(self.handle, frames, n, ctypes.byref(m), _stream_handle(stream)),
               "tfn_normals_batch_host")
         return normals, masks
 
     def plan(self, inputs, cams, *, grad="fd", phi="mean", output="f32", disparity=False, disp_scale=1.0 / 16,
-             normals=None, masks=None, points=None, flags=0):
+             normals=None, masks=None, points=None, flags=0, weights=None):
         """Freezes a batch into a Plan (descriptors uploaded once, launches captured in a CUDA graph)."""
         n = len(inputs)
         if isinstance(cams, dict):
@@ -367,7 +371,7 @@ class Context:
             masks = [empty_image(tuple(x.shape), _torch().uint8, x.device) for x in inputs]
         frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output,
                                               points[k] if points is not None else None) for k in range(n)])
-        m = make_method(grad, phi, output, flags)
+        m = make_method(grad, phi, output, flags, weights)
         h = ctypes.c_void_p()
         check(tfn_plan_create(self.handle, frames, n, ctypes.byref(m), ctypes.byref(h)), "tfn_plan_create")
         return Plan(h, inputs, normals, masks)
@@ -377,7 +381,7 @@ class Context:
         check(tfn_set_tile_shape(self.handle, index), "tfn_set_tile_shape")
 
     def autotune(self, inputs, cams, *, grad="fd", phi="mean", output="f32", disparity=False, disp_scale=1.0 / 16,
-                 normals=None, masks=None, reps=10, stream=None):
+                 normals=None, masks=None, reps=10, stream=None, weights=None):
         """Times every tile shape on this batch; returns (best index, [ms per run of each shape])."""
         n = len(inputs)
         if isinstance(cams, dict):
@@ -388,7 +392,7 @@ class Context:
             masks = [empty_image(tuple(x.shape), _torch().uint8, x.device) for x in inputs]
         frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output)
                                    for k in range(n)])
-        m = make_method(grad, phi, output)
+        m = make_method(grad, phi, output, 0, weights)
         best = ctypes.c_int()
         ms = (ctypes.c_float * tfn_tile_shape_count())()
         check(tfn_autotune(self.handle, frames, n, ctypes.byref(m), reps, _stream_handle(stream), ctypes.byref(best),
@@ -461,9 +465,9 @@ class Server:
     alive until wait() returns for their ticket."""
 
     def __init__(self, ctx: Context, *, grad="fd", phi="mean", output="f32", flags=0, mem_budget=0,
-                 max_batch=0, max_queue=0, max_delay_us=0, pipelines=0):
+                 max_batch=0, max_queue=0, max_delay_us=0, pipelines=0, weights=None):
         o = tfn_server_opts()
-        o.method = make_method(grad, phi, output, flags)
+        o.method = make_method(grad, phi, output, flags, weights)
         o.mem_budget_bytes = mem_budget
         o.max_batch_frames, o.max_queue, o.max_delay_us, o.pipelines = max_batch, max_queue, max_delay_us, pipelines
         h = ctypes.c_void_p()

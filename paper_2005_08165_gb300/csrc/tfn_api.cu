@@ -115,6 +115,11 @@ tfn_status validate_method(const tfn_method *m)
     if (m->grad < 0 || m->grad >= GRAD_COUNT || m->phi < 0 || m->phi >= PHI_COUNT || m->output < 0 ||
         m->output > OUT_OCT16 || (m->flags & ~TFN_FLAG_REFINE_ALL))
         return TFN_ERR_INVALID_ARG;
+    if (m->grad == GRAD_WEIGHTED) {
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(m->weights[k])) return TFN_ERR_INVALID_ARG;
+        if (m->weights[0] == 0.f && m->weights[1] == 0.f && m->weights[2] == 0.f) return TFN_ERR_INVALID_ARG;
+    }
     return TFN_OK;
 }
 
@@ -272,6 +277,8 @@ tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDes
     a.total_tiles = total_tiles;
     a.out_fmt = m.output;
     a.flags = m.flags;
+    for (int k = 0; k < 3; ++k) a.w[k] = m.grad == GRAD_WEIGHTED ? m.weights[k] : 0.f;
+    a.pad = 0;
     void *params[] = {&a};
     if (!cuda_ok(cudaLaunchKernel((const void *)fn, dim3(grid), dim3(threads), params, smem, stream),
                  "cudaLaunchKernel"))

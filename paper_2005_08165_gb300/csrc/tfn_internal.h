@@ -8,7 +8,7 @@
 namespace tfn {
 
 enum Kind { KIND_DEPTH_F32 = 0, KIND_DEPTH_F16 = 1, KIND_DISP_U16 = 2, KIND_DISP_F32 = 3, KIND_COUNT = 4 };
-enum Grad { GRAD_FD = 0, GRAD_SOBEL = 1, GRAD_SCHARR = 2, GRAD_PREWITT = 3, GRAD_COUNT = 4 };
+enum Grad { GRAD_FD = 0, GRAD_SOBEL = 1, GRAD_SCHARR = 2, GRAD_PREWITT = 3, GRAD_WEIGHTED = 4, GRAD_COUNT = 5 };
 enum Phi { PHI_MEAN = 0, PHI_MEDIAN = 1, PHI_COUNT = 2 };
 enum OutFmt { OUT_F32 = 0, OUT_F16 = 1, OUT_BF16 = 2, OUT_F16X4 = 3, OUT_BF16X4 = 4, OUT_OCT16 = 5 };
 
@@ -47,6 +47,8 @@ struct LaunchArgs {
     int32_t total_tiles;
     int32_t out_fmt;
     int32_t flags;
+    float w[3];               // GRAD_WEIGHTED: row weights (w0 w1 w2)
+    int32_t pad;
 };
 
 // Work-item shapes the kernels are compiled for.  An item is a band of tw =

@@ -203,12 +203,32 @@ __device__ __forceinline__ df filter_sum(df t0, df t1, df t2)
     return {s2.h, lo};
 }
 
+// Weighted filter sum G = w0 T0 + w1 T1 + w2 T2 with the caller's row weights
+// (the weighted family), compensated like Scharr's: error-free products and
+// sums.  A zero-weight row drops out entirely (its taps may be holes).
+__device__ __forceinline__ df filter_sum_w(df t0, df t1, df t2, float w0, float w1, float w2)
+{
+    const df z = {0.f, 0.f};
+    const df a = w0 != 0.f ? t0 : z, b = w1 != 0.f ? t1 : z, c = w2 != 0.f ? t2 : z;
+    const df p0 = two_prod(w0, a.h), p1 = two_prod(w1, b.h), p2 = two_prod(w2, c.h);
+    const df s = two_sum(p0.h, p1.h);
+    const df s2 = two_sum(s.h, p2.h);
+    float lo = __fadd_rn(__fadd_rn(s.l, s2.l), __fadd_rn(__fadd_rn(p0.l, p1.l), p2.l));
+    lo = __fadd_rn(lo, __fmaf_rn(w0, a.l, __fmaf_rn(w1, b.l, __fmul_rn(w2, c.l))));
+    return {s2.h, lo};
+}
+
 template <int KIND, int GRAD>
-__device__ __forceinline__ void gradients(const float (&z)[3][3], df &Gu, df &Gv)
+__device__ __forceinline__ void gradients(const float (&z)[3][3], df &Gu, df &Gv, float w0, float w1, float w2)
 {
     if (GRAD == GRAD_FD) {
         Gu = grad_term<KIND>(z[1][0], z[1][2]);
         Gv = grad_term<KIND>(z[0][1], z[2][1]);
+    } else if (GRAD == GRAD_WEIGHTED) {
+        Gu = filter_sum_w(grad_term<KIND>(z[0][0], z[0][2]), grad_term<KIND>(z[1][0], z[1][2]),
+                          grad_term<KIND>(z[2][0], z[2][2]), w0, w1, w2);
+        Gv = filter_sum_w(grad_term<KIND>(z[0][0], z[2][0]), grad_term<KIND>(z[0][1], z[2][1]),
+                          grad_term<KIND>(z[0][2], z[2][2]), w0, w1, w2);
     } else {
         Gu = filter_sum<GRAD>(grad_term<KIND>(z[0][0], z[0][2]), grad_term<KIND>(z[1][0], z[1][2]),
                               grad_term<KIND>(z[2][0], z[2][2]));
@@ -245,14 +265,14 @@ struct Vec3 {
 template <int KIND, int GRAD, int PHI>
 __device__ __noinline__ Vec3 refine_pixel(float z00, float z01, float z02, float z10, float z11, float z12, float z20,
                                           float z21, float z22, unsigned okbits, int u, int v, float fx, float fy,
-                                          float u0, float v0)
+                                          float u0, float v0, float w0, float w1, float w2)
 {
     const float z[3][3] = {{z00, z01, z02}, {z10, z11, z12}, {z20, z21, z22}};
     bool ok[3][3];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) ok[a][b] = (okbits >> (3 * a + b)) & 1u;
     df Gu, Gv;
-    gradients<KIND, GRAD>(z, Gu, Gv);
+    gradients<KIND, GRAD>(z, Gu, Gv, w0, w1, w2);
     const float zi = z[1][1];
     df R[8];
     int m = 0;
@@ -512,8 +532,8 @@ __device__ __forceinline__ void carry_down(const Row<KIND, GRAD> &C, const Row<K
 template <int KIND, int GRAD, int PHI>
 __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIND, GRAD> &C, const Row<KIND, GRAD> &N,
                                          UpCarry &cy, const float (&uc)[4], float vc, float fx, float fy, float thr,
-                                         float (&ox)[4], float (&oy)[4], float (&oz)[4], uint32_t &mword,
-                                         unsigned &rbits)
+                                         const float (&wts)[3], float (&ox)[4], float (&oy)[4], float (&oz)[4],
+                                         uint32_t &mword, unsigned &rbits)
 {
     // edges of this row (c -> c+1) and to the row below, computed pixel by
     // pixel: pixel c needs those of columns c-1 and c only
@@ -547,6 +567,22 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
             Gu = fd_term<KIND>(C.z[c - 1], C.z[c + 1]);
             Gv = fd_term<KIND>(P.z[c], N.z[c]);
             ev_ok = fmaxf(fmaxf(fmaxf(C.z[c - 1], zi), C.z[c + 1]), fmaxf(P.z[c], N.z[c])) <= kValidHi;
+        } else if constexpr (GRAD == GRAD_WEIGHTED) {
+            const float w0 = wts[0], w1 = wts[1], w2 = wts[2];
+            Gu = filter_sum_w(tap_diff(P, c - 1, P, c + 1), tap_diff(C, c - 1, C, c + 1), tap_diff(N, c - 1, N, c + 1),
+                              w0, w1, w2);
+            Gv = filter_sum_w(tap_diff(P, c - 1, N, c - 1), tap_diff(P, c, N, c), tap_diff(P, c + 1, N, c + 1), w0,
+                              w1, w2);
+            // tap (row a, column b) is needed when its row's weight is non-zero in the horizontal
+            // filter (outer columns) or its column's weight in the vertical one (outer rows)
+            const bool n0 = w0 != 0.f, n1 = w1 != 0.f, n2 = w2 != 0.f;
+            float mx = zi;
+            mx = fmaxf(mx, n0 ? P.z[c - 1] : 0.f);
+            mx = fmaxf(mx, (n0 || n2) ? P.z[c + 1] : 0.f);
+            mx = fmaxf(mx, (n0 || n2) ? N.z[c - 1] : 0.f);
+            mx = fmaxf(mx, n2 ? N.z[c + 1] : 0.f);
+            mx = fmaxf(mx, n1 ? fmaxf(fmaxf(P.z[c], N.z[c]), fmaxf(C.z[c - 1], C.z[c + 1])) : 0.f);
+            ev_ok = mx <= kValidHi;
         } else {
             Gu = filter_sum<GRAD>(tap_diff(P, c - 1, P, c + 1), tap_diff(C, c - 1, C, c + 1),
                                   tap_diff(N, c - 1, N, c + 1));
@@ -859,7 +895,7 @@ __device__ __forceinline__ void store1(const OutDesc &fd, int fmt, int u, int v,
 // main loop never waits on it.
 template <int KIND, int GRAD, int PHI>
 __device__ __noinline__ Vec3 refine_from_input(const void *in, int64_t pitch, int H, int W, int x, int y, float fx,
-                                               float fy, float u0, float v0)
+                                               float fy, float u0, float v0, float w0, float w1, float w2)
 {
     typedef typename KindTraits<KIND>::T T;
     float z[9];
@@ -876,7 +912,7 @@ __device__ __noinline__ Vec3 refine_from_input(const void *in, int64_t pitch, in
             okb |= (v <= kValidHi ? 1u : 0u) << (3 * a + b);
         }
     return refine_pixel<KIND, GRAD, PHI>(z[0], z[1], z[2], z[3], z[4], z[5], z[6], z[7], z[8], okb, x, y, fx, fy, u0,
-                                         v0);
+                                         v0, w0, w1, w2);
 }
 
 // ------------------------------------------------------------ the kernel
@@ -953,6 +989,7 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
         for (int cc = 0; cc < NST; ++cc) issue(cc);
 
     const bool refine_all = args.flags & TFN_FLAG_REFINE_ALL;  // a negative threshold refines every pixel
+    const float wts[3] = {args.w[0], args.w[1], args.w[2]};  // GRAD_WEIGHTED's row weights
     int cf = 0, fail_cc = 0;
     unsigned nref = 0;
     bool failed = false;
@@ -1027,7 +1064,7 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
             float ox[4], oy[4], oz[4];
             uint32_t mw;
             unsigned rb;
-            row_step<KIND, GRAD, PHI>(P, C, N, cy, uc, __fsub_rn((float)y, v0), fx, fy, thr, ox, oy, oz, mw, rb);
+            row_step<KIND, GRAD, PHI>(P, C, N, cy, uc, __fsub_rn((float)y, v0), fx, fy, thr, wts, ox, oy, oz, mw, rb);
             if (y < H && nvalid > 0) {
                 store4(out, args.out_fmt, x0, y, nvalid, ox, oy, oz, mw);
                 if (pts.pts)  // the fused point cloud of this row
@@ -1075,7 +1112,7 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
             }
             const int x = x0 + (b & 3), y = y0 + (b >> 2);
             store1(out, args.out_fmt, x, y,
-                   refine_from_input<KIND, GRAD, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0));
+                   refine_from_input<KIND, GRAD, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0, wts[0], wts[1], wts[2]));
             ++nref;
         }
     }
@@ -1103,7 +1140,7 @@ KernelFn select_kernel(int grad, int phi, int cfg)
     if (grad == G && phi == P && cfg == C) return &normals_kernel<KIND, G, P, C>;
 #define TFN_KC(G, P) TFN_K(G, P, 0) TFN_K(G, P, 1) TFN_K(G, P, 2) TFN_K(G, P, 3)
 #define TFN_KP(G) TFN_KC(G, PHI_MEAN) TFN_KC(G, PHI_MEDIAN)
-    TFN_KP(GRAD_FD) TFN_KP(GRAD_SOBEL) TFN_KP(GRAD_SCHARR) TFN_KP(GRAD_PREWITT)
+    TFN_KP(GRAD_FD) TFN_KP(GRAD_SOBEL) TFN_KP(GRAD_SCHARR) TFN_KP(GRAD_PREWITT) TFN_KP(GRAD_WEIGHTED)
 #undef TFN_KP
 #undef TFN_KC
 #undef TFN_K

@@ -36,11 +36,11 @@ def median_gap_bound(cands, nprime, idx):
 
 
 def compare(gpu_n, gpu_m, img, cam, *, grad, phi, disparity=False, baseline=1.0, disp_scale=1.0 / 16,
-            tol=TOL_DEG):
+            tol=TOL_DEG, weights=None):
     """Raises AssertionError with details when the GPU result breaks the rules; returns stats."""
     ref_n, ref_m, cands, npr = oracle.normals(img, cam["fx"], cam["fy"], cam["u0"], cam["v0"], grad=grad, phi=phi,
                                               disparity=disparity, baseline=baseline, disp_scale=disp_scale,
-                                              diagnostics=True)
+                                              diagnostics=True, weights=weights)
     gpu_n = np.asarray(gpu_n, np.float64)
     gpu_m = np.asarray(gpu_m)
     bad_mask = gpu_m != ref_m

@@ -147,6 +147,50 @@ def test_refine_all_path_is_tight(torch, tfn, ctx, grad, phi):
         assert st["over"] == 0 or phi == "median"
 
 
+WEIGHTS = [(1.0, 3.0, 1.0), (1.0, 0.0, 0.0), (2.0, -1.0, 0.5), (0.0, 1.0, 0.0)]
+
+
+@pytest.mark.parametrize("weights", WEIGHTS)
+@pytest.mark.parametrize("phi", PHIS)
+def test_weighted_gradient_family(torch, tfn, ctx, weights, phi):
+    frames = depth_frames(SIZES, 2100)
+    inputs = [to_dev(torch, tfn, img) for img, _ in frames]
+    cams = [cam for _, cam in frames]
+    n, m = ctx.normals_batch(inputs, cams, grad="weighted", phi=phi, weights=weights)
+    torch.cuda.synchronize()
+    for k, (img, cam) in enumerate(frames):
+        compare(n[k].cpu().numpy(), m[k].cpu().numpy(), img, cam, grad="weighted", phi=phi, weights=weights)
+    # u16 disparity too
+    dframes = disparity_frames([(67, 131)], 2150)
+    raw, cam = dframes[0]
+    dn, dm = ctx.normals(to_dev(torch, tfn, raw), cam, grad="weighted", phi=phi, weights=weights, disparity=True)
+    torch.cuda.synchronize()
+    compare(dn.cpu().numpy(), dm.cpu().numpy(), raw, cam, grad="weighted", phi=phi, disparity=True, baseline=0.1,
+            weights=weights)
+
+
+def test_weighted_family_double_float_path_and_shapes(torch, tfn, ctx):
+    img, cam = depth_frames([(61, 99)], 2200)[0]
+    d = to_dev(torch, tfn, img)
+    w = (1.0, 0.7, 0.2)
+    n, m = ctx.normals(d, cam, grad="weighted", weights=w, flags=tfn.TFN_FLAG_REFINE_ALL)
+    torch.cuda.synchronize()
+    compare(n.cpu().numpy(), m.cpu().numpy(), img, cam, grad="weighted", phi="mean", weights=w, tol=1e-5)
+    ref = None
+    with tfn.Context(0) as c:
+        for shape in range(tfn.tfn_tile_shape_count()):
+            c.set_tile_shape(shape)
+            nn, mm = c.normals(d, cam, grad="weighted", weights=w)
+            torch.cuda.synchronize()
+            got = (nn.cpu(), mm.cpu())
+            if ref is None:
+                ref = got
+            assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1]), f"shape {shape} differs"
+    with pytest.raises(tfn.TfnError) as e:
+        ctx.normals(d, cam, grad="weighted", weights=(0.0, 0.0, 0.0))
+    assert e.value.status == tfn.TFN_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("output", ["f16", "bf16", "f16x4", "bf16x4"])
 def test_reduced_precision_outputs_round_the_f32_result(torch, tfn, ctx, output):
     img, cam = depth_frames([(61, 99)], 1100)[0]

@@ -23,11 +23,12 @@ _SRC = os.path.join(_HERE, "tfn_oracle.c")
 _LIB = os.path.join(_HERE, "libtfn_oracle.so")
 
 DEPTH_F32, DEPTH_F16, DISP_U16, DISP_F32, DEPTH_F64 = 0, 1, 2, 3, 100
-FD, SOBEL, SCHARR, PREWITT, WEIGHTED = 0, 1, 2, 3, 4
+FD, SOBEL, SCHARR, PREWITT, WEIGHTED, SEP5, FD5, SOBEL5, PREWITT5 = 0, 1, 2, 3, 4, 5, 6, 7, 8
 MEAN, MEDIAN = 0, 1
 LITERAL, ALGEBRAIC = 0, 1
 
-_GRADS = {"fd": FD, "sobel": SOBEL, "scharr": SCHARR, "prewitt": PREWITT, "weighted": WEIGHTED}
+_GRADS = {"fd": FD, "sobel": SOBEL, "scharr": SCHARR, "prewitt": PREWITT, "weighted": WEIGHTED, "sep5": SEP5,
+          "fd5": FD5, "sobel5": SOBEL5, "prewitt5": PREWITT5}
 _PHIS = {"mean": MEAN, "median": MEDIAN}
 
 
@@ -99,7 +100,9 @@ def normals(img, fx, fy, u0, v0, *, grad="fd", phi="mean", disparity=False, base
     (H, W) uint8; with ``diagnostics=True`` also ``cands`` (8, H, W; NaN where
     a neighbour gives no candidate, neighbour raster order) and ``nprime``
     (3, H, W), the unnormalised (nx, ny, n_z) of Eq. (nx2_ny2_nz2).
-    ``grad="weighted"`` takes the row weights (w0, w1, w2) in ``weights``.
+    ``grad="weighted"`` takes the row weights (w0, w1, w2) in ``weights``; ``grad="sep5"`` takes the
+    5x5 separable profiles (d1, d2, s0, s1, s2) (reading R15); "fd5", "sobel5" and "prewitt5" are its
+    named members.
     """
     img = np.ascontiguousarray(img)
     H, W = img.shape
@@ -108,7 +111,7 @@ def normals(img, fx, fy, u0, v0, *, grad="fd", phi="mean", disparity=False, base
     m = np.empty((H, W), np.uint8)
     cands = np.empty((8, H, W), np.float64) if diagnostics else None
     npr = np.empty((3, H, W), np.float64) if diagnostics else None
-    w = (ctypes.c_double * 3)(*weights) if weights is not None else None
+    w = (ctypes.c_double * len(weights))(*weights) if weights is not None else None
     st = (lib or _load()).tfn_oracle_normals_weighted(
         img.ctypes.data, img.strides[0], H, W, t, disp_scale, fx, fy, u0, v0, baseline,
         _code(_GRADS, grad), w, _code(_PHIS, phi), form, n.ctypes.data, m.ctypes.data,

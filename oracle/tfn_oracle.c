@@ -26,6 +26,15 @@
  *      Prewitt (1 1 1)/6; the weighted family (the 3x3 kernels of the
  *      brute-force search, Sec. IV) takes any row weights (w0 w1 w2) /
  *      (2 (|w0| + |w1| + |w2|)).
+ *   R15 filter sizes (Fig. 2 compares "types and sizes"): a 5x5 gradient filter
+ *      is separable, an antisymmetric derivative profile (d1 at offsets +-1,
+ *      d2 at +-2) along its axis times a symmetric smoothing profile (s0 at 0,
+ *      s1 at +-1, s2 at +-2) across it, divided by
+ *      2 (d1 + 2 d2) (s0 + 2 s1 + 2 s2), so that it returns the derivative of
+ *      an affine image (both sums must be non-zero).  Named members: FD5
+ *      (8 -1 | 1 0 0), the fourth-order central difference; Sobel5
+ *      (2 1 | 6 4 1), the binomial pair; Prewitt5 (1 2 | 1 1 1), the box pair.
+ *      The candidates and Phi keep the 8-connected neighbourhood (Sec. V-A).
  *   R4 candidates come from valid neighbours with dz != 0 only.
  *   R5 Phi = median of an even count is the mean of the two middle values.
  *   R6 if both gradients are exactly zero the normal is [0, 0, -1] (this holds
@@ -40,7 +49,8 @@
 #include <string.h>
 
 enum { OR_DEPTH_F32 = 0, OR_DEPTH_F16 = 1, OR_DISP_U16 = 2, OR_DISP_F32 = 3, OR_DEPTH_F64 = 100 };
-enum { OR_FD = 0, OR_SOBEL = 1, OR_SCHARR = 2, OR_PREWITT = 3, OR_WEIGHTED = 4 };
+enum { OR_FD = 0, OR_SOBEL = 1, OR_SCHARR = 2, OR_PREWITT = 3, OR_WEIGHTED = 4, OR_SEP5 = 5, OR_FD5 = 6,
+       OR_SOBEL5 = 7, OR_PREWITT5 = 8 };
 enum { OR_MEAN = 0, OR_MEDIAN = 1 };
 enum { OR_LITERAL = 0, OR_ALGEBRAIC = 1 };
 
@@ -85,20 +95,35 @@ static double read_sample(const void *in, int64_t pitch, int type, double disp_s
 
 static int is_valid(double s) { return isfinite(s) && s >= VALID_LO && s <= VALID_HI; }
 
-/* Row weights of the 3x3 gradient filters (reading R3); the horizontal filter
- * is weight[dv] * [-1 0 1][du] / norm, the vertical one its transpose. */
-static void filter_weights(int grad, const double *custom, double w[3], double *norm)
+/* Profiles of the gradient filters (readings R3, R15) on a 5x5 window: the
+ * horizontal filter's tap at offset (dv, du) is rho[dv+2] * sign(du) *
+ * delta[|du|] / norm, the vertical one its transpose.  The 3x3 filters use
+ * the inner window only (rho[0] = rho[4] = 0, delta[2] = 0). */
+static void filter_profile(int grad, const double *custom, double rho[5], double delta[3], double *norm)
 {
+    double w[3], d1 = 1, d2 = 0, s0, s1, s2;
+    delta[0] = 0;
     switch (grad) {
-    case OR_WEIGHTED:
-        w[0] = custom[0]; w[1] = custom[1]; w[2] = custom[2];
+    case OR_SEP5: d1 = custom[0]; d2 = custom[1]; s0 = custom[2]; s1 = custom[3]; s2 = custom[4]; break;
+    case OR_FD5: d1 = 8; d2 = -1; s0 = 1; s1 = 0; s2 = 0; break;
+    case OR_SOBEL5: d1 = 2; d2 = 1; s0 = 6; s1 = 4; s2 = 1; break;
+    case OR_PREWITT5: d1 = 1; d2 = 2; s0 = 1; s1 = 1; s2 = 1; break;
+    default:
+        switch (grad) {
+        case OR_WEIGHTED: w[0] = custom[0]; w[1] = custom[1]; w[2] = custom[2]; break;
+        case OR_FD: w[0] = 0; w[1] = 1; w[2] = 0; break;
+        case OR_SOBEL: w[0] = 1; w[1] = 2; w[2] = 1; break;
+        case OR_SCHARR: w[0] = 3; w[1] = 10; w[2] = 3; break;
+        default: w[0] = 1; w[1] = 1; w[2] = 1; break;
+        }
+        rho[0] = 0; rho[1] = w[0]; rho[2] = w[1]; rho[3] = w[2]; rho[4] = 0;
+        delta[1] = 1; delta[2] = 0;
         *norm = 2 * (fabs(w[0]) + fabs(w[1]) + fabs(w[2]));
-        break;
-    case OR_FD: w[0] = 0; w[1] = 1; w[2] = 0; *norm = 2; break;
-    case OR_SOBEL: w[0] = 1; w[1] = 2; w[2] = 1; *norm = 8; break;
-    case OR_SCHARR: w[0] = 3; w[1] = 10; w[2] = 3; *norm = 32; break;
-    default: w[0] = 1; w[1] = 1; w[2] = 1; *norm = 6; break;
+        return;
     }
+    rho[0] = s2; rho[1] = s1; rho[2] = s0; rho[3] = s1; rho[4] = s2;
+    delta[1] = d1; delta[2] = d2;
+    *norm = 2 * (d1 + 2 * d2) * (s0 + 2 * s1 + 2 * s2);
 }
 
 static int cmp_double(const void *a, const void *b)
@@ -112,7 +137,7 @@ typedef struct {
     int64_t pitch;
     int H, W, type, grad, phi, form;
     double disp_scale, fx, fy, u0, v0, tc;
-    double cw[3];          /* row weights of the weighted filter family (grad == OR_WEIGHTED) */
+    double cw[5];          /* weights of OR_WEIGHTED (w0 w1 w2) or OR_SEP5 (d1 d2 s0 s1 s2) */
     double *normals;       /* 3 planes of H*W doubles */
     uint8_t *mask;         /* H*W */
     double *cands;         /* optional: 8 planes of H*W candidates (NAN = excluded) */
@@ -124,16 +149,16 @@ static void pixel(const job_t *J, int u, int v)
 {
     const int64_t HW = (int64_t)J->H * J->W, idx = (int64_t)v * J->W + u;
     const int disparity = (J->type == OR_DISP_U16 || J->type == OR_DISP_F32);
-    double s[3][3]; /* samples, s[dv+1][du+1] */
-    int ok[3][3];
-    for (int dv = -1; dv <= 1; ++dv)
-        for (int du = -1; du <= 1; ++du) {
+    double s[5][5]; /* samples, s[dv+2][du+2] */
+    int ok[5][5];
+    for (int dv = -2; dv <= 2; ++dv)
+        for (int du = -2; du <= 2; ++du) {
             int x = u + du, y = v + dv;
             int inside = x >= 0 && x < J->W && y >= 0 && y < J->H;
             double val = inside ? read_sample(J->in, J->pitch, J->type, J->disp_scale, x, y) : 0.0;
-            s[dv + 1][du + 1] = val;
+            s[dv + 2][du + 2] = val;
             /* R1: fixed-point disparity is a hole only where the raw value is 0 */
-            ok[dv + 1][du + 1] = inside && (J->type == OR_DISP_U16 ? val > 0.0 : is_valid(val));
+            ok[dv + 2][du + 2] = inside && (J->type == OR_DISP_U16 ? val > 0.0 : is_valid(val));
         }
     double *n0 = J->normals, *n1 = J->normals + HW, *n2 = J->normals + 2 * HW;
     if (J->cands)
@@ -142,14 +167,15 @@ static void pixel(const job_t *J, int u, int v)
         for (int c = 0; c < 3; ++c) J->nprime[c * HW + idx] = 0.0;
 
     /* Reading R2: evaluable pixels. */
-    double wt[3], norm;
-    filter_weights(J->grad, J->cw, wt, &norm);
-    int evaluable = ok[1][1];
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-            int du = b - 1, dv = a - 1;
-            /* tap weight in the horizontal filter: wt[dv+1]*du; vertical: wt[du+1]*dv */
-            int used = (wt[a] != 0 && du != 0) || (wt[b] != 0 && dv != 0);
+    double rho[5], delta[3], norm;
+    filter_profile(J->grad, J->cw, rho, delta, &norm);
+    int evaluable = ok[2][2];
+    for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) {
+            int du = b - 2, dv = a - 2;
+            /* tap weight in the horizontal filter: rho[dv+2] sign(du) delta[|du|]; vertical: transposed */
+            int used = (rho[a] != 0 && du != 0 && delta[abs(du)] != 0) ||
+                       (rho[b] != 0 && dv != 0 && delta[abs(dv)] != 0);
             if (used && !ok[a][b]) evaluable = 0;
         }
     if (!evaluable) {
@@ -160,18 +186,25 @@ static void pixel(const job_t *J, int u, int v)
 
     /* Sec. III: the filters run on the inverse-depth image 1/Z (depth form) or
      * directly on the disparity image (disparity form, Eq. nx2_ny2_nz3). */
-    double img[3][3];
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
+    double img[5][5];
+    for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b)
             img[a][b] = ok[a][b] ? (disparity ? s[a][b] : 1.0 / s[a][b]) : 0.0;
-    /* Correlation with [-1 0 1]: per row (column) the difference of the two
-     * outer taps, weighted by the row (column) weight.  Equal taps give an
-     * exact zero, so the special case below is decided exactly. */
+    /* Correlation with the derivative profile: per row (column) the weighted
+     * differences of the taps at +-1 and +-2, then weighted by the row
+     * (column) weight.  Equal taps give an exact zero, so the special case
+     * below is decided exactly. */
     double gu = 0, gv = 0;
-    for (int k = 0; k < 3; ++k) {
-        if (wt[k] == 0) continue;
-        gu += wt[k] * (img[k][2] - img[k][0]);
-        gv += wt[k] * (img[2][k] - img[0][k]);
+    for (int k = 0; k < 5; ++k) {
+        if (rho[k] == 0) continue;
+        double hu = 0, hv = 0;
+        for (int b = 1; b <= 2; ++b) {
+            if (delta[b] == 0) continue;
+            hu += delta[b] * (img[k][2 + b] - img[k][2 - b]);
+            hv += delta[b] * (img[2 + b][k] - img[2 - b][k]);
+        }
+        gu += rho[k] * hu;
+        gv += rho[k] * hv;
     }
     gu /= norm;
     gv /= norm;
@@ -187,10 +220,10 @@ static void pixel(const job_t *J, int u, int v)
     else { nx = J->fx * gu; ny = J->fy * gv; }
 
     /* Depth of every neighbour: Z directly, or Z = f t_c / d (Eq. z_d). */
-    double Z[3][3];
+    double Z[3][3]; /* the 8-connected neighbourhood, Z[dv+1][du+1] */
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b)
-            Z[a][b] = ok[a][b] ? (disparity ? J->fx * J->tc / s[a][b] : s[a][b]) : 0.0;
+            Z[a][b] = ok[a + 1][b + 1] ? (disparity ? J->fx * J->tc / s[a + 1][b + 1] : s[a + 1][b + 1]) : 0.0;
 
     double c[8];
     int m = 0;
@@ -200,7 +233,7 @@ static void pixel(const job_t *J, int u, int v)
             int du = b - 1, dv = a - 1;
             if (du == 0 && dv == 0) continue;
             int slot = j++;
-            if (!ok[a][b]) continue;
+            if (!ok[a + 1][b + 1]) continue;
             double dz = Z[a][b] - Z[1][1];
             if (dz == 0.0) continue; /* reading R4 */
             double cand;
@@ -257,7 +290,7 @@ static int check_args(const void *in, int64_t pitch, int H, int W, int type, int
     if (type != OR_DEPTH_F32 && type != OR_DEPTH_F16 && type != OR_DISP_U16 && type != OR_DISP_F32 &&
         type != OR_DEPTH_F64)
         return OR_BAD_ARG;
-    if (grad < 0 || grad > 4 || phi < 0 || phi > 1 || form < 0 || form > 1) return OR_BAD_ARG;
+    if (grad < 0 || grad > OR_PREWITT5 || phi < 0 || phi > 1 || form < 0 || form > 1) return OR_BAD_ARG;
     if (!(fx > 0) || !(fy > 0)) return OR_BAD_ARG;
     int esz = type == OR_DEPTH_F64 ? 8 : (type == OR_DEPTH_F32 || type == OR_DISP_F32) ? 4 : 2;
     if (pitch < (int64_t)W * esz) return OR_BAD_ARG;
@@ -280,16 +313,19 @@ int tfn_oracle_normals_weighted(const void *in, int64_t pitch, int H, int W, int
 {
     int st = check_args(in, pitch, H, W, type, grad, phi, form, fx, fy, tc, disp_scale);
     if (st || !normals || !mask) return st ? st : OR_BAD_ARG;
-    if (grad == OR_WEIGHTED) {
+    const int nw = grad == OR_WEIGHTED ? 3 : grad == OR_SEP5 ? 5 : 0;
+    if (nw) {
         if (!weights) return OR_BAD_ARG;
-        for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < nw; ++k)
             if (!isfinite(weights[k])) return OR_BAD_ARG;
-        if (weights[0] == 0 && weights[1] == 0 && weights[2] == 0) return OR_BAD_ARG;
+        if (grad == OR_WEIGHTED && weights[0] == 0 && weights[1] == 0 && weights[2] == 0) return OR_BAD_ARG;
+        /* OR_SEP5: the profiles must measure a derivative (reading R15) */
+        if (grad == OR_SEP5 && (weights[0] + 2 * weights[1] == 0 || weights[2] + 2 * weights[3] + 2 * weights[4] == 0))
+            return OR_BAD_ARG;
     }
-    job_t J = {in, pitch, H, W, type, grad, phi, form, disp_scale, fx, fy, u0, v0, tc, {0, 0, 0},
+    job_t J = {in, pitch, H, W, type, grad, phi, form, disp_scale, fx, fy, u0, v0, tc, {0, 0, 0, 0, 0},
                normals, mask, cands, nprime};
-    if (grad == OR_WEIGHTED)
-        for (int k = 0; k < 3; ++k) J.cw[k] = weights[k];
+    for (int k = 0; k < nw; ++k) J.cw[k] = weights[k];
     run_rows(&J, 0, H);
     return OR_OK;
 }
@@ -298,7 +334,7 @@ int tfn_oracle_normals(const void *in, int64_t pitch, int H, int W, int type, do
                        double fx, double fy, double u0, double v0, double tc, int grad, int phi,
                        int form, double *normals, uint8_t *mask, double *cands, double *nprime)
 {
-    if (grad == OR_WEIGHTED) return OR_BAD_ARG; /* needs its weights: tfn_oracle_normals_weighted */
+    if (grad == OR_WEIGHTED || grad == OR_SEP5) return OR_BAD_ARG; /* need weights: tfn_oracle_normals_weighted */
     return tfn_oracle_normals_weighted(in, pitch, H, W, type, disp_scale, fx, fy, u0, v0, tc, grad, NULL, phi, form,
                                        normals, mask, cands, nprime);
 }
@@ -332,14 +368,14 @@ int tfn_oracle_normals_batch(const void *in, int64_t pitch, int n, int H, int W,
                              uint8_t *mask, int threads)
 {
     int st = check_args(in, pitch, H, W, type, grad, phi, form, fx, fy, tc, disp_scale);
-    if (st || !normals || !mask || n < 0 || grad == OR_WEIGHTED) return st ? st : OR_BAD_ARG;
+    if (st || !normals || !mask || n < 0 || grad == OR_WEIGHTED || grad == OR_SEP5) return st ? st : OR_BAD_ARG;
     if (threads < 1) threads = 1;
     job_t *jobs = (job_t *)calloc(n > 0 ? n : 1, sizeof(job_t));
     if (!jobs) return OR_BAD_ARG;
     const int64_t HW = (int64_t)H * W;
     for (int k = 0; k < n; ++k) {
         job_t J = {(const char *)in + (int64_t)k * H * pitch, pitch, H, W, type, grad, phi, form,
-                   disp_scale, fx, fy, u0, v0, tc, {0, 0, 0}, normals + 3 * HW * k, mask + HW * k, NULL, NULL};
+                   disp_scale, fx, fy, u0, v0, tc, {0, 0, 0, 0, 0}, normals + 3 * HW * k, mask + HW * k, NULL, NULL};
         jobs[k] = J;
     }
     pool_t P = {jobs, n, 0, PTHREAD_MUTEX_INITIALIZER};

@@ -13,6 +13,7 @@ import pytest
 import oracle
 from tests import test_oracle_pins as pins
 from tests import test_oracle_points as point_pins
+from tests import test_oracle_sep5 as sep5_pins
 from tests import test_oracle_weighted as weighted_pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "tfn_oracle.c")
@@ -26,10 +27,10 @@ MUTANTS = {
                                       "double px = Z[1][1] * (u - J->u0) / J->fx, py = Z[1][1] * (v - J->v0) / J->fx;"),
     "swapped_principal_point": ("double qx = Z[a][b] * (u + du - J->u0) / J->fx, qy = Z[a][b] * (v + dv - J->v0) / J->fy;",
                                 "double qx = Z[a][b] * (u + du - J->v0) / J->fx, qy = Z[a][b] * (v + dv - J->u0) / J->fy;"),
-    "convolution_not_correlation": ("gu += wt[k] * (img[k][2] - img[k][0]);",
-                                    "gu += wt[k] * (img[k][0] - img[k][2]);"),
-    "transposed_vertical_filter": ("gv += wt[k] * (img[2][k] - img[0][k]);",
-                                   "gv += wt[k] * (img[k][2] - img[k][0]);"),
+    "convolution_not_correlation": ("hu += delta[b] * (img[k][2 + b] - img[k][2 - b]);",
+                                    "hu += delta[b] * (img[k][2 - b] - img[k][2 + b]);"),
+    "transposed_vertical_filter": ("hv += delta[b] * (img[2 + b][k] - img[2 - b][k]);",
+                                   "hv += delta[b] * (img[k][2 + b] - img[k][2 - b]);"),
     "upper_median": ("phi = (m & 1) ? c[m / 2] : 0.5 * (c[m / 2 - 1] + c[m / 2]);",
                      "phi = c[m / 2];"),
     "mean_divides_by_eight": ("phi = acc / m;", "phi = acc / 8;"),
@@ -47,8 +48,8 @@ MUTANTS = {
                                       "(disparity ? 1.0 / s[a][b] : 1.0 / s[a][b])"),
     "depth_instead_of_inverse": ("img[a][b] = ok[a][b] ? (disparity ? s[a][b] : 1.0 / s[a][b]) : 0.0;",
                                  "img[a][b] = ok[a][b] ? s[a][b] : 0.0;"),
-    "prewitt_weights": ("default: w[0] = 1; w[1] = 1; w[2] = 1; *norm = 6;",
-                        "default: w[0] = 1; w[1] = 2; w[2] = 1; *norm = 6;"),
+    "prewitt_weights": ("default: w[0] = 1; w[1] = 1; w[2] = 1; break;",
+                        "default: w[0] = 1; w[1] = 2; w[2] = 1; break;"),
     "nx_without_focal": ("else { nx = J->fx * gu; ny = J->fy * gv; }", "else { nx = gu; ny = J->fy * gv; }"),
     # the back-projected point cloud
     "points_wrong_focal": ("Y = Z * (v - v0) / fy;", "Y = Z * (v - v0) / fx;"),
@@ -59,6 +60,17 @@ MUTANTS = {
                           "w[0] = custom[2]; w[1] = custom[1]; w[2] = custom[0];"),
     "weighted_ignores_weights": ("w[0] = custom[0]; w[1] = custom[1]; w[2] = custom[2];",
                                  "w[0] = 1; w[1] = 2; w[2] = 1;"),
+    # the 5x5 separable family
+    "fd5_profile_swapped": ("case OR_FD5: d1 = 8; d2 = -1;", "case OR_FD5: d1 = -1; d2 = 8;"),
+    "sobel5_smoothing_order": ("case OR_SOBEL5: d1 = 2; d2 = 1; s0 = 6; s1 = 4; s2 = 1;",
+                               "case OR_SOBEL5: d1 = 2; d2 = 1; s0 = 4; s1 = 6; s2 = 1;"),
+    "sep5_smoothing_reversed": ("rho[0] = s2; rho[1] = s1; rho[2] = s0; rho[3] = s1; rho[4] = s2;",
+                                "rho[0] = s0; rho[1] = s1; rho[2] = s2; rho[3] = s1; rho[4] = s0;"),
+    "sep5_outer_taps_at_offset_one": ("hu += delta[b] * (img[k][2 + b] - img[k][2 - b]);",
+                                      "hu += delta[b] * (img[k][3] - img[k][1]);"),
+    "sep5_norm_drops_d2": ("*norm = 2 * (d1 + 2 * d2) *", "*norm = 2 * (d1 + d2) *"),
+    "sep5_outer_taps_not_required": ("(rho[a] != 0 && du != 0 && delta[abs(du)] != 0)",
+                                     "(rho[a] != 0 && abs(du) == 1 && delta[abs(du)] != 0)"),
     "points_keep_holes": ("double X = 0, Y = 0, Z = 0;\n            if (ok) {", "double X = 0, Y = 0, Z = 0;\n            if (1) {"),
 }
 
@@ -69,6 +81,8 @@ def _pins_fail(lib):
     if point_pins.check_points(lib):
         return True
     if weighted_pins.check_weighted(lib):
+        return True
+    if sep5_pins.check_sep5(lib):
         return True
     for grad in pins.GRADS:
         for phi in pins.PHIS:

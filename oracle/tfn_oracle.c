@@ -37,8 +37,11 @@
  *      The candidates and Phi keep the 8-connected neighbourhood (Sec. V-A).
  *   R4 candidates come from valid neighbours with dz != 0 only.
  *   R5 Phi = median of an even count is the mean of the two middle values.
- *   R6 if both gradients are exactly zero the normal is [0, 0, -1] (this holds
- *      in particular when all neighbours share the centre depth).
+ *   R6 the normal is [0, 0, -1] if both gradients are exactly zero, or if no
+ *      neighbour gives a candidate, i.e. every valid neighbour shares the
+ *      centre's depth (Sec. III special case).  With 3x3 filters the second
+ *      implies the first (the taps are among the neighbours); a 5x5 filter can
+ *      see a depth change in its outer taps only.
  *   R7 the output is n = -n'/|n'| with n' = (nx, ny, n_z): it faces the camera.
  *   R8 invalid pixels get normal (0, 0, 0) and mask 0; evaluable ones mask 1.
  */
@@ -254,12 +257,13 @@ static void pixel(const job_t *J, int u, int v)
             if (J->cands) J->cands[slot * HW + idx] = cand;
         }
 
-    /* Phi: mean or median (reading R5).  m >= 1 here: a non-zero gradient
-     * needs two taps of different depth, and one of them differs from Z_i. */
+    if (m == 0) { /* reading R6: every valid neighbour at the centre's depth */
+        n0[idx] = 0.0; n1[idx] = 0.0; n2[idx] = -1.0;
+        return;
+    }
+    /* Phi: mean or median (reading R5). */
     double phi;
-    if (m == 0) {
-        phi = 0.0;
-    } else if (J->phi == OR_MEAN) {
+    if (J->phi == OR_MEAN) {
         double acc = 0;
         for (int k = 0; k < m; ++k) acc += c[k];
         phi = acc / m;

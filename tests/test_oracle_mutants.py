@@ -71,6 +71,8 @@ MUTANTS = {
     "sep5_norm_drops_d2": ("*norm = 2 * (d1 + 2 * d2) *", "*norm = 2 * (d1 + d2) *"),
     "sep5_outer_taps_not_required": ("(rho[a] != 0 && du != 0 && delta[abs(du)] != 0)",
                                      "(rho[a] != 0 && abs(du) == 1 && delta[abs(du)] != 0)"),
+    "no_candidate_not_special": ("    if (m == 0) { /* reading R6: every valid neighbour at the centre's depth */\n        n0[idx] = 0.0; n1[idx] = 0.0; n2[idx] = -1.0;\n        return;\n    }",
+                                 "    if (m == 0) { c[m++] = 0.0; }"),
     "points_keep_holes": ("double X = 0, Y = 0, Z = 0;\n            if (ok) {", "double X = 0, Y = 0, Z = 0;\n            if (1) {"),
 }
 

@@ -117,6 +117,21 @@ def check_sep5(lib=None):
             want[2 + b, 2 + a] = 0
     if not np.array_equal(_mask_pattern5("sep5", (1.0, 0.0, 1.0, 0.0, 1.0), lib), want):
         fails.append("taps (1 0 | 1 0 1)")
+    # Sec. III special case (reading R6): every neighbour at the centre's depth gives [0, 0, -1] even
+    # though a 5x5 filter sees the depth change in its outer taps
+    img = np.full((9, 9), 2.0)
+    img[:, 6:] = 2.5
+    img[6:, :] = 2.25
+    for grad in ("fd5", "sobel5"):
+        for phi in ("mean", "median"):
+            n, m = oracle.normals(img, 3.0, 3.0, 4.0, 4.0, grad=grad, phi=phi, lib=lib)
+            if not (m[4, 4] == 1 and np.array_equal(n[:, 4, 4], [0.0, 0.0, -1.0])):
+                fails.append(f"no-candidate special case {grad} {phi}")
+    # (the window is what it claims: no neighbour of the centre gives a candidate, while FD5's outer
+    # taps (4, 2) and (4, 6) differ)
+    _, _, c1, npr = oracle.normals(img, 1.0, 1.0, 4.0, 4.0, grad="fd", diagnostics=True, lib=lib)
+    if np.isfinite(c1[:, 4, 4]).any() or npr[:, 4, 4].any() or img[4, 2] == img[4, 6]:
+        fails.append("no-candidate window")
     # transpose: x and y of the normal swap
     w = (1.0, 0.4, 3.0, 1.0, 0.2)
     a, ma = oracle.normals(d, **CAM, grad="sep5", weights=w, lib=lib)

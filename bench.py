@@ -360,6 +360,14 @@ def run_ours(args):
             lm = statistics.mean(pv)
             variants["weighted_131_mean_f32"] = {"frames_per_s": round(nf / (lm * 1e-3), 1),
                                                  "hbm_gbs": round(BYTES_PER_PX["f32_in_f32_out"] * px / (lm * 1e-3) / 1e9, 1)}
+            # the 5x5 gradient filters (filter sizes)
+            for grad, phi in (("fd5", "mean"), ("sobel5", "mean"), ("sobel5", "median")):
+                splan = ctx.plan(ins, cam, grad=grad, phi=phi, normals=outs, masks=mks)
+                tot, pv = time_launches(torch, lambda: splan.launch(stream), max(5, args.steps // 2), 3, stream)
+                splan.close()
+                lm = statistics.mean(pv)
+                variants[f"{grad}_{phi}_f32"] = {"frames_per_s": round(nf / (lm * 1e-3), 1),
+                                                 "hbm_gbs": round(BYTES_PER_PX["f32_in_f32_out"] * px / (lm * 1e-3) / 1e9, 1)}
         serving = None
         if not args.no_serving:
             serving = run_serving(torch, tfn, ctx, dev, d, args.serve_requests)

@@ -80,15 +80,30 @@ typedef enum tfn_input {
  * [-1 0 1] horizontally (its transpose vertically), row weights
  * FD (0 1 0), Sobel (1 2 1), Scharr (3 10 3), Prewitt (1 1 1), or any row
  * weights (w0 w1 w2) given in tfn_method.weights (TFN_GRAD_WEIGHTED: the 3x3
- * kernels of the paper's brute-force kernel search, Sec. IV-B).  A pixel is
- * evaluable when it and every tap with a non-zero weight in either filter are
- * valid. */
+ * kernels of the paper's brute-force kernel search, Sec. IV-B).
+ *
+ * 5x5 filters (Fig. 2 compares filter types and sizes): separable, an
+ * antisymmetric derivative profile (d1 at offsets +-1, d2 at +-2) along the
+ * filter's axis times a symmetric smoothing profile (s0 at 0, s1 at +-1, s2 at
+ * +-2) across it; TFN_GRAD_SEP5 takes (d1 d2 s0 s1 s2) in tfn_method.weights
+ * (d1 + 2 d2 and s0 + 2 s1 + 2 s2 must be non-zero), and the named members
+ * fix them: FD5 (8 -1 | 1 0 0), the fourth-order central difference, Sobel5
+ * (2 1 | 6 4 1) and Prewitt5 (1 2 | 1 1 1).  The candidates and Phi keep the
+ * 8-connected neighbourhood.
+ *
+ * A pixel is evaluable when it and every tap with a non-zero weight in either
+ * filter are valid (a 5x5 filter with d2 or s2 non-zero leaves a 2-pixel
+ * border). */
 typedef enum tfn_grad {
     TFN_GRAD_FD = 0,
     TFN_GRAD_SOBEL = 1,
     TFN_GRAD_SCHARR = 2,
     TFN_GRAD_PREWITT = 3,
-    TFN_GRAD_WEIGHTED = 4
+    TFN_GRAD_WEIGHTED = 4,
+    TFN_GRAD_SEP5 = 5,
+    TFN_GRAD_FD5 = 6,
+    TFN_GRAD_SOBEL5 = 7,
+    TFN_GRAD_PREWITT5 = 8
 } tfn_grad;
 
 /* Phi of Eq. (nx2_ny2_nz2). */
@@ -153,7 +168,8 @@ typedef struct tfn_method {
     int32_t phi;      /* tfn_phi */
     int32_t output;   /* tfn_output */
     int32_t flags;    /* TFN_FLAG_* */
-    float weights[3]; /* TFN_GRAD_WEIGHTED: row weights (w0 w1 w2), finite, not all 0; else ignored */
+    float weights[5]; /* TFN_GRAD_WEIGHTED: row weights (w0 w1 w2), finite, not all 0;
+                         TFN_GRAD_SEP5: (d1 d2 s0 s1 s2), finite; else ignored */
     int32_t reserved; /* 0 */
 } tfn_method;
 

@@ -26,14 +26,16 @@ _lib = ctypes.CDLL(LIB_PATH)
 TFN_OK, TFN_ERR_INVALID_ARG, TFN_ERR_UNSUPPORTED, TFN_ERR_MISALIGNED, TFN_ERR_OUT_OF_MEMORY, TFN_ERR_CUDA, \
     TFN_ERR_TIMEOUT, TFN_ERR_CANCELLED, TFN_ERR_BUSY, TFN_ERR_DEVICE, TFN_ERR_IO = range(11)
 TFN_DEPTH_F32, TFN_DEPTH_F16, TFN_DISP_U16, TFN_DISP_F32 = range(4)
-TFN_GRAD_FD, TFN_GRAD_SOBEL, TFN_GRAD_SCHARR, TFN_GRAD_PREWITT, TFN_GRAD_WEIGHTED = range(5)
+TFN_GRAD_FD, TFN_GRAD_SOBEL, TFN_GRAD_SCHARR, TFN_GRAD_PREWITT, TFN_GRAD_WEIGHTED, TFN_GRAD_SEP5, TFN_GRAD_FD5, \
+    TFN_GRAD_SOBEL5, TFN_GRAD_PREWITT5 = range(9)
 TFN_PHI_MEAN, TFN_PHI_MEDIAN = range(2)
 TFN_OUT_F32, TFN_OUT_F16, TFN_OUT_BF16, TFN_OUT_F16X4, TFN_OUT_BF16X4, TFN_OUT_OCT16 = range(6)
 TFN_FLAG_REFINE_ALL = 1
 TFN_REQ_HOST = 1
 
 GRADS = {"fd": TFN_GRAD_FD, "sobel": TFN_GRAD_SOBEL, "scharr": TFN_GRAD_SCHARR, "prewitt": TFN_GRAD_PREWITT,
-         "weighted": TFN_GRAD_WEIGHTED}
+         "weighted": TFN_GRAD_WEIGHTED, "sep5": TFN_GRAD_SEP5, "fd5": TFN_GRAD_FD5, "sobel5": TFN_GRAD_SOBEL5,
+         "prewitt5": TFN_GRAD_PREWITT5}
 PHIS = {"mean": TFN_PHI_MEAN, "median": TFN_PHI_MEDIAN}
 OUTPUTS = {"f32": TFN_OUT_F32, "f16": TFN_OUT_F16, "bf16": TFN_OUT_BF16, "f16x4": TFN_OUT_F16X4,
            "bf16x4": TFN_OUT_BF16X4, "oct16": TFN_OUT_OCT16}
@@ -58,7 +60,7 @@ class tfn_frame(ctypes.Structure):
 
 class tfn_method(ctypes.Structure):
     _fields_ = [("grad", ctypes.c_int32), ("phi", ctypes.c_int32), ("output", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("weights", ctypes.c_float * 3), ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("weights", ctypes.c_float * 5), ("reserved", ctypes.c_int32)]
 
 
 class tfn_server_opts(ctypes.Structure):
@@ -272,14 +274,17 @@ def make_frame(inp, normals, mask, cam, disparity=False, disp_scale=1.0 / 16, ou
 
 
 def make_method(grad="fd", phi="mean", output="f32", flags=0, weights=None) -> tfn_method:
-    """grad="weighted" takes the row weights (w0, w1, w2) of the gradient filter in `weights`."""
+    """grad="weighted" takes the row weights (w0, w1, w2) of the gradient filter in `weights`; grad="sep5" takes
+    the 5x5 profiles (d1, d2, s0, s1, s2)."""
     m = tfn_method()
     m.grad = GRADS[grad] if isinstance(grad, str) else grad
     m.phi = PHIS[phi] if isinstance(phi, str) else phi
     m.output = OUTPUTS[output] if isinstance(output, str) else output
     m.flags = flags
     if weights is not None:
-        m.weights = (ctypes.c_float * 3)(*weights)
+        if len(weights) > 5:
+            raise ValueError("at most 5 weights")
+        m.weights = (ctypes.c_float * 5)(*weights)
     return m
 
 

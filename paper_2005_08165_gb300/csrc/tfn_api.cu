@@ -25,6 +25,7 @@ KernelFn kernels_disp_f32(int grad, int phi, int cfg);
 
 KernelFn kernel_for(int kind, int grad, int phi, int cfg)
 {
+    if (grad_is_sep5(grad)) grad = GRAD_SEP5;  // the named 5x5 filters are weight presets
     switch (kind) {
     case KIND_DEPTH_F32: return kernels_depth_f32(grad, phi, cfg);
     case KIND_DEPTH_F16: return kernels_depth_f16(grad, phi, cfg);
@@ -119,6 +120,15 @@ tfn_status validate_method(const tfn_method *m)
         for (int k = 0; k < 3; ++k)
             if (!std::isfinite(m->weights[k])) return TFN_ERR_INVALID_ARG;
         if (m->weights[0] == 0.f && m->weights[1] == 0.f && m->weights[2] == 0.f) return TFN_ERR_INVALID_ARG;
+    }
+    if (m->grad == GRAD_SEP5) {
+        // (d1 d2 s0 s1 s2): the profiles must measure a derivative, so neither
+        // d1 + 2 d2 nor s0 + 2 s1 + 2 s2 may vanish (computed in double: exact)
+        const float *w = m->weights;
+        for (int k = 0; k < 5; ++k)
+            if (!std::isfinite(w[k])) return TFN_ERR_INVALID_ARG;
+        if ((double)w[0] + 2.0 * w[1] == 0.0 || (double)w[2] + 2.0 * w[3] + 2.0 * w[4] == 0.0)
+            return TFN_ERR_INVALID_ARG;
     }
     return TFN_OK;
 }
@@ -256,7 +266,7 @@ tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDes
     KernelFn fn = kernel_for(kind, m.grad, m.phi, cfg);
     if (!fn) return TFN_ERR_UNSUPPORTED;
     const int threads = cfg_threads(cfg);
-    const size_t smem = smem_bytes(kind, cfg);
+    const size_t smem = smem_bytes(kind, cfg, m.grad);
     if (!cuda_ok(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                  "cudaFuncSetAttribute"))
         return TFN_ERR_CUDA;
@@ -277,8 +287,9 @@ tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDes
     a.total_tiles = total_tiles;
     a.out_fmt = m.output;
     a.flags = m.flags;
-    for (int k = 0; k < 3; ++k) a.w[k] = m.grad == GRAD_WEIGHTED ? m.weights[k] : 0.f;
-    a.pad = 0;
+    for (int k = 0; k < 5; ++k) a.w[k] = m.grad == GRAD_WEIGHTED && k < 3 ? m.weights[k] : 0.f;
+    if (grad_is_sep5(m.grad)) sep5_weights(m.grad, m.weights, a.w);
+    a.pad[0] = a.pad[1] = a.pad[2] = 0;
     void *params[] = {&a};
     if (!cuda_ok(cudaLaunchKernel((const void *)fn, dim3(grid), dim3(threads), params, smem, stream),
                  "cudaLaunchKernel"))

@@ -8,7 +8,20 @@
 namespace tfn {
 
 enum Kind { KIND_DEPTH_F32 = 0, KIND_DEPTH_F16 = 1, KIND_DISP_U16 = 2, KIND_DISP_F32 = 3, KIND_COUNT = 4 };
-enum Grad { GRAD_FD = 0, GRAD_SOBEL = 1, GRAD_SCHARR = 2, GRAD_PREWITT = 3, GRAD_WEIGHTED = 4, GRAD_COUNT = 5 };
+// GRAD_FD5 .. GRAD_PREWITT5 are GRAD_SEP5 with fixed weights (sep5_weights);
+// the kernels are compiled for GRAD_FD .. GRAD_SEP5.
+enum Grad {
+    GRAD_FD = 0,
+    GRAD_SOBEL = 1,
+    GRAD_SCHARR = 2,
+    GRAD_PREWITT = 3,
+    GRAD_WEIGHTED = 4,
+    GRAD_SEP5 = 5,
+    GRAD_FD5 = 6,
+    GRAD_SOBEL5 = 7,
+    GRAD_PREWITT5 = 8,
+    GRAD_COUNT = 9
+};
 enum Phi { PHI_MEAN = 0, PHI_MEDIAN = 1, PHI_COUNT = 2 };
 enum OutFmt { OUT_F32 = 0, OUT_F16 = 1, OUT_BF16 = 2, OUT_F16X4 = 3, OUT_BF16X4 = 4, OUT_OCT16 = 5 };
 
@@ -47,15 +60,16 @@ struct LaunchArgs {
     int32_t total_tiles;
     int32_t out_fmt;
     int32_t flags;
-    float w[3];               // GRAD_WEIGHTED: row weights (w0 w1 w2)
-    int32_t pad;
+    float w[5];               // GRAD_WEIGHTED: row weights (w0 w1 w2); GRAD_SEP5: (d1 d2 s0 s1 s2)
+    int32_t pad[3];
 };
 
 // Work-item shapes the kernels are compiled for.  An item is a band of tw =
 // 128 pixel columns (32 lanes x 4) by th rows of one frame, computed by one
 // warp that rolls down its rows (pr = th rows per lane); the rows stream
 // through a ring of nst shared-memory stages of cr rows each (th + 2 rows per
-// item: one above, one below), per warp; a CTA has `warps` warps.
+// item: one above, one below; th + 4 for the 5x5 filters, the last chunk of
+// an item then partly unused), per warp; a CTA has `warps` warps.
 struct TileCfg {
     int tw, th, pr, cr, nst, warps;
 };
@@ -73,9 +87,23 @@ inline int box_w(int kind, int c) { return kCfgs[c].tw + 2 * kind_padx(kind); }
 inline int box_h(int c) { return kCfgs[c].cr; }
 inline size_t stage_bytes(int kind, int c) { return (size_t)box_w(kind, c) * box_h(c) * kind_elem_size(kind); }
 inline size_t stage_stride(int kind, int c) { return (stage_bytes(kind, c) + 127) & ~(size_t)127; }
-inline size_t smem_bytes(int kind, int c)
+// GRAD_SEP5 keeps each lane's row derivatives and smoothings of the last 5
+// sample rows in shared memory: 5 rows x 4 float4 per lane.
+constexpr size_t kSep5RingBytes = 5 * 4 * 32 * 16;
+inline bool grad_is_sep5(int grad) { return grad >= GRAD_SEP5; }
+inline size_t smem_bytes(int kind, int c, int grad)
 {
-    return (size_t)kCfgs[c].warps * kCfgs[c].nst * stage_stride(kind, c) + 128;
+    return (size_t)kCfgs[c].warps * (kCfgs[c].nst * stage_stride(kind, c) + (grad_is_sep5(grad) ? kSep5RingBytes : 0)) +
+           128;
+}
+// The profiles (d1 d2 s0 s1 s2) of a 5x5 filter: the named members' fixed
+// ones, else the caller's.
+inline void sep5_weights(int grad, const float *given, float w[5])
+{
+    static const float fd5[5] = {8.f, -1.f, 1.f, 0.f, 0.f}, sobel5[5] = {2.f, 1.f, 6.f, 4.f, 1.f},
+                       prewitt5[5] = {1.f, 2.f, 1.f, 1.f, 1.f};
+    const float *src = grad == GRAD_FD5 ? fd5 : grad == GRAD_SOBEL5 ? sobel5 : grad == GRAD_PREWITT5 ? prewitt5 : given;
+    for (int k = 0; k < 5; ++k) w[k] = src[k];
 }
 
 // Kernel entry points, one per (kind, grad, phi, cfg); defined in tfn_k_*.cu.

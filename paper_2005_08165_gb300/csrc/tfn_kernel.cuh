@@ -262,17 +262,11 @@ struct Vec3 {
 
 // The window travels by value (9 samples + 9 validity bits) so that the
 // caller keeps it in registers; a reference would force it to local memory.
-template <int KIND, int GRAD, int PHI>
-__device__ __noinline__ Vec3 refine_pixel(float z00, float z01, float z02, float z10, float z11, float z12, float z20,
-                                          float z21, float z22, unsigned okbits, int u, int v, float fx, float fy,
-                                          float u0, float v0, float w0, float w1, float w2)
+// The candidates, Phi and the normal in double-float, given the gradients.
+template <int KIND, int PHI>
+__device__ __forceinline__ Vec3 refine_candidates(const float (&z)[3][3], const bool (&ok)[3][3], df Gu, df Gv, int u,
+                                                  int v, float fx, float fy, float u0, float v0)
 {
-    const float z[3][3] = {{z00, z01, z02}, {z10, z11, z12}, {z20, z21, z22}};
-    bool ok[3][3];
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) ok[a][b] = (okbits >> (3 * a + b)) & 1u;
-    df Gu, Gv;
-    gradients<KIND, GRAD>(z, Gu, Gv, w0, w1, w2);
     const float zi = z[1][1];
     df R[8];
     int m = 0;
@@ -329,6 +323,20 @@ __device__ __noinline__ Vec3 refine_pixel(float z00, float z01, float z02, float
     const float x = ldexpf(nxp, -ex), y = ldexpf(nyp, -ex), w = ldexpf(nzp, -ex);
     const float rs = rsqrt_approx(x * x + y * y + w * w);
     return {-x * rs, -y * rs, -w * rs};
+}
+
+template <int KIND, int GRAD, int PHI>
+__device__ __noinline__ Vec3 refine_pixel(float z00, float z01, float z02, float z10, float z11, float z12, float z20,
+                                          float z21, float z22, unsigned okbits, int u, int v, float fx, float fy,
+                                          float u0, float v0, float w0, float w1, float w2)
+{
+    const float z[3][3] = {{z00, z01, z02}, {z10, z11, z12}, {z20, z21, z22}};
+    bool ok[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) ok[a][b] = (okbits >> (3 * a + b)) & 1u;
+    df Gu, Gv;
+    gradients<KIND, GRAD>(z, Gu, Gv, w0, w1, w2);
+    return refine_candidates<KIND, PHI>(z, ok, Gu, Gv, u, v, fx, fy, u0, v0);
 }
 
 // ------------------------------------------------------------ main path
@@ -532,8 +540,9 @@ __device__ __forceinline__ void carry_down(const Row<KIND, GRAD> &C, const Row<K
 template <int KIND, int GRAD, int PHI>
 __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIND, GRAD> &C, const Row<KIND, GRAD> &N,
                                          UpCarry &cy, const float (&uc)[4], float vc, float fx, float fy, float thr,
-                                         const float (&wts)[3], float (&ox)[4], float (&oy)[4], float (&oz)[4],
-                                         uint32_t &mword, unsigned &rbits)
+                                         const float (&wts)[3], const df (&gin_u)[4], const df (&gin_v)[4],
+                                         float (&ox)[4], float (&oy)[4], float (&oz)[4], uint32_t &mword,
+                                         unsigned &rbits)
 {
     // edges of this row (c -> c+1) and to the row below, computed pixel by
     // pixel: pixel c needs those of columns c-1 and c only
@@ -583,6 +592,11 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
             mx = fmaxf(mx, n2 ? N.z[c + 1] : 0.f);
             mx = fmaxf(mx, n1 ? fmaxf(fmaxf(P.z[c], N.z[c]), fmaxf(C.z[c - 1], C.z[c + 1])) : 0.f);
             ev_ok = mx <= kValidHi;
+        } else if constexpr (GRAD == GRAD_SEP5) {
+            // the 5x5 gradients come from the caller, NaN where a needed tap is a hole
+            Gu = gin_u[k];
+            Gv = gin_v[k];
+            ev_ok = zi <= kValidHi && Gu.h == Gu.h && Gv.h == Gv.h;
         } else {
             Gu = filter_sum<GRAD>(tap_diff(P, c - 1, P, c + 1), tap_diff(C, c - 1, C, c + 1),
                                   tap_diff(N, c - 1, N, c + 1));
@@ -606,6 +620,7 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
         const float n3 = __fadd_rn(__fsub_rn(Gu.h, Gv.h), __fsub_rn(Gu.l, Gv.l));
 
         float mF, mbound, scale;
+        bool none;  // no neighbour gives a candidate
         if constexpr (PHI == PHI_MEAN) {
             // sum over the pairs (j, -j) of num_p (rho_j - rho_-j), carried
             // unnormalised: n' scaled by m > 0 keeps its direction
@@ -619,6 +634,7 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
                                                    __fmul_rn(fabsf(n3), __fadd_rn(fabsf(rur), fabsf(rdl))))));
             mF = S;
             scale = m;
+            none = m == 0.f;
         } else {
             const float rho8[8] = {rr, rl, rd, ru, rdr, rul, rur, rdl};
             const float num8[8] = {gu, -gu, gv, -gv, n2, -n2, n3, -n3};
@@ -646,12 +662,18 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
             TFN_CE(1, 2) TFN_CE(3, 4) TFN_CE(5, 6)
 #undef TFN_CE
             const bool odd = cnt & 1;
+            none = cnt == 0;
             mF = odd ? s[3] : __fmul_rn(0.5f, __fadd_rn(s[3], s[4]));
             mbound = odd ? fabsf(s[3]) : fmaxf(fabsf(s[3]), fabsf(s[4]));
             scale = 1.f;
         }
+        // Sec. III special case when every valid neighbour shares the centre's
+        // depth: with 3x3 filters the gradients are then zero (flat already);
+        // a 5x5 filter can still see a depth change in its outer taps
+        if constexpr (GRAD == GRAD_SEP5) flat = flat || none;
+        const float gxo = GRAD == GRAD_SEP5 && flat ? 0.f : gu, gyo = GRAD == GRAD_SEP5 && flat ? 0.f : gv;
         const float A = __fmaf_rn(uc[k], gu, __fmul_rn(vc, gv));
-        const float nxp = __fmul_rn(__fmul_rn(scale, fx), gu), nyp = __fmul_rn(__fmul_rn(scale, fy), gv);
+        const float nxp = __fmul_rn(__fmul_rn(scale, fx), gxo), nyp = __fmul_rn(__fmul_rn(scale, fy), gyo);
         // (a non-evaluable pixel's median may be a +-inf sentinel: keep n' finite so that rs = 0 zeroes it)
         const float nzp = (flat || !ev_ok) ? 1.f : -__fmaf_rn(scale, A, mF);
         const float nn = __fmaf_rn(nxp, nxp, __fmaf_rn(nyp, nyp, __fmul_rn(nzp, nzp)));
@@ -672,6 +694,121 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
         cy.rur[k] = rho_bwd<KIND>(C.z[c + 1], N.z[c], ea[c].r);
         cy.ku[k] = __fadd_rn(__fadd_rn(ev.k, ed[c - 1].k), ea[c].k);
     }
+}
+
+// ------------------------------------------------------------ 5x5 filters
+//
+// The separable 5x5 gradient filters: an antisymmetric derivative profile
+// (d1 at offsets +-1, d2 at +-2) along the filter's axis times a symmetric
+// smoothing profile (s0, s1, s2) across it.  As each sample row arrives, a
+// lane computes at its 4 columns the row's derivative Dh = d1 (w_{+1} -
+// w_{-1}) + d2 (w_{+2} - w_{-2}) and smoothing Sh = s0 w_0 + s1 (w_{-1} +
+// w_{+1}) + s2 (w_{-2} + w_{+2}) (w = 1/Z or the disparity), both
+// compensated, and keeps them for 5 rows; then G_u = sum_a s_|a| Dh(y + a)
+// and G_v = d1 (Sh(y+1) - Sh(y-1)) + d2 (Sh(y+2) - Sh(y-2)).  The common
+// normalisation is dropped (it cancels from the direction).  A value whose
+// needed taps include a hole is NaN, which marks the pixels that use it as
+// not evaluable; zero-weight terms are never read.
+
+struct Sep5W {
+    float d1, d2, s0, s1, s2;
+};
+
+__device__ __forceinline__ float f4_at(const float4 &v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+
+__device__ __forceinline__ df df_nan() { return {__int_as_float(0x7fc00000), __int_as_float(0x7fc00000)}; }
+
+// One sample row of a lane's 5x5 window: image columns x0-2 .. x0+5.
+template <int KIND, int BOXW, int PADX>
+__device__ __forceinline__ void load_row8(const unsigned char *stage, int jr, int lane, float (&z)[8])
+{
+    typedef typename KindTraits<KIND>::T T;
+    static_assert(PADX >= 2, "the box halo must hold 2 columns");
+    const T *p = reinterpret_cast<const T *>(stage) + jr * BOXW + PADX + 4 * lane;
+    T raw[8];
+    raw[0] = p[-2];
+    raw[1] = p[-1];
+    if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        raw[2] = q.x;
+        raw[3] = q.y;
+        raw[4] = q.z;
+        raw[5] = q.w;
+    } else {
+        const uint2 q = *reinterpret_cast<const uint2 *>(p);
+        raw[2] = from_bits16<T>(q.x & 0xffffu);
+        raw[3] = from_bits16<T>(q.x >> 16);
+        raw[4] = from_bits16<T>(q.y & 0xffffu);
+        raw[5] = from_bits16<T>(q.y >> 16);
+    }
+    raw[6] = p[4];
+    raw[7] = p[5];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) z[c] = decode<KIND>(raw[c]);
+}
+
+// Dh and Sh of one sample row at the lane's 4 columns (sample c + 2 of z is
+// column x0 + c).
+template <int KIND>
+__device__ __forceinline__ void sep5_row(const float (&z)[8], const Sep5W &w, df (&Dh)[4], df (&Sh)[4])
+{
+    float wh[8], wl[8];
+    bool ok[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        ok[i] = z[i] <= kValidHi;
+        if constexpr (KindTraits<KIND>::disparity) {
+            wh[i] = z[i];
+            wl[i] = 0.f;
+        } else {  // 1/Z as wh + wl: hardware reciprocal plus its FMA residual
+            wh[i] = rcp_approx(z[i]);
+            wl[i] = __fmul_rn(__fmaf_rn(-wh[i], z[i], 1.f), wh[i]);
+        }
+    }
+    // w_b - w_a, exact up to the low parts' rounding
+    auto diff = [&](int a, int b) -> df {
+        if constexpr (KindTraits<KIND>::exact_diff) {
+            return {__fsub_rn(wh[b], wh[a]), 0.f};
+        } else {
+            const df h = two_sum(wh[b], -wh[a]);
+            return {h.h, __fadd_rn(h.l, __fsub_rn(wl[b], wl[a]))};
+        }
+    };
+    auto val = [&](int a) -> df { return {wh[a], wl[a]}; };
+    const df zero = {0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int c = k + 2;
+        const bool ok1 = ok[c - 1] && ok[c + 1], ok2 = ok[c - 2] && ok[c + 2];
+        const df t1 = w.d1 != 0.f ? df_mul_f(diff(c - 1, c + 1), w.d1) : zero;
+        const df t2 = w.d2 != 0.f ? df_mul_f(diff(c - 2, c + 2), w.d2) : zero;
+        const bool dok = (w.d1 == 0.f || ok1) && (w.d2 == 0.f || ok2);
+        Dh[k] = dok ? df_add(t1, t2) : df_nan();
+        const df a0 = w.s0 != 0.f ? df_mul_f(val(c), w.s0) : zero;
+        const df a1 = w.s1 != 0.f ? df_mul_f(df_add(val(c - 1), val(c + 1)), w.s1) : zero;
+        const df a2 = w.s2 != 0.f ? df_mul_f(df_add(val(c - 2), val(c + 2)), w.s2) : zero;
+        const bool sok = (w.s0 == 0.f || ok[c]) && (w.s1 == 0.f || ok1) && (w.s2 == 0.f || ok2);
+        Sh[k] = sok ? df_add(a0, df_add(a1, a2)) : df_nan();
+    }
+}
+
+// G = c0 a2 + c1 (a1 + a3) + c2 (a0 + a4) with zero-weight terms dropped.
+__device__ __forceinline__ df sep5_sym(df a0, df a1, df a2, df a3, df a4, float c0, float c1, float c2)
+{
+    const df zero = {0.f, 0.f};
+    const df t0 = c0 != 0.f ? df_mul_f(a2, c0) : zero;
+    const df t1 = c1 != 0.f ? df_mul_f(df_add(a1, a3), c1) : zero;
+    const df t2 = c2 != 0.f ? df_mul_f(df_add(a0, a4), c2) : zero;
+    return df_add(t0, df_add(t1, t2));
+}
+
+// G = c1 (a3 - a1) + c2 (a4 - a0) with zero-weight terms dropped.
+__device__ __forceinline__ df sep5_anti(df a0, df a1, df a3, df a4, float c1, float c2)
+{
+    const df zero = {0.f, 0.f};
+    const df t1 = c1 != 0.f ? df_mul_f(df_add(a3, df_neg(a1)), c1) : zero;
+    const df t2 = c2 != 0.f ? df_mul_f(df_add(a4, df_neg(a0)), c2) : zero;
+    return df_add(t1, t2);
 }
 
 // ------------------------------------------------------------ TMA / mbarrier
@@ -915,6 +1052,51 @@ __device__ __noinline__ Vec3 refine_from_input(const void *in, int64_t pitch, in
                                          v0, w0, w1, w2);
 }
 
+// The same for a 5x5 filter: the gradients from the 5x5 window in
+// double-float (per row or column the weighted differences of the taps at
+// +-1 and +-2, then the smoothing profile across), then the candidates of
+// the 3x3 window.  Zero-weight taps are never read.
+template <int KIND, int PHI>
+__device__ __noinline__ Vec3 refine_from_input_sep5(const void *in, int64_t pitch, int H, int W, int x, int y, float fx,
+                                                    float fy, float u0, float v0, float d1, float d2, float s0,
+                                                    float s1, float s2)
+{
+    typedef typename KindTraits<KIND>::T T;
+    float z[5][5];
+    for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) {
+            const int yy = y - 2 + a, xx = x - 2 + b;
+            float v = kHole;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                v = decode<KIND>(reinterpret_cast<const T *>(static_cast<const char *>(in) + (int64_t)yy * pitch)[xx]);
+            z[a][b] = v;
+        }
+    const float sw[5] = {s2, s1, s0, s1, s2};
+    df Gu = {0.f, 0.f}, Gv = {0.f, 0.f};
+    for (int a = 0; a < 5; ++a) {
+        if (sw[a] == 0.f) continue;
+        df hu = {0.f, 0.f}, hv = {0.f, 0.f};
+        if (d1 != 0.f) {
+            hu = df_add(hu, df_mul_f(grad_term<KIND>(z[a][1], z[a][3]), d1));
+            hv = df_add(hv, df_mul_f(grad_term<KIND>(z[1][a], z[3][a]), d1));
+        }
+        if (d2 != 0.f) {
+            hu = df_add(hu, df_mul_f(grad_term<KIND>(z[a][0], z[a][4]), d2));
+            hv = df_add(hv, df_mul_f(grad_term<KIND>(z[0][a], z[4][a]), d2));
+        }
+        Gu = df_add(Gu, df_mul_f(hu, sw[a]));
+        Gv = df_add(Gv, df_mul_f(hv, sw[a]));
+    }
+    float zi[3][3];
+    bool ok[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            zi[a][b] = z[a + 1][b + 1];
+            ok[a][b] = zi[a][b] <= kValidHi;
+        }
+    return refine_candidates<KIND, PHI>(zi, ok, Gu, Gv, x, y, fx, fy, u0, v0);
+}
+
 // ------------------------------------------------------------ the kernel
 
 // Persistent kernel of independent warps.  The work item is a band of 128
@@ -936,8 +1118,10 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
     typedef typename KindTraits<KIND>::T T;
     typedef Row<KIND, GRAD> R;
     constexpr int TH = kCfgs[CFG].th, CR = kCfgs[CFG].cr, NST = kCfgs[CFG].nst, NW = kCfgs[CFG].warps;
-    constexpr int NCH = (TH + 2) / CR;  // chunks per item: rows y0-1 .. y0+TH
-    static_assert((TH + 2) % CR == 0 && NCH >= 1, "chunks must tile an item's rows");
+    constexpr bool SEP5 = GRAD == GRAD_SEP5;
+    constexpr int HR = SEP5 ? 2 : 1;                  // halo rows above and below an item
+    constexpr int NCH = (TH + 2 * HR + CR - 1) / CR;  // chunks per item: rows y0-HR .. y0+TH-1+HR
+    static_assert(SEP5 || (TH + 2) % CR == 0, "3x3 items' chunks tile their rows exactly");
     static_assert(kCfgs[CFG].tw == 128, "a band is 32 lanes x 4 columns");
     static_assert(TH <= 32, "pending-refinement bits hold 32 rows");
     constexpr int PADX = 16 / (int)sizeof(T);
@@ -949,7 +1133,10 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
     __shared__ __align__(8) unsigned long long full[NW][NST];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // (an offset from smem_raw keeps the compiler's knowledge that this is shared memory)
-    unsigned char *ring = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u) + warp * NST * STRIDE;
+    unsigned char *const sbase = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    unsigned char *ring = sbase + warp * NST * STRIDE;
+    // (5x5 filters) this lane's slots of the per-warp ring of row derivatives and smoothings
+    float4 *const dring = reinterpret_cast<float4 *>(sbase + NW * NST * STRIDE + warp * kSep5RingBytes) + lane;
     if (lane == 0) {
 #pragma unroll
         for (int s = 0; s < NST; ++s) mbar_init(smem_addr(&full[warp][s]), 1);
@@ -970,7 +1157,7 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
         const FrameDesc *f = args.frames + pf;
         const int lt = t - __ldg(&f->tile_begin), txs = __ldg(&f->tiles_x);
         const int x = (lt % txs) * 128 - PADX;
-        const int y = (lt / txs) * TH - 1 + (cc % NCH) * CR;
+        const int y = (lt / txs) * TH - HR + (cc % NCH) * CR;
         const uint32_t bar = smem_addr(&full[warp][cc % NST]);
         if (y < __ldg(&f->H)) {
             const CUtensorMap *map = args.maps + pf;
@@ -990,6 +1177,7 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
 
     const bool refine_all = args.flags & TFN_FLAG_REFINE_ALL;  // a negative threshold refines every pixel
     const float wts[3] = {args.w[0], args.w[1], args.w[2]};  // GRAD_WEIGHTED's row weights
+    const Sep5W sw = {args.w[0], args.w[1], args.w[2], args.w[3], args.w[4]};  // GRAD_SEP5's profiles
     int cf = 0, fail_cc = 0;
     unsigned nref = 0;
     bool failed = false;
@@ -1024,13 +1212,14 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
             ucf[k] = __fdiv_rn(uc[k], fx);
         }
 
-        // Sample row j (0 .. TH+1) of the item is image row y0 - 1 + j; rows
-        // at or past the bottom read as holes.  The rows arrive in order, so
-        // the chunk state advances incrementally: row jr of chunk cc.
-        const int rows_in = H - (y0 - 1);
+        // Sample row j (0 .. TH+2HR-1) of the item is image row y0 - HR + j;
+        // rows at or past the bottom read as holes.  The rows arrive in
+        // order, so the chunk state advances incrementally: row jr of chunk cc.
+        const int rows_in = H - (y0 - HR);
         int jr = 0, cc = i * NCH;
         const unsigned char *stage = ring;
-        auto fetch = [&](R &row, int j) -> bool {
+        // (load(in_frame) reads row jr of `stage` into registers)
+        auto fetch_with = [&](auto &&load, int j) -> bool {
             if (jr == 0) {
                 const int st = cc % NST;
                 stage = ring + st * STRIDE;
@@ -1039,10 +1228,7 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
                     return false;
                 }
             }
-            if (j < rows_in)
-                load_row<KIND, GRAD, BOXW, PADX>(stage, jr, lane, row);
-            else
-                hole_row(row);
+            load(j < rows_in);
             if (++jr == CR) {  // the stage's last row is in registers: refill it
                 __syncwarp();
                 if (lane == 0) {
@@ -1054,17 +1240,28 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
             }
             return true;
         };
+        auto fetch = [&](R &row, int j) -> bool {
+            return fetch_with(
+                [&](bool in_frame) {
+                    if (in_frame)
+                        load_row<KIND, GRAD, BOXW, PADX>(stage, jr, lane, row);
+                    else
+                        hole_row(row);
+                },
+                j);
+        };
 
         unsigned long long pend_a = 0, pend_b = 0;  // bit 4 s + k: row y0 + s, column x0 + k
         UpCarry cy;
-        // output row y0 + s from sample rows P (above), C and N (below, fetched here)
-        auto step = [&](const R &P, const R &C, R &N, int s) -> bool {
-            if (!fetch(N, s + 2)) return false;
+        // output row y0 + s from sample rows P (above), C and N (below); the
+        // 5x5 filters' gradients come in gu, gv
+        auto emit = [&](const R &P, const R &C, const R &N, int s, const df(&gu)[4], const df(&gv)[4]) {
             const int y = y0 + s;
             float ox[4], oy[4], oz[4];
             uint32_t mw;
             unsigned rb;
-            row_step<KIND, GRAD, PHI>(P, C, N, cy, uc, __fsub_rn((float)y, v0), fx, fy, thr, wts, ox, oy, oz, mw, rb);
+            row_step<KIND, GRAD, PHI>(P, C, N, cy, uc, __fsub_rn((float)y, v0), fx, fy, thr, wts, gu, gv, ox, oy, oz,
+                                      mw, rb);
             if (y < H && nvalid > 0) {
                 store4(out, args.out_fmt, x0, y, nvalid, ox, oy, oz, mw);
                 if (pts.pts)  // the fused point cloud of this row
@@ -1078,27 +1275,118 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
                 pend_a |= (unsigned long long)rb << (4 * s);
             else
                 pend_b |= (unsigned long long)rb << (4 * (s - 16));
-            return true;
         };
-        R P, C, N;
-        if (!fetch(C, 0) || !fetch(N, 1)) {
-            failed = true;
-            break;
-        }
-        carry_down(C, N, cy);
-        P = C;
-        C = N;
-        // (a rolled loop: unrolling it to rotate the roles of P, C, N costs
-        // more in instruction fetch than the row copies it saves)
-        for (int s = 0; s < TH; ++s) {
-            if (!step(P, C, N, s)) {
+        if constexpr (!SEP5) {
+            const df g0[4] = {};  // (3x3 filters compute their gradients in row_step)
+            R P, C, N;
+            if (!fetch(C, 0) || !fetch(N, 1)) {
                 failed = true;
                 break;
             }
+            carry_down(C, N, cy);
             P = C;
             C = N;
+            // (a rolled loop: unrolling it to rotate the roles of P, C, N costs
+            // more in instruction fetch than the row copies it saves)
+            for (int s = 0; s < TH; ++s) {
+                if (!fetch(N, s + 2)) {
+                    failed = true;
+                    break;
+                }
+                emit(P, C, N, s, g0, g0);
+                P = C;
+                C = N;
+            }
+        } else {
+            // 5x5 filters: sample row j's derivative and smoothing go to ring
+            // slot j % 5 (4 float4 per lane: Dh.h, Dh.l, Sh.h, Sh.l); output
+            // row y0 + s is made once sample row s + 4 has arrived, from
+            // slots s .. s + 4 and the sample rows P, C, N (image rows
+            // y0 + s - 1 .. y0 + s + 1).
+            int wslot = 0;
+            float z8[8];
+            auto take = [&](R &row, int j) -> bool {
+                if (!fetch_with(
+                        [&](bool in_frame) {
+                            if (in_frame) {
+                                load_row8<KIND, BOXW, PADX>(stage, jr, lane, z8);
+                            } else {
+#pragma unroll
+                                for (int c = 0; c < 8; ++c) z8[c] = kHole;
+                            }
+                        },
+                        j))
+                    return false;
+                df Dh[4], Sh[4];
+                sep5_row<KIND>(z8, sw, Dh, Sh);
+                float4 *q = dring + wslot * (4 * 32);
+                q[0] = make_float4(Dh[0].h, Dh[1].h, Dh[2].h, Dh[3].h);
+                q[32] = make_float4(Dh[0].l, Dh[1].l, Dh[2].l, Dh[3].l);
+                q[64] = make_float4(Sh[0].h, Sh[1].h, Sh[2].h, Sh[3].h);
+                q[96] = make_float4(Sh[0].l, Sh[1].l, Sh[2].l, Sh[3].l);
+                wslot = wslot == 4 ? 0 : wslot + 1;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) row.z[c] = z8[c + 1];
+                return true;
+            };
+            R P, C, N, X;
+            if (!take(X, 0) || !take(P, 1) || !take(C, 2) || !take(N, 3)) {
+                failed = true;
+                break;
+            }
+            carry_down(P, C, cy);
+            int rslot = 0;  // ring slot of sample row s
+            for (int s = 0; s < TH; ++s) {
+                if (!take(X, s + 4)) {
+                    failed = true;
+                    break;
+                }
+                float4 dh[5], dl[5], sh[5], sl[5];
+#pragma unroll
+                for (int a = 0; a < 5; ++a) {
+                    const int q = rslot + a < 5 ? rslot + a : rslot + a - 5;
+                    const float4 *r = dring + q * (4 * 32);
+                    dh[a] = r[0];
+                    dl[a] = r[32];
+                    if (a != 2) {
+                        sh[a] = r[64];
+                        sl[a] = r[96];
+                    } else {
+                        sh[a] = sl[a] = make_float4(0.f, 0.f, 0.f, 0.f);  // (the centre row's Sh is not used)
+                    }
+                }
+                df gu[4], gv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    df D[5], S[5];
+#pragma unroll
+                    for (int a = 0; a < 5; ++a) {
+                        D[a] = {f4_at(dh[a], k), f4_at(dl[a], k)};
+                        S[a] = {f4_at(sh[a], k), f4_at(sl[a], k)};
+                    }
+                    gu[k] = sep5_sym(D[0], D[1], D[2], D[3], D[4], sw.s0, sw.s1, sw.s2);
+                    gv[k] = sep5_anti(S[0], S[1], S[3], S[4], sw.d1, sw.d2);
+                }
+                emit(P, C, N, s, gu, gv);
+                P = C;
+                C = N;
+                N = X;
+                rslot = rslot == 4 ? 0 : rslot + 1;
+            }
         }
         if (failed) break;
+        if constexpr ((TH + 2 * HR) % CR != 0) {
+            // the item's last chunk is partly unused: its stage is free now
+            if (jr != 0) {
+                __syncwarp();
+                if (lane == 0) {
+                    fence_async_shared();
+                    issue(cc + NST);
+                }
+                jr = 0;
+                ++cc;
+            }
+        }
         // Rare: the double-float path for this item's flagged pixels (lanes in
         // parallel); the later store to the same pixel wins.
         while (pend_a | pend_b) {
@@ -1111,8 +1399,13 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
                 pend_b &= pend_b - 1;
             }
             const int x = x0 + (b & 3), y = y0 + (b >> 2);
-            store1(out, args.out_fmt, x, y,
-                   refine_from_input<KIND, GRAD, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0, wts[0], wts[1], wts[2]));
+            Vec3 nr;
+            if constexpr (SEP5)
+                nr = refine_from_input_sep5<KIND, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0, sw.d1, sw.d2, sw.s0,
+                                                       sw.s1, sw.s2);
+            else
+                nr = refine_from_input<KIND, GRAD, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0, wts[0], wts[1], wts[2]);
+            store1(out, args.out_fmt, x, y, nr);
             ++nref;
         }
     }
@@ -1140,7 +1433,7 @@ KernelFn select_kernel(int grad, int phi, int cfg)
     if (grad == G && phi == P && cfg == C) return &normals_kernel<KIND, G, P, C>;
 #define TFN_KC(G, P) TFN_K(G, P, 0) TFN_K(G, P, 1) TFN_K(G, P, 2) TFN_K(G, P, 3)
 #define TFN_KP(G) TFN_KC(G, PHI_MEAN) TFN_KC(G, PHI_MEDIAN)
-    TFN_KP(GRAD_FD) TFN_KP(GRAD_SOBEL) TFN_KP(GRAD_SCHARR) TFN_KP(GRAD_PREWITT) TFN_KP(GRAD_WEIGHTED)
+    TFN_KP(GRAD_FD) TFN_KP(GRAD_SOBEL) TFN_KP(GRAD_SCHARR) TFN_KP(GRAD_PREWITT) TFN_KP(GRAD_WEIGHTED) TFN_KP(GRAD_SEP5)
 #undef TFN_KP
 #undef TFN_KC
 #undef TFN_K

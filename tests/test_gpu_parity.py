@@ -310,7 +310,7 @@ def test_invalid_arguments_are_rejected(torch, tfn, ctx):
     assert tfn.tfn_normals(ctx.handle, ctypes.byref(f), ctypes.byref(meth), s) == tfn.TFN_ERR_UNSUPPORTED
     f = tfn.make_frame(img, n, m, dict(fx=float("nan"), fy=10.0, u0=8.0, v0=8.0))
     assert tfn.tfn_normals(ctx.handle, ctypes.byref(f), ctypes.byref(meth), s) == tfn.TFN_ERR_INVALID_ARG
-    bad = tfn.make_method(grad=7)
+    bad = tfn.make_method(grad=9)
     f = tfn.make_frame(img, n, m, dict(fx=10.0, fy=10.0, u0=8.0, v0=8.0))
     assert tfn.tfn_normals(ctx.handle, ctypes.byref(f), ctypes.byref(bad), s) == tfn.TFN_ERR_INVALID_ARG
 

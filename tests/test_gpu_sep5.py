@@ -1,0 +1,148 @@
+"""Parity of the CUDA path's 5x5 gradient filters (TFN_GRAD_SEP5 and its named members FD5, Sobel5,
+Prewitt5) with the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+from tests.parity import compare
+from tests.test_gpu_parity import SIZES, depth_frames, disparity_frames, to_dev
+
+pytestmark = pytest.mark.gpu
+
+NAMED = ["fd5", "sobel5", "prewitt5"]
+PROFILES = [(1.0, 0.3, 2.0, 0.5, 0.1), (1.0, 0.0, 1.0, 0.0, 1.0), (3.0, -1.0, 1.0, 2.0, -0.5),
+            (1.0, 0.0, 2.0, 1.0, 0.0)]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def tfn(torch):
+    import paper_2005_08165_gb300 as tfn
+    return tfn
+
+
+@pytest.fixture(scope="module")
+def ctx(tfn):
+    c = tfn.Context(0)
+    yield c
+    assert c.device_status() == 0
+    c.close()
+
+
+@pytest.mark.parametrize("grad", NAMED)
+@pytest.mark.parametrize("phi", ["mean", "median"])
+def test_named_5x5_filters(torch, tfn, ctx, grad, phi):
+    frames = depth_frames(SIZES + [(480, 640)], 2300)
+    inputs = [to_dev(torch, tfn, img) for img, _ in frames]
+    n, m = ctx.normals_batch(inputs, [cam for _, cam in frames], grad=grad, phi=phi)
+    torch.cuda.synchronize()
+    for k, (img, cam) in enumerate(frames):
+        compare(n[k].cpu().numpy(), m[k].cpu().numpy(), img, cam, grad=grad, phi=phi)
+
+
+@pytest.mark.parametrize("weights", PROFILES)
+@pytest.mark.parametrize("phi", ["mean", "median"])
+def test_sep5_profiles(torch, tfn, ctx, weights, phi):
+    frames = depth_frames(SIZES, 2400)
+    inputs = [to_dev(torch, tfn, img) for img, _ in frames]
+    n, m = ctx.normals_batch(inputs, [cam for _, cam in frames], grad="sep5", phi=phi, weights=weights)
+    torch.cuda.synchronize()
+    for k, (img, cam) in enumerate(frames):
+        compare(n[k].cpu().numpy(), m[k].cpu().numpy(), img, cam, grad="sep5", phi=phi, weights=weights)
+
+
+@pytest.mark.parametrize("kind", ["f16", "u16", "dispf32"])
+def test_5x5_filters_on_other_inputs(torch, tfn, ctx, kind):
+    if kind == "f16":
+        img, cam = depth_frames([(67, 131)], 2500)[0]
+        img = img.astype(np.float16)
+        n, m = ctx.normals(to_dev(torch, tfn, img), cam, grad="sobel5")
+        torch.cuda.synchronize()
+        compare(n.cpu().numpy(), m.cpu().numpy(), img, cam, grad="sobel5", phi="mean")
+        return
+    raw, cam = disparity_frames([(67, 131)], 2550)[0]
+    if kind == "u16":
+        for grad, phi in (("fd5", "median"), ("sobel5", "mean")):
+            n, m = ctx.normals(to_dev(torch, tfn, raw), cam, grad=grad, phi=phi, disparity=True)
+            torch.cuda.synchronize()
+            compare(n.cpu().numpy(), m.cpu().numpy(), raw, cam, grad=grad, phi=phi, disparity=True, baseline=0.1)
+    else:
+        d = (raw / 16.0).astype(np.float32)
+        n, m = ctx.normals(to_dev(torch, tfn, d), cam, grad="prewitt5", disparity=True, disp_scale=1.0)
+        torch.cuda.synchronize()
+        compare(n.cpu().numpy(), m.cpu().numpy(), d, cam, grad="prewitt5", phi="mean", disparity=True,
+                baseline=0.1, disp_scale=1.0)
+
+
+def test_5x5_double_float_path_and_tile_shapes(torch, tfn, ctx):
+    img, cam = depth_frames([(61, 99)], 2600)[0]
+    d = to_dev(torch, tfn, img)
+    for grad, w in (("sobel5", None), ("sep5", (3.0, -1.0, 1.0, 2.0, -0.5))):
+        n, m = ctx.normals(d, cam, grad=grad, weights=w, flags=tfn.TFN_FLAG_REFINE_ALL)
+        torch.cuda.synchronize()
+        compare(n.cpu().numpy(), m.cpu().numpy(), img, cam, grad=grad, phi="mean", weights=w, tol=1e-5)
+    ref = None
+    with tfn.Context(0) as c:
+        for shape in range(tfn.tfn_tile_shape_count()):
+            c.set_tile_shape(shape)
+            nn, mm = c.normals(d, cam, grad="fd5", phi="median")
+            torch.cuda.synchronize()
+            got = (nn.cpu(), mm.cpu())
+            if ref is None:
+                ref = got
+            assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1]), f"shape {shape} differs"
+        assert c.device_status() == 0
+
+
+def test_5x5_filters_through_host_path_and_plan(torch, tfn, ctx):
+    frames = depth_frames([(96, 128)] * 3, 2700)
+    cam = frames[0][1]
+    imgs = [img for img, _ in frames]
+    dev_in = [to_dev(torch, tfn, x) for x in imgs]
+    ref_n, ref_m = ctx.normals_batch(dev_in, cam, grad="sobel5")
+    torch.cuda.synchronize()
+    stack = torch.from_numpy(np.stack(imgs)).pin_memory()
+    hn = torch.empty((3, 3, 96, 128), dtype=torch.float32).pin_memory()
+    hm = torch.empty((3, 96, 128), dtype=torch.uint8).pin_memory()
+    ctx.normals_batch_host([stack[k] for k in range(3)], cam, [hn[k] for k in range(3)], [hm[k] for k in range(3)],
+                           grad="sobel5")
+    for k in range(3):
+        assert torch.equal(hn[k], ref_n[k].cpu()) and torch.equal(hm[k], ref_m[k].cpu())
+    plan = ctx.plan(dev_in, cam, grad="sobel5")
+    plan.launch()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(plan.normals, ref_n))
+    plan.close()
+
+
+@pytest.mark.parametrize("phi", ["mean", "median"])
+def test_no_candidate_special_case(torch, tfn, ctx, phi):
+    # plateaus of equal depth: pixels whose 8 neighbours all share their depth while a 5x5 filter's outer
+    # taps see the next plateau get [0, 0, -1] (Sec. III special case)
+    img = np.full((40, 48), 2.0, np.float32)
+    img[:, 20:] = 2.5
+    img[24:, :] += 0.25
+    img[10, 10] = 0.0  # a hole
+    cam = dict(fx=40.0, fy=40.0, u0=23.5, v0=19.5)
+    for grad in ("fd5", "sobel5", "fd"):
+        n, m = ctx.normals(to_dev(torch, tfn, img), cam, grad=grad, phi=phi)
+        torch.cuda.synchronize()
+        compare(n.cpu().numpy(), m.cpu().numpy(), img, cam, grad=grad, phi=phi)
+    n, m = ctx.normals(to_dev(torch, tfn, img), cam, grad="fd5", phi=phi)
+    torch.cuda.synchronize()
+    assert n[:, 19, 18].tolist() == [0.0, 0.0, -1.0]
+
+
+def test_sep5_weights_are_validated(torch, tfn, ctx):
+    d = to_dev(torch, tfn, np.full((16, 16), 2.0, np.float32))
+    cam = dict(fx=20.0, fy=20.0, u0=7.5, v0=7.5)
+    for w in ((2.0, -1.0, 1.0, 0.0, 0.0), (1.0, 0.0, 1.0, -0.5, 0.0), (float("nan"), 0.0, 1.0, 0.0, 0.0)):
+        with pytest.raises(tfn.TfnError) as e:
+            ctx.normals(d, cam, grad="sep5", weights=w)
+        assert e.value.status == tfn.TFN_ERR_INVALID_ARG

@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--frames", type=int, default=N_FRAMES, help="frames per batch (profiling cases only)")
-    ap.add_argument("--grad", default="fd", choices=["fd", "sobel", "scharr", "prewitt"])
+    ap.add_argument("--grad", default="fd", choices=["fd", "sobel", "scharr", "prewitt", "fd5", "sobel5", "prewitt5"])
     ap.add_argument("--phi", default="mean", choices=["mean", "median"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

@@ -792,25 +792,6 @@ __device__ __forceinline__ void sep5_row(const float (&z)[8], const Sep5W &w, df
     }
 }
 
-// G = c0 a2 + c1 (a1 + a3) + c2 (a0 + a4) with zero-weight terms dropped.
-__device__ __forceinline__ df sep5_sym(df a0, df a1, df a2, df a3, df a4, float c0, float c1, float c2)
-{
-    const df zero = {0.f, 0.f};
-    const df t0 = c0 != 0.f ? df_mul_f(a2, c0) : zero;
-    const df t1 = c1 != 0.f ? df_mul_f(df_add(a1, a3), c1) : zero;
-    const df t2 = c2 != 0.f ? df_mul_f(df_add(a0, a4), c2) : zero;
-    return df_add(t0, df_add(t1, t2));
-}
-
-// G = c1 (a3 - a1) + c2 (a4 - a0) with zero-weight terms dropped.
-__device__ __forceinline__ df sep5_anti(df a0, df a1, df a3, df a4, float c1, float c2)
-{
-    const df zero = {0.f, 0.f};
-    const df t1 = c1 != 0.f ? df_mul_f(df_add(a3, df_neg(a1)), c1) : zero;
-    const df t2 = c2 != 0.f ? df_mul_f(df_add(a4, df_neg(a0)), c2) : zero;
-    return df_add(t1, t2);
-}
-
 // ------------------------------------------------------------ TMA / mbarrier
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -1341,31 +1322,59 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
                     failed = true;
                     break;
                 }
-                float4 dh[5], dl[5], sh[5], sl[5];
-#pragma unroll
-                for (int a = 0; a < 5; ++a) {
+                // G_u = s0 Dh(s+2) + s1 (Dh(s+1) + Dh(s+3)) + s2 (Dh(s) + Dh(s+4)),
+                // G_v = d1 (Sh(s+3) - Sh(s+1)) + d2 (Sh(s+4) - Sh(s)); the ring
+                // rows are read pair by pair to keep few registers live
+                auto ring_at = [&](int a, int v) -> float4 {
                     const int q = rslot + a < 5 ? rslot + a : rslot + a - 5;
-                    const float4 *r = dring + q * (4 * 32);
-                    dh[a] = r[0];
-                    dl[a] = r[32];
-                    if (a != 2) {
-                        sh[a] = r[64];
-                        sl[a] = r[96];
-                    } else {
-                        sh[a] = sl[a] = make_float4(0.f, 0.f, 0.f, 0.f);  // (the centre row's Sh is not used)
+                    return dring[(q * 4 + v) * 32];
+                };
+                const df zero = {0.f, 0.f};
+                df gu[4], gv[4], t[4];
+                {
+                    const float4 h = ring_at(2, 0), l = ring_at(2, 1);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        gu[k] = sw.s0 != 0.f ? df_mul_f(df{f4_at(h, k), f4_at(l, k)}, sw.s0) : zero;
+                }
+                {
+                    const float4 h1 = ring_at(1, 0), l1 = ring_at(1, 1), h3 = ring_at(3, 0), l3 = ring_at(3, 1);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        t[k] = sw.s1 != 0.f ? df_mul_f(df_add(df{f4_at(h1, k), f4_at(l1, k)}, df{f4_at(h3, k), f4_at(l3, k)}),
+                                                       sw.s1)
+                                            : zero;
+                }
+                {
+                    const float4 h0 = ring_at(0, 0), l0 = ring_at(0, 1), h4 = ring_at(4, 0), l4 = ring_at(4, 1);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const df t2 = sw.s2 != 0.f ? df_mul_f(df_add(df{f4_at(h0, k), f4_at(l0, k)},
+                                                                     df{f4_at(h4, k), f4_at(l4, k)}),
+                                                              sw.s2)
+                                                   : zero;
+                        gu[k] = df_add(gu[k], df_add(t[k], t2));
                     }
                 }
-                df gu[4], gv[4];
+                {
+                    const float4 h1 = ring_at(1, 2), l1 = ring_at(1, 3), h3 = ring_at(3, 2), l3 = ring_at(3, 3);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    df D[5], S[5];
+                    for (int k = 0; k < 4; ++k)
+                        gv[k] = sw.d1 != 0.f ? df_mul_f(df_add(df{f4_at(h3, k), f4_at(l3, k)},
+                                                               df_neg(df{f4_at(h1, k), f4_at(l1, k)})),
+                                                        sw.d1)
+                                             : zero;
+                }
+                {
+                    const float4 h0 = ring_at(0, 2), l0 = ring_at(0, 3), h4 = ring_at(4, 2), l4 = ring_at(4, 3);
 #pragma unroll
-                    for (int a = 0; a < 5; ++a) {
-                        D[a] = {f4_at(dh[a], k), f4_at(dl[a], k)};
-                        S[a] = {f4_at(sh[a], k), f4_at(sl[a], k)};
+                    for (int k = 0; k < 4; ++k) {
+                        const df t2 = sw.d2 != 0.f ? df_mul_f(df_add(df{f4_at(h4, k), f4_at(l4, k)},
+                                                                     df_neg(df{f4_at(h0, k), f4_at(l0, k)})),
+                                                              sw.d2)
+                                                   : zero;
+                        gv[k] = df_add(gv[k], t2);
                     }
-                    gu[k] = sep5_sym(D[0], D[1], D[2], D[3], D[4], sw.s0, sw.s1, sw.s2);
-                    gv[k] = sep5_anti(S[0], S[1], S[3], S[4], sw.d1, sw.d2);
                 }
                 emit(P, C, N, s, gu, gv);
                 P = C;

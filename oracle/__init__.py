@@ -150,6 +150,9 @@ def points(img, fx, fy, u0, v0, *, disparity=False, baseline=1.0, disp_scale=1.0
     return out
 
 
+from .pca import planepca  # noqa: E402  (Sec. II-A, Eq. planepca; uses points() above)
+
+
 def oct_encode(n):
     """Octahedral map of vectors (3, ...) onto the square [-1, 1]^2 (Cigolle et al., "A Survey of
     Efficient Representations for Independent Unit Vectors", JCGT 3(2), 2014, the "oct" mapping):

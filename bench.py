@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--frames", type=int, default=N_FRAMES, help="frames per batch (profiling cases only)")
-    ap.add_argument("--grad", default="fd", choices=["fd", "sobel", "scharr", "prewitt", "fd5", "sobel5", "prewitt5"])
+    ap.add_argument("--grad", default="fd",
+                    choices=["fd", "sobel", "scharr", "prewitt", "fd5", "sobel5", "prewitt5", "planepca"])
     ap.add_argument("--phi", default="mean", choices=["mean", "median"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -360,14 +361,15 @@ def run_ours(args):
             lm = statistics.mean(pv)
             variants["weighted_131_mean_f32"] = {"frames_per_s": round(nf / (lm * 1e-3), 1),
                                                  "hbm_gbs": round(BYTES_PER_PX["f32_in_f32_out"] * px / (lm * 1e-3) / 1e9, 1)}
-            # the 5x5 gradient filters (filter sizes)
-            for grad, phi in (("fd5", "mean"), ("sobel5", "mean"), ("sobel5", "median")):
+            # the 5x5 gradient filters (filter sizes), and the PlanePCA estimator on the same batch
+            for grad, phi in (("fd5", "mean"), ("sobel5", "mean"), ("sobel5", "median"), ("planepca", "mean")):
                 splan = ctx.plan(ins, cam, grad=grad, phi=phi, normals=outs, masks=mks)
                 tot, pv = time_launches(torch, lambda: splan.launch(stream), max(5, args.steps // 2), 3, stream)
                 splan.close()
                 lm = statistics.mean(pv)
-                variants[f"{grad}_{phi}_f32"] = {"frames_per_s": round(nf / (lm * 1e-3), 1),
-                                                 "hbm_gbs": round(BYTES_PER_PX["f32_in_f32_out"] * px / (lm * 1e-3) / 1e9, 1)}
+                key = "planepca_f32" if grad == "planepca" else f"{grad}_{phi}_f32"
+                variants[key] = {"frames_per_s": round(nf / (lm * 1e-3), 1),
+                                 "hbm_gbs": round(BYTES_PER_PX["f32_in_f32_out"] * px / (lm * 1e-3) / 1e9, 1)}
         serving = None
         if not args.no_serving:
             serving = run_serving(torch, tfn, ctx, dev, d, args.serve_requests)

@@ -162,15 +162,26 @@ typedef struct tfn_frame {
     int64_t points_plane_stride;  /* bytes, multiple of 16, >= points_pitch * height */
 } tfn_frame;
 
+/* Estimators.  TFN_EST_3F2N is the paper's method (Sec. III).  TFN_EST_PLANEPCA
+ * is the comparison estimator of Sec. II-A (Eq. planepca): the 9 back-projected
+ * points of the 3x3 neighbourhood (Eq. intrinsic matrix) have their mean
+ * removed, and the normal is the principal component of smallest variance,
+ * turned to face the camera (n . p < 0).  A pixel is evaluable when it and
+ * its 8 neighbours are valid.  It has no gradient filter and no Phi: grad,
+ * phi and weights are ignored.  FP32 arithmetic; its direction error grows
+ * as the two smallest eigenvalues of the scatter matrix approach each other
+ * (the estimator itself is ill-conditioned there). */
+typedef enum tfn_estimator { TFN_EST_3F2N = 0, TFN_EST_PLANEPCA = 1 } tfn_estimator;
+
 /* Method selection. */
 typedef struct tfn_method {
-    int32_t grad;     /* tfn_grad */
-    int32_t phi;      /* tfn_phi */
-    int32_t output;   /* tfn_output */
-    int32_t flags;    /* TFN_FLAG_* */
-    float weights[5]; /* TFN_GRAD_WEIGHTED: row weights (w0 w1 w2), finite, not all 0;
-                         TFN_GRAD_SEP5: (d1 d2 s0 s1 s2), finite; else ignored */
-    int32_t reserved; /* 0 */
+    int32_t grad;      /* tfn_grad */
+    int32_t phi;       /* tfn_phi */
+    int32_t output;    /* tfn_output */
+    int32_t flags;     /* TFN_FLAG_* */
+    float weights[5];  /* TFN_GRAD_WEIGHTED: row weights (w0 w1 w2), finite, not all 0;
+                          TFN_GRAD_SEP5: (d1 d2 s0 s1 s2), finite; else ignored */
+    int32_t estimator; /* tfn_estimator (0: the paper's 3F2N) */
 } tfn_method;
 
 /* Compute every pixel on the compensated (double-float) path instead of only

@@ -29,6 +29,7 @@ TFN_DEPTH_F32, TFN_DEPTH_F16, TFN_DISP_U16, TFN_DISP_F32 = range(4)
 TFN_GRAD_FD, TFN_GRAD_SOBEL, TFN_GRAD_SCHARR, TFN_GRAD_PREWITT, TFN_GRAD_WEIGHTED, TFN_GRAD_SEP5, TFN_GRAD_FD5, \
     TFN_GRAD_SOBEL5, TFN_GRAD_PREWITT5 = range(9)
 TFN_PHI_MEAN, TFN_PHI_MEDIAN = range(2)
+TFN_EST_3F2N, TFN_EST_PLANEPCA = range(2)
 TFN_OUT_F32, TFN_OUT_F16, TFN_OUT_BF16, TFN_OUT_F16X4, TFN_OUT_BF16X4, TFN_OUT_OCT16 = range(6)
 TFN_FLAG_REFINE_ALL = 1
 TFN_REQ_HOST = 1
@@ -60,7 +61,7 @@ class tfn_frame(ctypes.Structure):
 
 class tfn_method(ctypes.Structure):
     _fields_ = [("grad", ctypes.c_int32), ("phi", ctypes.c_int32), ("output", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("weights", ctypes.c_float * 5), ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("weights", ctypes.c_float * 5), ("estimator", ctypes.c_int32)]
 
 
 class tfn_server_opts(ctypes.Structure):
@@ -275,8 +276,11 @@ def make_frame(inp, normals, mask, cam, disparity=False, disp_scale=1.0 / 16, ou
 
 def make_method(grad="fd", phi="mean", output="f32", flags=0, weights=None) -> tfn_method:
     """grad="weighted" takes the row weights (w0, w1, w2) of the gradient filter in `weights`; grad="sep5" takes
-    the 5x5 profiles (d1, d2, s0, s1, s2)."""
+    the 5x5 profiles (d1, d2, s0, s1, s2); grad="planepca" selects the PlanePCA estimator (TFN_EST_PLANEPCA,
+    which has no gradient filter and no Phi)."""
     m = tfn_method()
+    if grad == "planepca":
+        m.estimator, grad = TFN_EST_PLANEPCA, "fd"
     m.grad = GRADS[grad] if isinstance(grad, str) else grad
     m.phi = PHIS[phi] if isinstance(phi, str) else phi
     m.output = OUTPUTS[output] if isinstance(output, str) else output

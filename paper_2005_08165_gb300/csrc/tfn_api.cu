@@ -113,7 +113,8 @@ int out_elem_bytes(int fmt)
 tfn_status validate_method(const tfn_method *m)
 {
     if (!m) return TFN_ERR_INVALID_ARG;
-    if (m->grad < 0 || m->grad >= GRAD_COUNT || m->phi < 0 || m->phi >= PHI_COUNT || m->output < 0 ||
+    if (m->estimator != TFN_EST_3F2N && m->estimator != TFN_EST_PLANEPCA) return TFN_ERR_INVALID_ARG;
+    if (m->grad < 0 || m->grad > GRAD_PREWITT5 || m->phi < 0 || m->phi >= PHI_COUNT || m->output < 0 ||
         m->output > OUT_OCT16 || (m->flags & ~TFN_FLAG_REFINE_ALL))
         return TFN_ERR_INVALID_ARG;
     if (m->grad == GRAD_WEIGHTED) {
@@ -263,10 +264,11 @@ int frame_tiles(const tfn_frame &f, int cfg)
 tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
                           uint32_t *d_status, int nframes, int total_tiles, int num_sms, cudaStream_t stream)
 {
-    KernelFn fn = kernel_for(kind, m.grad, m.phi, cfg);
+    const int grad = method_grad(m);
+    KernelFn fn = kernel_for(kind, grad, method_phi(m), cfg);
     if (!fn) return TFN_ERR_UNSUPPORTED;
     const int threads = cfg_threads(cfg);
-    const size_t smem = smem_bytes(kind, cfg, m.grad);
+    const size_t smem = smem_bytes(kind, cfg, grad);
     if (!cuda_ok(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                  "cudaFuncSetAttribute"))
         return TFN_ERR_CUDA;

@@ -105,7 +105,7 @@ inline bool small_launch(const tfn_frame *frames, int n, int num_sms)
 inline int choose_cfg(const tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method &m)
 {
     if (c->forced_cfg >= 0) return c->forced_cfg;
-    const int t = c->tuned[frames[0].input_type][m.grad][m.phi][m.output];
+    const int t = c->tuned[frames[0].input_type][method_grad(m)][method_phi(m)][m.output];
     if (t >= 0) return t;
     return small_launch(frames, n, c->num_sms) ? kSmallCfg : 0;
 }

@@ -9,7 +9,9 @@ namespace tfn {
 
 enum Kind { KIND_DEPTH_F32 = 0, KIND_DEPTH_F16 = 1, KIND_DISP_U16 = 2, KIND_DISP_F32 = 3, KIND_COUNT = 4 };
 // GRAD_FD5 .. GRAD_PREWITT5 are GRAD_SEP5 with fixed weights (sep5_weights);
-// the kernels are compiled for GRAD_FD .. GRAD_SEP5.
+// GRAD_PLANEPCA stands for the PlanePCA estimator (tfn_method.estimator), a
+// kernel with no gradient filter and no Phi.  The kernels are compiled for
+// GRAD_FD .. GRAD_SEP5 and GRAD_PLANEPCA (with PHI_MEAN).
 enum Grad {
     GRAD_FD = 0,
     GRAD_SOBEL = 1,
@@ -20,7 +22,8 @@ enum Grad {
     GRAD_FD5 = 6,
     GRAD_SOBEL5 = 7,
     GRAD_PREWITT5 = 8,
-    GRAD_COUNT = 9
+    GRAD_PLANEPCA = 9,
+    GRAD_COUNT = 10
 };
 enum Phi { PHI_MEAN = 0, PHI_MEDIAN = 1, PHI_COUNT = 2 };
 enum OutFmt { OUT_F32 = 0, OUT_F16 = 1, OUT_BF16 = 2, OUT_F16X4 = 3, OUT_BF16X4 = 4, OUT_OCT16 = 5 };
@@ -90,7 +93,7 @@ inline size_t stage_stride(int kind, int c) { return (stage_bytes(kind, c) + 127
 // GRAD_SEP5 keeps each lane's row derivatives and smoothings of the last 5
 // sample rows in shared memory: 5 rows x 4 float4 per lane.
 constexpr size_t kSep5RingBytes = 5 * 4 * 32 * 16;
-inline bool grad_is_sep5(int grad) { return grad >= GRAD_SEP5; }
+inline bool grad_is_sep5(int grad) { return grad >= GRAD_SEP5 && grad <= GRAD_PREWITT5; }
 inline size_t smem_bytes(int kind, int c, int grad)
 {
     return (size_t)kCfgs[c].warps * (kCfgs[c].nst * stage_stride(kind, c) + (grad_is_sep5(grad) ? kSep5RingBytes : 0)) +
@@ -115,6 +118,11 @@ KernelFn kernel_for(int kind, int grad, int phi, int cfg);
 #include "../../include/tfn.h"
 
 namespace tfn {
+
+// The kernel a method runs: its filter (GRAD_PLANEPCA for the PlanePCA
+// estimator) and Phi (PHI_MEAN for PlanePCA).
+inline int method_grad(const tfn_method &m) { return m.estimator == TFN_EST_PLANEPCA ? (int)GRAD_PLANEPCA : m.grad; }
+inline int method_phi(const tfn_method &m) { return m.estimator == TFN_EST_PLANEPCA ? (int)PHI_MEAN : m.phi; }
 
 // Host helpers shared by the entry points (tfn_api.cu).
 bool cuda_ok(cudaError_t e, const char *what);

@@ -398,7 +398,8 @@ __device__ __forceinline__ T from_bits16(uint32_t b)
 // (Sobel-type) filter also carry w = 1/Z per sample as wh + wl.
 template <int KIND, int GRAD>
 struct Row {
-    static constexpr bool kW = !KindTraits<KIND>::disparity && GRAD != GRAD_FD;
+    static constexpr bool kW = !KindTraits<KIND>::disparity && GRAD != GRAD_FD && GRAD != GRAD_SEP5 &&
+                               GRAD != GRAD_PLANEPCA;
     float z[6];
     float wh[kW ? 6 : 1], wl[kW ? 6 : 1];
 };
@@ -789,6 +790,170 @@ __device__ __forceinline__ void sep5_row(const float (&z)[8], const Sep5W &w, df
         const df a2 = w.s2 != 0.f ? df_mul_f(df_add(val(c - 2), val(c + 2)), w.s2) : zero;
         const bool sok = (w.s0 == 0.f || ok[c]) && (w.s1 == 0.f || ok1) && (w.s2 == 0.f || ok2);
         Sh[k] = sok ? df_add(a0, df_add(a1, a2)) : df_nan();
+    }
+}
+
+// ------------------------------------------------------------ PlanePCA
+//
+// The comparison estimator of Sec. II-A (Eq. planepca): the normal is the
+// eigenvector of the smallest eigenvalue of the scatter matrix of the 9
+// back-projected points of the 3x3 neighbourhood, centred on their mean,
+// turned to face the camera.  The points are taken relative to the centre
+// pixel's in the algebraic form (dx = (dz (u - u0) + Z_j du)/fx, likewise dy,
+// with dz = Z_j - Z_i exact for depths within a factor 2, or computed as
+// f t_c (d_i - d_j)/(d_i d_j) for disparity), so that the FP32 coordinates
+// keep their accuracy relative to the neighbourhood's size.  The smallest
+// eigenvalue comes from Newton's method on the characteristic polynomial
+// started at 0 (below it; the iterates rise monotonically to it), and the
+// eigenvector from the largest cross product of two rows of M - lambda I.
+
+constexpr int kPcaNewton = 12;
+
+template <int KIND>
+__device__ __forceinline__ void pca_pixel(const float (&w)[3][3], float uc, float vc, float rfx, float rfy, float ztc,
+                                          float &nx, float &ny, float &nz, bool &ok)
+{
+    ok = fmaxf(fmaxf(fmaxf(w[0][0], w[0][1]), fmaxf(w[0][2], w[1][0])),
+               fmaxf(fmaxf(w[1][1], w[1][2]), fmaxf(fmaxf(w[2][0], w[2][1]), w[2][2]))) <= kValidHi;
+    const float si = w[1][1];
+    float rx[9], ry[9], rz[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const int j = 3 * a + b;
+            const float sj = w[a][b];
+            float dz, Zj;
+            if constexpr (KindTraits<KIND>::disparity) {
+                // Z = ztc / s: dz = ztc (s_i - s_j) / (s_i s_j)
+                Zj = __fdiv_rn(ztc, sj);
+                dz = __fdiv_rn(__fmul_rn(ztc, __fsub_rn(si, sj)), __fmul_rn(si, sj));
+            } else {
+                Zj = sj;
+                dz = __fsub_rn(sj, si);
+            }
+            const float du = (float)(b - 1), dv = (float)(a - 1);
+            rx[j] = __fmul_rn(__fmaf_rn(dz, uc, __fmul_rn(du, Zj)), rfx);
+            ry[j] = __fmul_rn(__fmaf_rn(dz, vc, __fmul_rn(dv, Zj)), rfy);
+            rz[j] = dz;
+        }
+    float mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        mx = __fadd_rn(mx, rx[j]);
+        my = __fadd_rn(my, ry[j]);
+        mz = __fadd_rn(mz, rz[j]);
+    }
+    const float r9 = 1.f / 9.f;
+    mx = __fmul_rn(mx, r9);
+    my = __fmul_rn(my, r9);
+    mz = __fmul_rn(mz, r9);
+    float m00 = 0.f, m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        const float x = __fsub_rn(rx[j], mx), y = __fsub_rn(ry[j], my), z = __fsub_rn(rz[j], mz);
+        m00 = __fmaf_rn(x, x, m00);
+        m01 = __fmaf_rn(x, y, m01);
+        m02 = __fmaf_rn(x, z, m02);
+        m11 = __fmaf_rn(y, y, m11);
+        m12 = __fmaf_rn(y, z, m12);
+        m22 = __fmaf_rn(z, z, m22);
+    }
+    // trace 1 (the direction does not depend on the scale; this keeps the
+    // cubic's coefficients in range)
+    const float tr = __fadd_rn(__fadd_rn(m00, m11), m22);
+    const float s = ok && tr > 0.f ? __frcp_rn(tr) : 0.f;
+    m00 = __fmul_rn(m00, s);
+    m01 = __fmul_rn(m01, s);
+    m02 = __fmul_rn(m02, s);
+    m11 = __fmul_rn(m11, s);
+    m12 = __fmul_rn(m12, s);
+    m22 = __fmul_rn(m22, s);
+    // det(M - l I) = c0 - c1 l + c2 l^2 - l^3, c2 = 1
+    const float k0 = __fmaf_rn(m11, m22, -__fmul_rn(m12, m12));
+    const float k1 = __fmaf_rn(m01, m22, -__fmul_rn(m12, m02));
+    const float k2 = __fmaf_rn(m01, m12, -__fmul_rn(m11, m02));
+    const float c0 = __fmaf_rn(m00, k0, __fmaf_rn(-m01, k1, __fmul_rn(m02, k2)));
+    const float c1 = __fadd_rn(__fadd_rn(k0, __fmaf_rn(m00, m22, -__fmul_rn(m02, m02))),
+                               __fmaf_rn(m00, m11, -__fmul_rn(m01, m01)));
+    float l = 0.f;
+#pragma unroll
+    for (int it = 0; it < kPcaNewton; ++it) {
+        const float p = __fmaf_rn(-l, __fmaf_rn(-l, __fsub_rn(1.f, l), c1), c0);  // c0 - l (c1 - l (1 - l))
+        const float dp = __fmaf_rn(l, __fmaf_rn(-3.f, l, 2.f), -c1);               // -c1 + l (2 - 3 l)
+        l = dp < 0.f ? __fsub_rn(l, __fdiv_rn(p, dp)) : l;
+    }
+    // The eigenvector: the largest cross product of two rows of A = M - l I.
+    // The cubic locates l only to about u / p'(l), coarse where the two
+    // smallest eigenvalues crowd together, so l is then replaced once by the
+    // Rayleigh quotient of that vector (accurate to the square of its error)
+    // and the cross products are taken again.
+    float bx = 0.f, by = 0.f, bz = 1.f;
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            // l = b^T M b / b^T b
+            const float mbx = __fmaf_rn(m00, bx, __fmaf_rn(m01, by, __fmul_rn(m02, bz)));
+            const float mby = __fmaf_rn(m01, bx, __fmaf_rn(m11, by, __fmul_rn(m12, bz)));
+            const float mbz = __fmaf_rn(m02, bx, __fmaf_rn(m12, by, __fmul_rn(m22, bz)));
+            const float num = __fmaf_rn(bx, mbx, __fmaf_rn(by, mby, __fmul_rn(bz, mbz)));
+            const float den = __fmaf_rn(bx, bx, __fmaf_rn(by, by, __fmul_rn(bz, bz)));
+            l = den > 0.f ? __fdiv_rn(num, den) : l;
+        }
+        const float a00 = __fsub_rn(m00, l), a11 = __fsub_rn(m11, l), a22 = __fsub_rn(m22, l);
+        float v[3][3];
+        // a0 x a1, a0 x a2, a1 x a2 with a0 = (a00, m01, m02), a1 = (m01, a11, m12), a2 = (m02, m12, a22)
+        v[0][0] = __fmaf_rn(m01, m12, -__fmul_rn(m02, a11));
+        v[0][1] = __fmaf_rn(m02, m01, -__fmul_rn(a00, m12));
+        v[0][2] = __fmaf_rn(a00, a11, -__fmul_rn(m01, m01));
+        v[1][0] = __fmaf_rn(m01, a22, -__fmul_rn(m02, m12));
+        v[1][1] = __fmaf_rn(m02, m02, -__fmul_rn(a00, a22));
+        v[1][2] = __fmaf_rn(a00, m12, -__fmul_rn(m01, m02));
+        v[2][0] = __fmaf_rn(a11, a22, -__fmul_rn(m12, m12));
+        v[2][1] = __fmaf_rn(m12, m02, -__fmul_rn(m01, a22));
+        v[2][2] = __fmaf_rn(m01, m12, -__fmul_rn(a11, m02));
+        float best = -1.f;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float n2 = __fmaf_rn(v[q][0], v[q][0], __fmaf_rn(v[q][1], v[q][1], __fmul_rn(v[q][2], v[q][2])));
+            const bool take = n2 > best;
+            best = take ? n2 : best;
+            bx = take ? v[q][0] : bx;
+            by = take ? v[q][1] : by;
+            bz = take ? v[q][2] : bz;
+        }
+        const float rs = ok && best > 0.f ? rsqrt_approx(best) : 0.f;
+        bx = __fmul_rn(bx, rs);
+        by = __fmul_rn(by, rs);
+        bz = __fmul_rn(bz, rs);
+    }
+    // face the camera: n . (uc / fx, vc / fy, 1) < 0; ties by n_z, n_y, n_x < 0
+    const float d = __fmaf_rn(bx, __fmul_rn(uc, rfx), __fmaf_rn(by, __fmul_rn(vc, rfy), bz));
+    const float key = d != 0.f ? d : bz != 0.f ? bz : by != 0.f ? by : bx;
+    const float sg = key > 0.f ? -1.f : 1.f;
+    // (a non-evaluable pixel's arithmetic may have overflowed: its output is 0)
+    nx = ok ? __fmaf_rn(sg, bx, 0.f) : 0.f;
+    ny = ok ? __fmaf_rn(sg, by, 0.f) : 0.f;
+    nz = ok ? __fmaf_rn(sg, bz, 0.f) : 0.f;
+}
+
+// A lane's 4 pixels of one row by PlanePCA (P, C, N: the sample rows above,
+// at and below; uc = u - u0 per column, vc = v - v0).
+template <int KIND, int GRAD>
+__device__ __forceinline__ void pca_row(const Row<KIND, GRAD> &P, const Row<KIND, GRAD> &C, const Row<KIND, GRAD> &N,
+                                        const float (&uc)[4], float vc, float rfx, float rfy, float ztc,
+                                        float (&ox)[4], float (&oy)[4], float (&oz)[4], uint32_t &mword)
+{
+    mword = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int c = k + 1;
+        const float w[3][3] = {{P.z[c - 1], P.z[c], P.z[c + 1]},
+                               {C.z[c - 1], C.z[c], C.z[c + 1]},
+                               {N.z[c - 1], N.z[c], N.z[c + 1]}};
+        bool ok;
+        pca_pixel<KIND>(w, uc[k], vc, rfx, rfy, ztc, ox[k], oy[k], oz[k], ok);
+        mword |= ok ? 1u << (8 * k) : 0u;
     }
 }
 
@@ -1183,6 +1348,7 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
         pts.pitch = __ldg(&f->pts_pitch);
         pts.plane = __ldg(&f->pts_plane);
         const float ztc = __ldg(&f->ztc);
+        const float rfx = __frcp_rn(fx), rfy = __frcp_rn(fy);  // (PlanePCA)
         const int lt = t - __ldg(&f->tile_begin);
         const int x0 = (lt % txs) * 128 + 4 * lane, y0 = (lt / txs) * TH;
         const int nvalid = min(4, W - x0);  // pixels of this lane inside the frame (may be <= 0)
@@ -1241,8 +1407,13 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
             float ox[4], oy[4], oz[4];
             uint32_t mw;
             unsigned rb;
-            row_step<KIND, GRAD, PHI>(P, C, N, cy, uc, __fsub_rn((float)y, v0), fx, fy, thr, wts, gu, gv, ox, oy, oz,
-                                      mw, rb);
+            if constexpr (GRAD == GRAD_PLANEPCA) {
+                pca_row<KIND, GRAD>(P, C, N, uc, __fsub_rn((float)y, v0), rfx, rfy, ztc, ox, oy, oz, mw);
+                rb = 0;
+            } else {
+                row_step<KIND, GRAD, PHI>(P, C, N, cy, uc, __fsub_rn((float)y, v0), fx, fy, thr, wts, gu, gv, ox, oy,
+                                          oz, mw, rb);
+            }
             if (y < H && nvalid > 0) {
                 store4(out, args.out_fmt, x0, y, nvalid, ox, oy, oz, mw);
                 if (pts.pts)  // the fused point cloud of this row
@@ -1264,7 +1435,7 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
                 failed = true;
                 break;
             }
-            carry_down(C, N, cy);
+            if constexpr (GRAD != GRAD_PLANEPCA) carry_down(C, N, cy);
             P = C;
             C = N;
             // (a rolled loop: unrolling it to rotate the roles of P, C, N costs
@@ -1408,11 +1579,11 @@ __global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __
                 pend_b &= pend_b - 1;
             }
             const int x = x0 + (b & 3), y = y0 + (b >> 2);
-            Vec3 nr;
+            Vec3 nr = {0.f, 0.f, 0.f};
             if constexpr (SEP5)
                 nr = refine_from_input_sep5<KIND, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0, sw.d1, sw.d2, sw.s0,
                                                        sw.s1, sw.s2);
-            else
+            else if constexpr (GRAD != GRAD_PLANEPCA)  // (PlanePCA never flags a pixel)
                 nr = refine_from_input<KIND, GRAD, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0, wts[0], wts[1], wts[2]);
             store1(out, args.out_fmt, x, y, nr);
             ++nref;
@@ -1443,6 +1614,7 @@ KernelFn select_kernel(int grad, int phi, int cfg)
 #define TFN_KC(G, P) TFN_K(G, P, 0) TFN_K(G, P, 1) TFN_K(G, P, 2) TFN_K(G, P, 3)
 #define TFN_KP(G) TFN_KC(G, PHI_MEAN) TFN_KC(G, PHI_MEDIAN)
     TFN_KP(GRAD_FD) TFN_KP(GRAD_SOBEL) TFN_KP(GRAD_SCHARR) TFN_KP(GRAD_PREWITT) TFN_KP(GRAD_WEIGHTED) TFN_KP(GRAD_SEP5)
+    TFN_KC(GRAD_PLANEPCA, PHI_MEAN)  // (PlanePCA has no Phi)
 #undef TFN_KP
 #undef TFN_KC
 #undef TFN_K

@@ -96,8 +96,8 @@ tfn_status tfn_autotune(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_me
         if (ms[k] < ms[b]) b = k;
     for (int i = 0; i < n; ++i) {
         const int kind = frames[i].input_type;
-        c->tuned[kind][m->grad][m->phi][m->output] = (signed char)b;
-        c->tuned_ms[kind][m->grad][m->phi][m->output] = ms[b];
+        c->tuned[kind][method_grad(*m)][method_phi(*m)][m->output] = (signed char)b;
+        c->tuned_ms[kind][method_grad(*m)][method_phi(*m)][m->output] = ms[b];
     }
     c->last_slot = -1;
     if (best) *best = b;
@@ -111,7 +111,7 @@ tfn_status tfn_tuned_shape(tfn_ctx *c, int input_type, const tfn_method *m, int 
     if (!c || !index || input_type < 0 || input_type >= KIND_COUNT) return TFN_ERR_INVALID_ARG;
     tfn_status st = validate_method(m);
     if (st) return st;
-    *index = c->tuned[input_type][m->grad][m->phi][m->output];
+    *index = c->tuned[input_type][method_grad(*m)][method_phi(*m)][m->output];
     return TFN_OK;
 }
 

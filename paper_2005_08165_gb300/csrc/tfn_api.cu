@@ -267,7 +267,7 @@ tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDes
     const int grad = method_grad(m);
     KernelFn fn = kernel_for(kind, grad, method_phi(m), cfg);
     if (!fn) return TFN_ERR_UNSUPPORTED;
-    const int threads = cfg_threads(cfg);
+    const int threads = cfg_threads(cfg, grad);
     const size_t smem = smem_bytes(kind, cfg, grad);
     if (!cuda_ok(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                  "cudaFuncSetAttribute"))
@@ -278,7 +278,7 @@ tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDes
         return TFN_ERR_CUDA;
     if (per_sm < 1) per_sm = 1;
     // one warp per work item at a time: no more CTAs than items / warps per CTA
-    const int nw = kCfgs[cfg].warps;
+    const int nw = cta_warps(cfg, grad);
     const int grid = std::min((total_tiles + nw - 1) / nw, per_sm * num_sms);
     if (grid < 1) return TFN_OK;
     LaunchArgs a;

@@ -82,7 +82,13 @@ constexpr TileCfg kCfgs[kNumCfg] = {
 // the default shape for launches with few items (short items spread one frame over many warps)
 constexpr int kSmallCfg = 3;
 
-inline int cfg_threads(int c) { return 32 * kCfgs[c].warps; }
+// Warps per CTA of the (shape, filter) kernel: the FD kernels (128
+// registers) run 2-warp CTAs, 8 of them per SM, whose finer grain schedules
+// better than 4 x 4 warps; the others keep the shape's CTA.
+constexpr int cta_warps(int c, int grad) { return grad == GRAD_FD ? 2 : kCfgs[c].warps; }
+// CTAs per SM that the FD kernels are compiled for (their register bound).
+constexpr int fd_ctas_per_sm(int c) { return 16 / cta_warps(c, GRAD_FD); }
+inline int cfg_threads(int c, int grad) { return 32 * cta_warps(c, grad); }
 inline int kind_elem_size(int kind) { return (kind == KIND_DEPTH_F32 || kind == KIND_DISP_F32) ? 4 : 2; }
 // Halo columns loaded on each side so that the TMA box starts on a 16-byte boundary.
 inline int kind_padx(int kind) { return 16 / kind_elem_size(kind); }
@@ -96,7 +102,7 @@ constexpr size_t kSep5RingBytes = 5 * 4 * 32 * 16;
 inline bool grad_is_sep5(int grad) { return grad >= GRAD_SEP5 && grad <= GRAD_PREWITT5; }
 inline size_t smem_bytes(int kind, int c, int grad)
 {
-    return (size_t)kCfgs[c].warps * (kCfgs[c].nst * stage_stride(kind, c) + (grad_is_sep5(grad) ? kSep5RingBytes : 0)) +
+    return (size_t)cta_warps(c, grad) * (kCfgs[c].nst * stage_stride(kind, c) + (grad_is_sep5(grad) ? kSep5RingBytes : 0)) +
            128;
 }
 // The profiles (d1 d2 s0 s1 s2) of a 5x5 filter: the named members' fixed

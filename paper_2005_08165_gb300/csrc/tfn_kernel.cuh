@@ -1259,11 +1259,12 @@ __device__ __noinline__ Vec3 refine_from_input_sep5(const void *in, int64_t pitc
 // row read as holes, and so does the TMA zero fill above the first row and
 // beyond the right edge, so borders need no special case.
 template <int KIND, int GRAD, int PHI, int CFG>
-__global__ void __launch_bounds__(32 * kCfgs[CFG].warps) normals_kernel(const __grid_constant__ LaunchArgs args)
+__global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? fd_ctas_per_sm(CFG) : 0)
+    normals_kernel(const __grid_constant__ LaunchArgs args)
 {
     typedef typename KindTraits<KIND>::T T;
     typedef Row<KIND, GRAD> R;
-    constexpr int TH = kCfgs[CFG].th, CR = kCfgs[CFG].cr, NST = kCfgs[CFG].nst, NW = kCfgs[CFG].warps;
+    constexpr int TH = kCfgs[CFG].th, CR = kCfgs[CFG].cr, NST = kCfgs[CFG].nst, NW = cta_warps(CFG, GRAD);
     constexpr bool SEP5 = GRAD == GRAD_SEP5;
     constexpr int HR = SEP5 ? 2 : 1;                  // halo rows above and below an item
     constexpr int NCH = (TH + 2 * HR + CR - 1) / CR;  // chunks per item: rows y0-HR .. y0+TH-1+HR

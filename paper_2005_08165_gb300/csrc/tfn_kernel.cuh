@@ -1070,10 +1070,21 @@ struct PtsDesc {
 // the frame): Z = the sample (disparity: ztc / sample), X = Z (u - u0)/fx,
 // Y = Z (v - v0)/fy with ucf = (u - u0)/fx per column and vcf = (v - v0)/fy;
 // holes give (0, 0, 0).
+// (out of line: the row loop's code stays small; the samples travel by value)
+template <int KIND>
+__device__ __noinline__ void store_points4_cold(PtsDesc p, int u, int v, int n, float z1, float z2, float z3, float z4,
+                                                float uf0, float uf1, float uf2, float uf3, float vcf, float ztc);
 template <int KIND>
 __device__ __forceinline__ void store_points4(const PtsDesc &p, int u, int v, int n, const float (&z)[6],
                                               const float (&ucf)[4], float vcf, float ztc)
 {
+    store_points4_cold<KIND>(p, u, v, n, z[1], z[2], z[3], z[4], ucf[0], ucf[1], ucf[2], ucf[3], vcf, ztc);
+}
+template <int KIND>
+__device__ __noinline__ void store_points4_cold(PtsDesc p, int u, int v, int n, float z1, float z2, float z3, float z4,
+                                                float uf0, float uf1, float uf2, float uf3, float vcf, float ztc)
+{
+    const float z[6] = {0.f, z1, z2, z3, z4, 0.f}, ucf[4] = {uf0, uf1, uf2, uf3};
     float X[4], Y[4], Z[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -1098,10 +1109,15 @@ __device__ __forceinline__ void store_points4(const PtsDesc &p, int u, int v, in
     }
 }
 
-// Stores 4 consecutive pixels (n valid of them, starting at column u).
-__device__ __forceinline__ void store4(const OutDesc &fd, int fmt, int u, int v, int n, const float (&x)[4],
-                                       const float (&y)[4], const float (&zz)[4], uint32_t mw)
+// Stores 4 consecutive pixels (n valid of them, starting at column u) in the
+// rarer cases (octahedral and packed layouts, a row's last pixels): out of
+// line, so that the row loop's code stays small (the row loop is bound by
+// instruction issue and fetch).
+static __device__ __noinline__ void store4_cold(OutDesc fd, int fmt, int u, int v, int n, float x0, float x1, float x2, float x3,
+                                        float y0, float y1, float y2, float y3, float z0, float z1, float z2, float z3,
+                                        uint32_t mw)
 {
+    const float x[4] = {x0, x1, x2, x3}, y[4] = {y0, y1, y2, y3}, zz[4] = {z0, z1, z2, z3};
     char *row = fd.out + (int64_t)v * fd.out_pitch;
     uint8_t *mrow = fd.mask + (int64_t)v * fd.mask_pitch;
     if (n == 4) {
@@ -1149,6 +1165,34 @@ __device__ __forceinline__ void store4(const OutDesc &fd, int fmt, int u, int v,
         }
         mrow[uu] = (uint8_t)(mw >> (8 * k));
     }
+}
+
+// Normals and mask of 4 pixels of row v: FP32 and FP16/BF16 planar full
+// quads inline, everything else through store4_cold.
+__device__ __forceinline__ void store4(const OutDesc &fd, int fmt, int u, int v, int n, const float (&x)[4],
+                                       const float (&y)[4], const float (&zz)[4], uint32_t mw)
+{
+    if (n == 4 && fmt == OUT_F32) {
+        char *row = fd.out + (int64_t)v * fd.out_pitch;
+        uint8_t *mrow = fd.mask + (int64_t)v * fd.mask_pitch;
+        __stcs(reinterpret_cast<float4 *>(row + (int64_t)u * 4), make_float4(x[0], x[1], x[2], x[3]));
+        __stcs(reinterpret_cast<float4 *>(row + fd.out_plane + (int64_t)u * 4), make_float4(y[0], y[1], y[2], y[3]));
+        __stcs(reinterpret_cast<float4 *>(row + 2 * fd.out_plane + (int64_t)u * 4), make_float4(zz[0], zz[1], zz[2], zz[3]));
+        __stcs(reinterpret_cast<unsigned int *>(mrow + u), mw);
+        return;
+    }
+    if (n == 4 && (fmt == OUT_F16 || fmt == OUT_BF16)) {
+        char *row = fd.out + (int64_t)v * fd.out_pitch;
+        uint8_t *mrow = fd.mask + (int64_t)v * fd.mask_pitch;
+        __stcs(reinterpret_cast<uint2 *>(row + (int64_t)u * 2), make_uint2(pack2(x[0], x[1], fmt), pack2(x[2], x[3], fmt)));
+        __stcs(reinterpret_cast<uint2 *>(row + fd.out_plane + (int64_t)u * 2),
+               make_uint2(pack2(y[0], y[1], fmt), pack2(y[2], y[3], fmt)));
+        __stcs(reinterpret_cast<uint2 *>(row + 2 * fd.out_plane + (int64_t)u * 2),
+               make_uint2(pack2(zz[0], zz[1], fmt), pack2(zz[2], zz[3], fmt)));
+        __stcs(reinterpret_cast<unsigned int *>(mrow + u), mw);
+        return;
+    }
+    store4_cold(fd, fmt, u, v, n, x[0], x[1], x[2], x[3], y[0], y[1], y[2], y[3], zz[0], zz[1], zz[2], zz[3], mw);
 }
 
 

@@ -27,6 +27,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -370,6 +372,7 @@ def run_ours(args):
                 key = "planepca_f32" if grad == "planepca" else f"{grad}_{phi}_f32"
                 variants[key] = {"frames_per_s": round(nf / (lm * 1e-3), 1),
                                  "hbm_gbs": round(BYTES_PER_PX["f32_in_f32_out"] * px / (lm * 1e-3) / 1e9, 1)}
+        accuracy = None if args.no_variants else run_accuracy(torch, tfn, ctx, dev)
         serving = None
         if not args.no_serving:
             serving = run_serving(torch, tfn, ctx, dev, d, args.serve_requests)
@@ -392,7 +395,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "gpu_launches": args.steps,
             "device_status": status,
-            "variants": variants,
+            "variants": variants, "accuracy_vs_truth": accuracy,
             "serving": serving,
         }
         if not args.no_cpu_baseline:
@@ -407,6 +410,45 @@ def run_ours(args):
     if result is not None:
         print(json.dumps(result), flush=True)
     return 0
+
+
+def ea_ep(n, n_gt, sel, phis=(10.0, 20.0, 30.0)):
+    """Sec. IV-A, Eq. (ea_ep): the average angular error e_A (degrees) and the proportions of good pixels
+    e_P(phi) (psi <= phi) of estimated normals n against ground truth n_gt, both (3, ...), over the pixels
+    `sel`.  psi is the angle between the two, taken as atan2(|n x n_gt|, n . n_gt)."""
+    a = np.asarray(n, np.float64)[:, sel]
+    b = np.asarray(n_gt, np.float64)[:, sel]
+    cr = np.cross(a, b, axis=0)
+    psi = np.degrees(np.arctan2(np.sqrt((cr * cr).sum(0)), (a * b).sum(0)))
+    out = {"m": int(psi.size), "e_A_deg": round(float(psi.mean()), 4) if psi.size else None}
+    for phi in phis:
+        out[f"e_P_{int(phi)}"] = round(float((psi <= phi).mean()), 4) if psi.size else None
+    return out
+
+
+def run_accuracy(torch, tfn, ctx, dev, n_frames=8):
+    """e_A / e_P of the GPU estimators against the scenes' analytic normals on clean and noisy 480x640
+    frames (the kind of comparison the paper's tables make, on synthetic scenes).  The pixels are those
+    every listed estimator evaluates and that lie on a surface."""
+    import scenes
+    methods = [("fd", "mean"), ("fd", "median"), ("sobel", "mean"), ("scharr", "mean"), ("prewitt", "mean"),
+               ("fd5", "mean"), ("sobel5", "mean"), ("planepca", "mean")]
+    out = {}
+    for label, recipe in (("clean", scenes.Recipe()), ("noisy", scenes.Recipe(noise_k=0.0012, hole_frac=0.03))):
+        frames = [scenes.render(5000 + k, recipe, with_truth=True) for k in range(n_frames)]
+        d = torch.stack([torch.from_numpy(f[0]) for f in frames]).to(dev)
+        ins = [d[k] for k in range(n_frames)]
+        res = {}
+        for grad, phi in methods:
+            nrm, msk = ctx.normals_batch(ins, scenes.CAMERA, grad=grad, phi=phi)
+            torch.cuda.synchronize()
+            res[(grad, phi)] = (torch.stack(nrm).cpu().numpy(), torch.stack(msk).cpu().numpy())
+        on_surface = np.stack([f[2] >= 0 for f in frames])
+        sel = on_surface & np.all(np.stack([m == 1 for _, m in res.values()]), axis=0)
+        gt = np.stack([f[3] for f in frames], axis=1)  # (3, N, H, W)
+        out[label] = {f"{g}_{p}" if g != "planepca" else g: ea_ep(np.moveaxis(n, 1, 0), gt, sel)
+                      for (g, p), (n, _) in res.items()}
+    return out
 
 
 def run_forms(torch, tfn, ctx, stream, dev, steps):

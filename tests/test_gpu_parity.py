@@ -269,6 +269,18 @@ def test_tiny_images(torch, tfn, ctx, shape):
             compare(n[0], m[0], img, cam, grad=grad, phi=phi)
 
 
+@pytest.mark.parametrize("shape", [(3, 32768), (32768, 5)])
+def test_maximum_extent_frames(torch, tfn, ctx, shape):
+    # the largest width and height the ABI accepts (32768), on thin frames the oracle finishes quickly
+    rng = np.random.default_rng(4)
+    img = (3.0 + 0.002 * rng.standard_normal(shape)).astype(np.float32)
+    img.ravel()[rng.integers(0, img.size, 50)] = 0.0
+    cam = dict(fx=500.0, fy=480.0, u0=(shape[1] - 1) / 2, v0=(shape[0] - 1) / 2)
+    for grad, phi in (("fd", "mean"), ("sobel", "median")):
+        n, m = run_batch(torch, tfn, ctx, [(img, cam)], grad=grad, phi=phi)
+        compare(n[0], m[0], img, cam, grad=grad, phi=phi)
+
+
 def test_special_values_all_holes_constant(torch, tfn, ctx):
     H, W = 23, 37
     img = np.full((H, W), 2.5, np.float32)

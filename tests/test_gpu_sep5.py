@@ -146,3 +146,40 @@ def test_sep5_weights_are_validated(torch, tfn, ctx):
         with pytest.raises(tfn.TfnError) as e:
             ctx.normals(d, cam, grad="sep5", weights=w)
         assert e.value.status == tfn.TFN_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (2, 3), (4, 4), (5, 5), (6, 9), (9, 1)])
+def test_5x5_and_planepca_tiny_images(torch, tfn, ctx, shape):
+    from tests.test_gpu_planepca import compare_pca
+    rng = np.random.default_rng(2)
+    img = rng.uniform(1, 2, size=shape).astype(np.float32)
+    cam = dict(fx=3.0, fy=3.0, u0=(shape[1] - 1) / 2, v0=(shape[0] - 1) / 2)
+    d = to_dev(torch, tfn, img)
+    for grad in ("fd5", "sobel5"):
+        for phi in ("mean", "median"):
+            n, m = ctx.normals(d, cam, grad=grad, phi=phi)
+            torch.cuda.synchronize()
+            compare(n.cpu().numpy(), m.cpu().numpy(), img, cam, grad=grad, phi=phi)
+    n, m = ctx.normals(d, cam, grad="planepca")
+    torch.cuda.synchronize()
+    compare_pca(n.cpu().numpy(), m.cpu().numpy(), img, cam)
+
+
+def test_special_values_5x5_and_planepca(torch, tfn, ctx):
+    from tests.test_gpu_planepca import compare_pca
+    H, W = 23, 37
+    img = np.full((H, W), 2.5, np.float32)
+    img += np.linspace(0, 0.3, W, dtype=np.float32)[None, :]
+    img[3, 4:11] = [np.nan, np.inf, -np.inf, -1.0, 0.0, 2.0 ** -17, 2.0 ** 17]
+    img[10, 10] = 2.0 ** -16
+    img[12, 12] = 2.0 ** 16
+    cam = dict(fx=20.0, fy=21.0, u0=18.0, v0=11.0)
+    d = to_dev(torch, tfn, img)
+    for grad in ("fd5", "sobel5", "prewitt5"):
+        for phi in ("mean", "median"):
+            n, m = ctx.normals(d, cam, grad=grad, phi=phi)
+            torch.cuda.synchronize()
+            compare(n.cpu().numpy(), m.cpu().numpy(), img, cam, grad=grad, phi=phi)
+    n, m = ctx.normals(d, cam, grad="planepca")
+    torch.cuda.synchronize()
+    compare_pca(n.cpu().numpy(), m.cpu().numpy(), img, cam)

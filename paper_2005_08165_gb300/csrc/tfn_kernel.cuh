@@ -881,7 +881,7 @@ __device__ __forceinline__ void pca_pixel(const float (&w)[3][3], float uc, floa
     for (int it = 0; it < kPcaNewton; ++it) {
         const float p = __fmaf_rn(-l, __fmaf_rn(-l, __fsub_rn(1.f, l), c1), c0);  // c0 - l (c1 - l (1 - l))
         const float dp = __fmaf_rn(l, __fmaf_rn(-3.f, l, 2.f), -c1);               // -c1 + l (2 - 3 l)
-        l = dp < 0.f ? __fsub_rn(l, __fdiv_rn(p, dp)) : l;
+        l = dp < 0.f ? __fmaf_rn(-p, rcp_approx(dp), l) : l;  // (the step need not be exact: the Rayleigh step below fixes l)
     }
     // The eigenvector: the largest cross product of two rows of A = M - l I.
     // The cubic locates l only to about u / p'(l), coarse where the two

@@ -230,9 +230,9 @@ tfn_status tfn_tile_shape_info(int index, int *tile_w, int *tile_h, int *rows_pe
 
 /* Forces the tile shape used by later calls of this context; index -1 (the
  * default) uses the context's tune table (see tfn_autotune), and for
- * combinations the table does not hold, shape 0, or a shape of short work
- * items when a launch has too few items to occupy the GPU (one or a few
- * small frames).  Results do not depend on the shape; speed does.  Plans and
+ * combinations the table does not hold, shape 1 (the tallest items), or a
+ * shape of short work items when a launch has too few items to occupy the
+ * GPU (one or a few small frames).  Results do not depend on the shape; speed does.  Plans and
  * batches built before the call keep their shape. */
 tfn_status tfn_set_tile_shape(tfn_ctx *ctx, int index);
 

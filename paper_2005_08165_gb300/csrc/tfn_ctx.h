@@ -43,7 +43,8 @@ struct tfn_ctx {
     tfn::Slot slots[tfn::kSlots];
     int next_slot = 0, last_slot = -1;
     // tile shape: forced >= 0 (tfn_set_tile_shape), else the tune table's
-    // entry for (input kind, gradient, phi, output), else shape 0
+    // entry for (input kind, gradient, phi, output), else kDefaultCfg (or
+    // kSmallCfg for a small launch)
     int forced_cfg = -1;
     signed char tuned[tfn::KIND_COUNT][tfn::GRAD_COUNT][tfn::PHI_COUNT][tfn::kOutCount];
     float tuned_ms[tfn::KIND_COUNT][tfn::GRAD_COUNT][tfn::PHI_COUNT][tfn::kOutCount];
@@ -90,8 +91,8 @@ struct DeviceGuard {  // switches to the context's device for the call's duratio
 tfn_status ctx_alloc(tfn_ctx *c, void **p, size_t bytes);
 void ctx_free(tfn_ctx *c, void *&p, size_t bytes);
 
-// True when a launch over frames[0..n) has fewer than two work items per
-// resident warp with the default shape (one or a few small frames).
+// True when a launch over frames[0..n) would have fewer than two 18-row work
+// items (shape 0) per resident warp (one or a few small frames).
 inline bool small_launch(const tfn_frame *frames, int n, int num_sms)
 {
     long long items = 0;
@@ -101,13 +102,13 @@ inline bool small_launch(const tfn_frame *frames, int n, int num_sms)
 
 // Tile shape for a launch over frames[0..n) (one input kind) with method m:
 // forced (tfn_set_tile_shape), else the tune table's, else the short-item
-// shape for a small launch, else shape 0.
+// shape for a small launch, else kDefaultCfg.
 inline int choose_cfg(const tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method &m)
 {
     if (c->forced_cfg >= 0) return c->forced_cfg;
     const int t = c->tuned[frames[0].input_type][method_grad(m)][method_phi(m)][m.output];
     if (t >= 0) return t;
-    return small_launch(frames, n, c->num_sms) ? kSmallCfg : 0;
+    return small_launch(frames, n, c->num_sms) ? kSmallCfg : kDefaultCfg;
 }
 
 // Enqueues the estimator over frames[0..n) (device pointers, already

@@ -81,6 +81,9 @@ constexpr TileCfg kCfgs[kNumCfg] = {
     {128, 18, 18, 5, 3, 4}, {128, 30, 30, 8, 3, 4}, {128, 12, 12, 7, 3, 4}, {128, 6, 6, 4, 2, 4}};
 // the default shape for launches with few items (short items spread one frame over many warps)
 constexpr int kSmallCfg = 3;
+// the default shape otherwise: the tallest items (the least halo per row) measured fastest for every
+// filter on 256 x 480x640 frames (FD mean 0.9%, Sobel 4.5%, the 5x5 filters 13% faster than 18 rows)
+constexpr int kDefaultCfg = 1;
 
 // Warps per CTA of the (shape, filter) kernel: the FD kernels (128
 // registers) run 2-warp CTAs, 8 of them per SM, whose finer grain schedules

@@ -89,7 +89,7 @@ extern "C" tfn_status tfn_normals_noalloc(const tfn_frame *frames, int n, const 
     for (int i = 0; i < n;) {
         int j = i + 1;
         while (j < n && frames[j].input_type == frames[i].input_type) ++j;
-        const int cfg = small_launch(frames + i, j - i, sms) ? kSmallCfg : 0;
+        const int cfg = small_launch(frames + i, j - i, sms) ? kSmallCfg : kDefaultCfg;
         for (int k = i; k < j; ++k) run_cfg[k] = cfg;
         i = j;
     }

@@ -883,24 +883,10 @@ __device__ __forceinline__ void pca_pixel(const float (&w)[3][3], float uc, floa
         const float dp = __fmaf_rn(l, __fmaf_rn(-3.f, l, 2.f), -c1);               // -c1 + l (2 - 3 l)
         l = dp < 0.f ? __fmaf_rn(-p, rcp_approx(dp), l) : l;  // (the step need not be exact: the Rayleigh step below fixes l)
     }
-    // The eigenvector: the largest cross product of two rows of A = M - l I.
-    // The cubic locates l only to about u / p'(l), coarse where the two
-    // smallest eigenvalues crowd together, so l is then replaced once by the
-    // Rayleigh quotient of that vector (accurate to the square of its error)
-    // and the cross products are taken again.
-    float bx = 0.f, by = 0.f, bz = 1.f;
-#pragma unroll
-    for (int pass = 0; pass < 2; ++pass) {
-        if (pass == 1) {
-            // l = b^T M b / b^T b
-            const float mbx = __fmaf_rn(m00, bx, __fmaf_rn(m01, by, __fmul_rn(m02, bz)));
-            const float mby = __fmaf_rn(m01, bx, __fmaf_rn(m11, by, __fmul_rn(m12, bz)));
-            const float mbz = __fmaf_rn(m02, bx, __fmaf_rn(m12, by, __fmul_rn(m22, bz)));
-            const float num = __fmaf_rn(bx, mbx, __fmaf_rn(by, mby, __fmul_rn(bz, mbz)));
-            const float den = __fmaf_rn(bx, bx, __fmaf_rn(by, by, __fmul_rn(bz, bz)));
-            l = den > 0.f ? __fdiv_rn(num, den) : l;
-        }
-        const float a00 = __fsub_rn(m00, l), a11 = __fsub_rn(m11, l), a22 = __fsub_rn(m22, l);
+    // The eigenvector of an eigenvalue l: the largest cross product of two
+    // rows of A = M - l I, normalised.
+    auto vec_for = [&](float lv, float &x, float &y, float &z) {
+        const float a00 = __fsub_rn(m00, lv), a11 = __fsub_rn(m11, lv), a22 = __fsub_rn(m22, lv);
         float v[3][3];
         // a0 x a1, a0 x a2, a1 x a2 with a0 = (a00, m01, m02), a1 = (m01, a11, m12), a2 = (m02, m12, a22)
         v[0][0] = __fmaf_rn(m01, m12, -__fmul_rn(m02, a11));
@@ -913,20 +899,45 @@ __device__ __forceinline__ void pca_pixel(const float (&w)[3][3], float uc, floa
         v[2][1] = __fmaf_rn(m12, m02, -__fmul_rn(m01, a22));
         v[2][2] = __fmaf_rn(m01, m12, -__fmul_rn(a11, m02));
         float best = -1.f;
+        x = 0.f, y = 0.f, z = 1.f;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
             const float n2 = __fmaf_rn(v[q][0], v[q][0], __fmaf_rn(v[q][1], v[q][1], __fmul_rn(v[q][2], v[q][2])));
             const bool take = n2 > best;
             best = take ? n2 : best;
-            bx = take ? v[q][0] : bx;
-            by = take ? v[q][1] : by;
-            bz = take ? v[q][2] : bz;
+            x = take ? v[q][0] : x;
+            y = take ? v[q][1] : y;
+            z = take ? v[q][2] : z;
         }
         const float rs = ok && best > 0.f ? rsqrt_approx(best) : 0.f;
-        bx = __fmul_rn(bx, rs);
-        by = __fmul_rn(by, rs);
-        bz = __fmul_rn(bz, rs);
-    }
+        x = __fmul_rn(x, rs);
+        y = __fmul_rn(y, rs);
+        z = __fmul_rn(z, rs);
+    };
+    // its Rayleigh quotient b^T M b / b^T b, never below the smallest eigenvalue
+    auto rayleigh = [&](float x, float y, float z) -> float {
+        const float mbx = __fmaf_rn(m00, x, __fmaf_rn(m01, y, __fmul_rn(m02, z)));
+        const float mby = __fmaf_rn(m01, x, __fmaf_rn(m11, y, __fmul_rn(m12, z)));
+        const float mbz = __fmaf_rn(m02, x, __fmaf_rn(m12, y, __fmul_rn(m22, z)));
+        const float num = __fmaf_rn(x, mbx, __fmaf_rn(y, mby, __fmul_rn(z, mbz)));
+        const float den = __fmaf_rn(x, x, __fmaf_rn(y, y, __fmul_rn(z, z)));
+        return den > 0.f ? __fdiv_rn(num, den) : 0.f;
+    };
+    // Two candidates: the vector of the Newton eigenvalue, and that of l = 0
+    // (the adjugate's largest column).  det(M) carries an absolute error of
+    // about u tr^3, which can throw the cubic's root past lambda_2 when
+    // lambda_2 / tr is below about u^(1/2) (a window across a steep slope);
+    // l = 0 is then the better start.  The candidate nearer the smallest
+    // eigenvector has the smaller Rayleigh quotient.  Two steps of l = the
+    // Rayleigh quotient, then the cross products again, refine it.
+    float xn, yn, zn, x0, y0, z0;
+    vec_for(l, xn, yn, zn);
+    vec_for(0.f, x0, y0, z0);
+    const float qn = rayleigh(xn, yn, zn), q0 = rayleigh(x0, y0, z0);
+    const bool newton = qn <= q0;
+    float bx = newton ? xn : x0, by = newton ? yn : y0, bz = newton ? zn : z0;
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) vec_for(rayleigh(bx, by, bz), bx, by, bz);
     // face the camera: n . (uc / fx, vc / fy, 1) < 0; ties by n_z, n_y, n_x < 0
     const float d = __fmaf_rn(bx, __fmul_rn(uc, rfx), __fmaf_rn(by, __fmul_rn(vc, rfy), bz));
     const float key = d != 0.f ? d : bz != 0.f ? bz : by != 0.f ? by : bx;

@@ -102,6 +102,21 @@ def test_planepca_clean_scenes_are_tight(torch, tfn, ctx):
         assert st["tight"] > 0.75 * st["pixels"] and st["max_tight_deg"] < 2e-4, st
 
 
+def test_planepca_steep_planes(torch, tfn, ctx):
+    # planes seen at grazing angles: the scatter matrix is strongly anisotropic (lambda_2 / tr down to
+    # about 1e-4), where the characteristic cubic alone can land on the wrong eigenvalue
+    from tests.geometry import plane_depth, tilted_normal
+    cam = dict(fx=481.2, fy=481.2, u0=63.5, v0=47.5)
+    for tilt, az in ((80, 30), (86, 200), (88.5, 120)):
+        nrm = tilted_normal(tilt, az)
+        Z = plane_depth(96, 128, cam, nrm, [0.0, 0.0, 2.0]).astype(np.float32)
+        Z = np.where((Z > 0.05) & (Z < 50), Z, 0).astype(np.float32)
+        n, m = ctx.normals(to_dev(torch, tfn, Z), cam, grad="planepca")
+        torch.cuda.synchronize()
+        st = compare_pca(n.cpu().numpy(), m.cpu().numpy(), Z, cam)
+        assert st["pixels"] > 1000
+
+
 @pytest.mark.parametrize("kind", ["f16", "u16", "dispf32"])
 def test_planepca_other_inputs(torch, tfn, ctx, kind):
     if kind == "f16":

@@ -183,3 +183,53 @@ def test_special_values_5x5_and_planepca(torch, tfn, ctx):
     n, m = ctx.normals(d, cam, grad="planepca")
     torch.cuda.synchronize()
     compare_pca(n.cpu().numpy(), m.cpu().numpy(), img, cam)
+
+
+@pytest.mark.parametrize("grad", ["sobel5", "planepca"])
+def test_full_batch_256_sampled(torch, tfn, ctx, grad):
+    # the bench's variant launch: 256 noisy 480x640 frames in one plan; three frames are compared with
+    # the oracle pixel by pixel, all frames for properties that hold at any size
+    import scenes
+    from tests.test_gpu_planepca import compare_pca
+    depth = scenes.noisy_batch(256)
+    d = tfn.empty_image(depth.shape, torch.float32)
+    d.copy_(torch.from_numpy(depth))
+    normals = tfn.empty_normals(480, 640, lead=(256,))
+    masks = tfn.empty_image((256, 480, 640), torch.uint8)
+    plan = ctx.plan([d[k] for k in range(256)], scenes.CAMERA, grad=grad, phi="mean",
+                    normals=[normals[k] for k in range(256)], masks=[masks[k] for k in range(256)])
+    plan.launch()
+    torch.cuda.synchronize()
+    plan.close()
+    for k in (3, 50, 200):
+        if grad == "planepca":
+            compare_pca(normals[k].cpu().numpy(), masks[k].cpu().numpy(), depth[k], scenes.CAMERA)
+        else:
+            compare(normals[k].cpu().numpy(), masks[k].cpu().numpy(), depth[k], scenes.CAMERA, grad=grad, phi="mean")
+    v = masks.bool()
+    nn = (normals.float() ** 2).sum(1)
+    assert torch.isfinite(normals).all()
+    assert ((nn - 1).abs()[v] < 1e-5).all() and (nn[~v] == 0).all()
+    halo = 2 if grad == "sobel5" else 1  # the filters' border of non-evaluable pixels
+    border = torch.zeros((480, 640), dtype=torch.bool, device=v.device)
+    border[:halo, :] = border[-halo:, :] = True
+    border[:, :halo] = border[:, -halo:] = True
+    assert not v[:, border].any()
+
+
+@pytest.mark.parametrize("grad", ["fd5", "planepca"])
+def test_server_runs_the_new_estimators(torch, tfn, ctx, grad):
+    # device requests through a server give the bits of a direct call
+    frames = depth_frames([(96, 128), (61, 99), (96, 128)], 3100)
+    with tfn.Server(ctx, grad=grad) as srv:
+        outs = []
+        for img, cam in frames:
+            d = to_dev(torch, tfn, img)
+            n = tfn.empty_normals(img.shape[0], img.shape[1])
+            m = tfn.empty_image(img.shape, torch.uint8)
+            outs.append((srv.submit(d, cam, n, m), d, cam, n, m))
+        for t, d, cam, n, m in outs:
+            assert srv.wait(t, 20000) == tfn.TFN_OK
+            rn, rm = ctx.normals(d, cam, grad=grad)
+            torch.cuda.synchronize()
+            assert torch.equal(n, rn) and torch.equal(m, rm)

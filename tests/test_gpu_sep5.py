@@ -185,8 +185,8 @@ def test_special_values_5x5_and_planepca(torch, tfn, ctx):
     compare_pca(n.cpu().numpy(), m.cpu().numpy(), img, cam)
 
 
-@pytest.mark.parametrize("grad", ["sobel5", "planepca"])
-def test_full_batch_256_sampled(torch, tfn, ctx, grad):
+@pytest.mark.parametrize("grad,phi", [("sobel5", "mean"), ("fd5", "median"), ("planepca", "mean")])
+def test_full_batch_256_sampled(torch, tfn, ctx, grad, phi):
     # the bench's variant launch: 256 noisy 480x640 frames in one plan; three frames are compared with
     # the oracle pixel by pixel, all frames for properties that hold at any size
     import scenes
@@ -196,7 +196,7 @@ def test_full_batch_256_sampled(torch, tfn, ctx, grad):
     d.copy_(torch.from_numpy(depth))
     normals = tfn.empty_normals(480, 640, lead=(256,))
     masks = tfn.empty_image((256, 480, 640), torch.uint8)
-    plan = ctx.plan([d[k] for k in range(256)], scenes.CAMERA, grad=grad, phi="mean",
+    plan = ctx.plan([d[k] for k in range(256)], scenes.CAMERA, grad=grad, phi=phi,
                     normals=[normals[k] for k in range(256)], masks=[masks[k] for k in range(256)])
     plan.launch()
     torch.cuda.synchronize()
@@ -205,12 +205,12 @@ def test_full_batch_256_sampled(torch, tfn, ctx, grad):
         if grad == "planepca":
             compare_pca(normals[k].cpu().numpy(), masks[k].cpu().numpy(), depth[k], scenes.CAMERA)
         else:
-            compare(normals[k].cpu().numpy(), masks[k].cpu().numpy(), depth[k], scenes.CAMERA, grad=grad, phi="mean")
+            compare(normals[k].cpu().numpy(), masks[k].cpu().numpy(), depth[k], scenes.CAMERA, grad=grad, phi=phi)
     v = masks.bool()
     nn = (normals.float() ** 2).sum(1)
     assert torch.isfinite(normals).all()
     assert ((nn - 1).abs()[v] < 1e-5).all() and (nn[~v] == 0).all()
-    halo = 2 if grad == "sobel5" else 1  # the filters' border of non-evaluable pixels
+    halo = 1 if grad == "planepca" else 2  # the estimator's border of non-evaluable pixels
     border = torch.zeros((480, 640), dtype=torch.bool, device=v.device)
     border[:halo, :] = border[-halo:, :] = True
     border[:, :halo] = border[:, -halo:] = True

@@ -152,12 +152,16 @@ static void pixel(const job_t *J, int u, int v)
 {
     const int64_t HW = (int64_t)J->H * J->W, idx = (int64_t)v * J->W + u;
     const int disparity = (J->type == OR_DISP_U16 || J->type == OR_DISP_F32);
-    double s[5][5]; /* samples, s[dv+2][du+2] */
+    /* the window: 3x3 for the 3x3 filters, 5x5 for the 5x5 ones (R15) */
+    double rho[5], delta[3], norm;
+    filter_profile(J->grad, J->cw, rho, delta, &norm);
+    const int reach = (rho[0] != 0 || rho[4] != 0 || delta[2] != 0) ? 2 : 1;
+    double s[5][5]; /* samples, s[dv+2][du+2]; 0 outside the window */
     int ok[5][5];
     for (int dv = -2; dv <= 2; ++dv)
         for (int du = -2; du <= 2; ++du) {
             int x = u + du, y = v + dv;
-            int inside = x >= 0 && x < J->W && y >= 0 && y < J->H;
+            int inside = abs(du) <= reach && abs(dv) <= reach && x >= 0 && x < J->W && y >= 0 && y < J->H;
             double val = inside ? read_sample(J->in, J->pitch, J->type, J->disp_scale, x, y) : 0.0;
             s[dv + 2][du + 2] = val;
             /* R1: fixed-point disparity is a hole only where the raw value is 0 */
@@ -170,8 +174,6 @@ static void pixel(const job_t *J, int u, int v)
         for (int c = 0; c < 3; ++c) J->nprime[c * HW + idx] = 0.0;
 
     /* Reading R2: evaluable pixels. */
-    double rho[5], delta[3], norm;
-    filter_profile(J->grad, J->cw, rho, delta, &norm);
     int evaluable = ok[2][2];
     for (int a = 0; a < 5; ++a)
         for (int b = 0; b < 5; ++b) {

@@ -567,6 +567,12 @@ def run_serving(torch, tfn, ctx, dev, depth_dev, n_req):
     d16.copy_(depth_dev)
     o16 = tfn.empty_normals(H, W, "f16", dev, lead=(nf,))
     frames16 = [[tfn.make_frame(d16[k], o16[k], msk[k], scenes.CAMERA, output="f16")] for k in range(nf)]
+    # autotuned tiles: the server inherits the context's tune table; tune on a batch of the size the
+    # server forms (the table is keyed by input kind, filter, Phi and output, not by batch size)
+    tuned = {}
+    b16, ms16 = ctx.autotune([d16[k] for k in range(16)], scenes.CAMERA, output="f16",
+                             normals=[o16[k] for k in range(16)], masks=[msk[k] for k in range(16)], reps=20)
+    tuned["fp16_in_f16_out_16_frames"] = {"shape": b16, "ms_per_shape": [round(x, 4) for x in ms16]}
     with tfn.Server(ctx, grad="fd", phi="mean", output="f16") as srv:
         serve_stream(tfn, srv, frames16, list(range(nf)), 0)  # warm-up
         order = [k % nf for k in range(8 * nf)]
@@ -582,6 +588,7 @@ def run_serving(torch, tfn, ctx, dev, depth_dev, n_req):
     # 2 output slots each
     rng = np.random.default_rng(10 ** 6)
     pool = []
+    pool_cams = []
     for si, (Hh, Ww) in enumerate(SERVE_SIZES):
         for k in range(4):
             f = 481.2 * Ww / 640 * rng.uniform(0.95, 1.05)
@@ -596,7 +603,21 @@ def run_serving(torch, tfn, ctx, dev, depth_dev, n_req):
                     m_ = torch.empty((Hh, Ww), dtype=torch.uint8, pin_memory=True)
                     slots.append((tfn.make_frame(inp, n_, m_, r.camera), n_, m_))
                 pool.append((inp, slots))
+                pool_cams.append(r.camera)
     frames = [[s[0] for s in slots] for _, slots in pool]
+    # autotune both input kinds on one device copy of each resolution (about the mix's mean batch)
+    for kind, dt in (("f32", torch.float32), ("f16", torch.float16)):
+        imgs = [pool[8 * si + (0 if kind == "f32" else 1)][0] for si in range(len(SERVE_SIZES))]
+        dimgs = []
+        for im in imgs:
+            t = tfn.empty_image(tuple(im.shape), dt, dev)
+            t.copy_(im)
+            dimgs.append(t)
+        cams = [pool_cams[8 * si] for si in range(len(SERVE_SIZES))]
+        best, ms = ctx.autotune(dimgs, cams, output="f32", reps=20)
+        tuned[f"mix_{kind}_in_f32_out"] = {"shape": best, "ms_per_shape": [round(x, 4) for x in ms]}
+        del dimgs
+    out["autotune"] = tuned
     rnd = random.Random(10 ** 6)
     order = [rnd.randrange(len(pool)) for _ in range(n_req)]
     mix = {"workload": f"{n_req} requests; resolution uniform over 240x320, 480x640, 720x1280, 1080x1920; "

@@ -385,6 +385,39 @@ def test_full_batch_256_sampled_against_oracle(torch, tfn, ctx):
     assert not v[:, border].any()
 
 
+def test_disparity_batch_256_sampled_against_oracle(torch, tfn, ctx):
+    # the u16 disparity workload in the bench's launch: 256 frames, 1/16 px, 5% zeros, FD median
+    raw = scenes.disparity_batch(256)
+    st = scenes.STEREO
+    cam = dict(fx=st["f"], fy=st["f"], u0=st["u0"], v0=st["v0"], baseline=st["baseline"])
+    dd = tfn.empty_image(raw.shape, torch.int16)
+    dd.copy_(torch.from_numpy(raw.view(np.int16)))
+    n, m = ctx.normals_batch([dd[k] for k in range(256)], cam, grad="fd", phi="median", disparity=True)
+    torch.cuda.synchronize()
+    for k in (0, 131, 255):
+        compare(n[k].cpu().numpy(), m[k].cpu().numpy(), raw[k], cam, grad="fd", phi="median", disparity=True,
+                baseline=st["baseline"])
+
+
+def test_fp16_batch_1024_sampled_against_oracle(torch, tfn, ctx):
+    # the precision form's launch: 1024 FP16 480x640 frames; FP32 normals held to the 1e-3 deg rule on the
+    # FP16-decoded depth, FP16 normals within 0.05 deg on average per frame
+    import oracle
+    depth16 = scenes.fp16_batch(1024)
+    d16 = tfn.empty_image(depth16.shape, torch.float16)
+    d16.copy_(torch.from_numpy(depth16))
+    ins = [d16[k] for k in range(1024)]
+    n32, m32 = ctx.normals_batch(ins, scenes.CAMERA)
+    n16, m16 = ctx.normals_batch(ins, scenes.CAMERA, output="f16")
+    torch.cuda.synchronize()
+    for k in (5, 1000):
+        compare(n32[k].cpu().numpy(), m32[k].cpu().numpy(), depth16[k], scenes.CAMERA, grad="fd", phi="mean")
+        ref, rm = oracle.normals(depth16[k], **scenes.CAMERA)
+        assert torch.equal(m16[k], m32[k])
+        ang = oracle.angle_deg(n16[k].cpu().numpy().astype(np.float64), ref)[rm == 1]
+        assert ang.mean() < 0.05, ang.mean()
+
+
 def test_plan_graph_replay_matches_batch(torch, tfn, ctx):
     # a frozen batch replayed as a CUDA graph gives the same bits as the direct call
     frames = depth_frames([(67, 131), (480, 640), (33, 64)], 1500)

@@ -332,3 +332,44 @@ def test_rejects_bad_arguments():
         oracle.normals(Z, 0.0, 1.0, 0, 0)
     with pytest.raises(ValueError):
         oracle.normals(Z.astype(np.uint16), 1.0, 2.0, 0, 0, disparity=True)  # fx != fy
+
+
+@pytest.mark.parametrize("phi", PHIS)
+def test_brute_force_back_projection_4x4(phi):
+    # tiny images done the long way: every pixel back-projected through the inverse of the intrinsic
+    # matrix (numpy.linalg.inv, not the oracle's per-axis formula), the FD gradients by scipy's
+    # correlation of 1/Z, each candidate from the back-projected difference vectors, and numpy's mean
+    # or median; the interior normals must match the oracle's
+    from scipy.ndimage import correlate
+    rng = np.random.default_rng(11)
+    for trial in range(20):
+        fx, fy = rng.uniform(3, 9), rng.uniform(3, 9)
+        u0, v0 = rng.uniform(0.5, 2.5), rng.uniform(0.5, 2.5)
+        Z = rng.uniform(1.0, 1.6, size=(4, 4))
+        K = np.array([[fx, 0, u0], [0, fy, v0], [0, 0, 1.0]])
+        Kinv = np.linalg.inv(K)
+        P = np.zeros((4, 4, 3))
+        for v in range(4):
+            for u in range(4):
+                P[v, u] = Z[v, u] * (Kinv @ np.array([u, v, 1.0]))
+        w = 1.0 / Z
+        gu = correlate(w, np.array([[0, 0, 0], [-1, 0, 1], [0, 0, 0]]) / 2.0, mode="constant")
+        gv = correlate(w, np.array([[0, -1, 0], [0, 0, 0], [0, 1, 0]]) / 2.0, mode="constant")
+        n_or, m_or = oracle.normals(Z, fx, fy, u0, v0, phi=phi)
+        for v in (1, 2):
+            for u in (1, 2):
+                nx, ny = fx * gu[v, u], fy * gv[v, u]
+                cands = []
+                for dv in (-1, 0, 1):
+                    for du in (-1, 0, 1):
+                        if (dv, du) == (0, 0):
+                            continue
+                        r = P[v + dv, u + du] - P[v, u]
+                        if r[2] != 0:
+                            cands.append((r[0] * nx + r[1] * ny) / r[2])
+                nz = -(np.mean(cands) if phi == "mean" else np.median(cands))
+                npr = np.array([nx, ny, nz])
+                want = -npr / np.linalg.norm(npr)
+                assert m_or[v, u] == 1
+                ang = oracle.angle_deg(want[:, None], n_or[:, v, u][:, None])[0]
+                assert ang < 1e-8, (trial, v, u, ang)

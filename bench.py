@@ -208,7 +208,10 @@ def job_throughput(local_ms: float, frames_per_rank: int, world: int, device="cp
     return job_ms, world * frames_per_rank / (job_ms * 1e-3)
 
 
-def cpu_baseline(seconds_target=12.0):
+def cpu_baseline(seconds_target=12.0, gpu=None):
+    """The FP64 oracle timed on the host cores on a bounded sample of the workload.  With `gpu`
+    (torch, tfn, ctx, dev) the same leg also states the precision form's angular error: the oracle's
+    normals of FP16-decoded frames against the GPU's FP16 / BF16 / FP32 outputs of those frames."""
     import oracle
     import scenes
     cores = os.cpu_count() or 1
@@ -222,9 +225,30 @@ def cpu_baseline(seconds_target=12.0):
     t0 = time.perf_counter()
     oracle.normals_batch(depth, **scenes.CAMERA, grad="fd", phi="mean", threads=cores)
     dt = time.perf_counter() - t0
-    return {"value": round(n / dt, 3), "unit": "frames/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n} of the 256 noisy 480x640 frames, FD mean, FP64 oracle on {cores} threads "
-                      f"({dt:.1f} s wall)"}
+    out = {"value": round(n / dt, 3), "unit": "frames/s", "cores": cores, "kind": "oracle",
+           "sample": f"{n} of the 256 noisy 480x640 frames, FD mean, FP64 oracle on {cores} threads "
+                     f"({dt:.1f} s wall)"}
+    if gpu is not None:
+        torch, tfn, ctx, dev = gpu
+        seeds = (3000, 3511, 4023)  # frames 0, 511 and 1023 of the 1024-frame FP16 batch
+        f16 = np.stack([scenes.render_batch(s, 1, scenes.Recipe())[0] for s in seeds]).astype(np.float16)
+        d16 = tfn.empty_image(f16.shape, torch.float16, dev)
+        d16.copy_(torch.from_numpy(f16))
+        ref, ref_m = oracle.normals_batch(f16, **scenes.CAMERA, grad="fd", phi="mean", threads=cores)
+        prec = {}
+        for fmt in ("f16", "bf16", "f32"):
+            n_, m_ = ctx.normals_batch([d16[k] for k in range(len(seeds))], scenes.CAMERA, output=fmt)
+            torch.cuda.synchronize()
+            rows = []
+            for k in range(len(seeds)):
+                v = ref_m[k] == 1
+                got = n_[k].float().cpu().numpy().astype(np.float64)
+                ang = oracle.angle_deg(got, ref[k])[v]
+                rows.append({"frame": int(seeds[k] - 3000), "mean_deg": round(float(ang.mean()), 5),
+                             "max_deg": round(float(ang.max()), 5)})
+            prec[f"fp16_in_{fmt}_out"] = rows
+        out["precision_vs_oracle"] = prec
+    return out
 
 
 def time_launches(torch, fn, steps, warmup, stream):
@@ -399,7 +423,7 @@ def run_ours(args):
             "serving": serving,
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(gpu=(torch, tfn, ctx, dev))
         result = line
     if world > 1:
         torch.distributed.barrier()

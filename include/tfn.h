@@ -19,12 +19,14 @@
  * CPU reference used by the tests:
  *   - a sample is a hole unless it is finite and 2^-16 <= value <= 2^16
  *     (TFN_DISP_U16: unless the raw value is non-zero);
- *   - a pixel is evaluable iff it and every tap of both gradient filters are
- *     inside the image and not holes (FD: the 4 axis neighbours; Sobel,
- *     Scharr, Prewitt: all 8); other pixels get normal (0,0,0), mask 0;
+ *   - a pixel is evaluable iff it and every tap with a non-zero weight in
+ *     either gradient filter are inside the image and not holes (FD: the 4
+ *     axis neighbours; Sobel, Scharr, Prewitt: all 8; the 5x5 filters: up to
+ *     2 pixels out); other pixels get normal (0,0,0), mask 0;
  *   - neighbours that are holes or have the centre's depth give no candidate;
  *   - the median of an even count is the mean of the two middle candidates;
- *   - if both gradients are exactly zero the normal is [0, 0, -1];
+ *   - if both gradients are exactly zero, or no neighbour gives a candidate
+ *     (every valid neighbour at the centre's depth), the normal is [0, 0, -1];
  *   - the normal is n = -n'/|n'|, n' = (nx, ny, n_z): it faces the camera.
  *
  * Memory.  Every image pointer in a tfn_frame is a DEVICE pointer owned by

@@ -99,31 +99,52 @@ def recorded_traffic(key: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region.
+
+    The sampler is live (its first reading is in) before the caller's warm-up starts; every reading
+    carries its arrival time, and the summary keeps the readings between `mark_start()` and
+    `mark_end()`, plus the first one after the end (it covers the region's last interval), so a
+    timed region shorter than the 100 ms sampling period still gets one reading taken under load.
+    """
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 100
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []  # (arrival time, line)
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            deadline = time.monotonic() + 10.0
+            while not self.lines and time.monotonic() < deadline and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark_start(self):
+        self.t0 = time.monotonic()
+
+    def mark_end(self):
+        self.t1 = time.monotonic()
+        # wait (bounded) for the reading that closes the region
+        deadline = self.t1 + 5 * self.PERIOD_MS / 1000
+        while self.proc and not any(t > self.t1 for t, _ in self.lines) and time.monotonic() < deadline:
+            time.sleep(0.01)
 
     def __exit__(self, *exc):
         if self.proc:
@@ -133,10 +154,18 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
+    def window(self):
+        """The readings of the timed region (all of them when it was never marked)."""
+        if self.t0 is None or self.t1 is None:
+            return [ln for _, ln in self.lines]
+        inside = [ln for t, ln in self.lines if self.t0 <= t <= self.t1]
+        after = [ln for t, ln in self.lines if t > self.t1][:1]
+        return inside + after
+
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.window():
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -148,10 +177,12 @@ class ClockSampler:
             for nm, val in zip(names, parts[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
+        window_ms = None if self.t0 is None or self.t1 is None else round((self.t1 - self.t0) * 1e3, 1)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0,
+                    "window_ms": window_ms}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "window_ms": window_ms, "period_ms": self.PERIOD_MS}
 
 
 # --------------------------------------------------------------------------------------------
@@ -316,7 +347,9 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+        clk.mark_start()
         total_ms, per = time_launches(torch, step, args.steps, 0, stream)
+        clk.mark_end()
         if world > 1:
             torch.distributed.barrier()
     torch.cuda.synchronize()

@@ -24,3 +24,58 @@ def test_ea_ep_selects_pixels():
     sel = np.array([[False, True], [True, True]])
     r = bench.ea_ep(n, gt, sel)
     assert r["m"] == 3 and r["e_A_deg"] == 0.0 and r["e_P_10"] == 1.0
+
+
+def test_clock_sampler_keeps_the_timed_window(tmp_path, monkeypatch):
+    # a stand-in nvidia-smi that prints one reading per 20 ms: idle clocks first, load clocks later
+    import os
+    import time
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/usr/bin/env python3\n"
+                    "import sys, time\n"
+                    "k = 0\n"
+                    "while True:\n"
+                    "    sm = 345 if k < 10 else 2070\n"
+                    "    cap = 'Active' if k >= 10 else 'Not Active'\n"
+                    "    print(f'0, {sm}, 2070, 300.0, 0x0, Not Active, Not Active, Not Active, {cap}', flush=True)\n"
+                    "    k += 1\n"
+                    "    time.sleep(0.02)\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ['PATH']}")
+    monkeypatch.setattr(bench.ClockSampler, "PERIOD_MS", 20)
+    with bench.ClockSampler(0) as clk:
+        assert clk.lines, "the sampler must be live before the caller's warm-up"
+        time.sleep(0.5)  # past the idle readings
+        clk.mark_start()
+        time.sleep(0.1)
+        clk.mark_end()
+    s = clk.summary()
+    assert s["sm_mhz"] == 2070 and s["sm_max_mhz"] == 2070 and s["reasons"] == ["sw_power_cap"]
+    assert 2 <= s["samples"] <= 12 and s["samples"] < len(clk.lines)
+    assert 90 <= s["window_ms"] <= 400
+
+
+def test_clock_sampler_short_window_gets_the_closing_reading(tmp_path, monkeypatch):
+    import os
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/usr/bin/env python3\n"
+                    "import time\n"
+                    "while True:\n"
+                    "    print('0, 1980, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active', flush=True)\n"
+                    "    time.sleep(0.05)\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ['PATH']}")
+    monkeypatch.setattr(bench.ClockSampler, "PERIOD_MS", 50)
+    with bench.ClockSampler(0) as clk:
+        clk.mark_start()
+        clk.mark_end()  # a region far shorter than the period
+    s = clk.summary()
+    assert s["samples"] == 1 and s["sm_mhz"] == 1980 and s["reasons"] == []
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    with bench.ClockSampler(0) as clk:
+        clk.mark_start()
+        clk.mark_end()
+    assert clk.summary()["reasons"] == ["unsampled"]

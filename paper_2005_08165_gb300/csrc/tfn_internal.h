@@ -102,10 +102,15 @@ inline size_t stage_stride(int kind, int c) { return (stage_bytes(kind, c) + 127
 // GRAD_SEP5 keeps each lane's row derivatives and smoothings of the last 5
 // sample rows in shared memory: 5 rows x 4 float4 per lane.
 constexpr size_t kSep5RingBytes = 5 * 4 * 32 * 16;
-inline bool grad_is_sep5(int grad) { return grad >= GRAD_SEP5 && grad <= GRAD_PREWITT5; }
+constexpr bool grad_is_sep5(int grad) { return grad >= GRAD_SEP5 && grad <= GRAD_PREWITT5; }
+// Stages of a warp's TMA ring.  The 5x5 filters keep 2: with their 10 KB
+// derivative ring a third stage makes shared memory the occupancy limit
+// (2 CTAs = 8 warps per SM instead of the 12 their registers allow), and a
+// chunk of 8 rows takes far longer to compute than one copy takes to land.
+constexpr int cfg_nst(int c, int grad) { return grad_is_sep5(grad) && kCfgs[c].nst > 2 ? 2 : kCfgs[c].nst; }
 inline size_t smem_bytes(int kind, int c, int grad)
 {
-    return (size_t)cta_warps(c, grad) * (kCfgs[c].nst * stage_stride(kind, c) + (grad_is_sep5(grad) ? kSep5RingBytes : 0)) +
+    return (size_t)cta_warps(c, grad) * (cfg_nst(c, grad) * stage_stride(kind, c) + (grad_is_sep5(grad) ? kSep5RingBytes : 0)) +
            128;
 }
 // The profiles (d1 d2 s0 s1 s2) of a 5x5 filter: the named members' fixed

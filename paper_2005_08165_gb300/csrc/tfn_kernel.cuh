@@ -1319,7 +1319,7 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
 {
     typedef typename KindTraits<KIND>::T T;
     typedef Row<KIND, GRAD> R;
-    constexpr int TH = kCfgs[CFG].th, CR = kCfgs[CFG].cr, NST = kCfgs[CFG].nst, NW = cta_warps(CFG, GRAD);
+    constexpr int TH = kCfgs[CFG].th, CR = kCfgs[CFG].cr, NST = cfg_nst(CFG, GRAD), NW = cta_warps(CFG, GRAD);
     constexpr bool SEP5 = GRAD == GRAD_SEP5;
     constexpr int HR = SEP5 ? 2 : 1;                  // halo rows above and below an item
     constexpr int NCH = (TH + 2 * HR + CR - 1) / CR;  // chunks per item: rows y0-HR .. y0+TH-1+HR

@@ -366,15 +366,12 @@ def run_ours(args):
     if rank == 0:
         # end to end through the C ABI with host buffers: pinned in, pinned out,
         # host<->device copies inside the timed region
-        hin_all = torch.from_numpy(depth).pin_memory()  # one pinned batch: frames back to back
-        hin = [hin_all[k] for k in range(nf)]
+        hin = torch.from_numpy(depth).pin_memory()  # one pinned batch: frames back to back
         hout = torch.empty((nf, 3, H, W), dtype=torch.float32).pin_memory()
         hmask = torch.empty((nf, H, W), dtype=torch.uint8).pin_memory()
-        houts = [hout[k] for k in range(nf)]
-        hmks = [hmask[k] for k in range(nf)]
 
         def e2e_step():
-            ctx.normals_batch_host(hin, cam, houts, hmks, grad=args.grad, phi=args.phi, stream=stream)
+            ctx.normals_batch_host(hin, cam, hout, hmask, grad=args.grad, phi=args.phi, stream=stream)
 
         e2e = None
         if not args.no_e2e:

@@ -274,6 +274,45 @@ def make_frame(inp, normals, mask, cam, disparity=False, disp_scale=1.0 / 16, ou
     return f
 
 
+def _stacked(t, ndim: int) -> bool:
+    return t is not None and hasattr(t, "data_ptr") and t.dim() == ndim + 1
+
+
+def make_frames(inputs, normals, masks, cams, disparity=False, disp_scale=1.0 / 16, output="f32", points=None):
+    """The tfn_frame array of a batch, as (keep-alive object, length, pointer to the first frame).
+
+    Lists of per-frame tensors take one make_frame per frame.  Stacks (inputs (N, H, W), normals and
+    masks with the same leading N, points too if given) are described in one pass instead: frame 0's
+    descriptor is replicated into numpy records that have the C struct's layout, and the data
+    pointers advance by each stack's leading stride, which saves the per-frame Python work of a
+    large batch (about 4 us a frame)."""
+    n = len(inputs)
+    single = isinstance(cams, dict)
+    # (every output layout has 3 dimensions per frame: (3, H, W), (H, W, 4) or (H, W, 2))
+    if (n >= 2 and _stacked(inputs, 2) and _stacked(normals, 3) and _stacked(masks, 2)
+            and (points is None or _stacked(points, 3))
+            and normals.shape[0] == n and masks.shape[0] == n and (points is None or points.shape[0] == n)):
+        import numpy as np
+        f0 = make_frame(inputs[0], normals[0], masks[0], cams if single else cams[0], disparity, disp_scale, output,
+                        points[0] if points is not None else None)
+        dt = np.dtype(tfn_frame)
+        arr = np.repeat(np.frombuffer(bytes(f0), dtype=dt), n)
+        k = np.arange(n, dtype=np.uint64)
+        for name, t in (("input", inputs), ("normals", normals), ("mask", masks), ("points", points)):
+            if t is not None:
+                arr[name] += k * np.uint64(t.stride(0) * t.element_size())
+        if not single:
+            for key in ("fx", "fy", "u0", "v0"):
+                arr["cam"][key] = [c[key] for c in cams]
+            arr["cam"]["baseline"] = [c.get("baseline", 1.0) for c in cams]
+        return arr, n, arr.ctypes.data_as(ctypes.POINTER(tfn_frame))
+    if single:
+        cams = [cams] * n
+    frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output,
+                                          points[k] if points is not None else None) for k in range(n)])
+    return frames, n, frames
+
+
 def make_method(grad="fd", phi="mean", output="f32", flags=0, weights=None) -> tfn_method:
     """grad="weighted" takes the row weights (w0, w1, w2) of the gradient filter in `weights`; grad="sep5" takes
     the 5x5 profiles (d1, d2, s0, s1, s2); grad="planepca" selects the PlanePCA estimator (TFN_EST_PLANEPCA,
@@ -342,27 +381,20 @@ class Context:
     def normals_batch(self, inputs, cams, *, grad="fd", phi="mean", output="f32", disparity=False,
                       disp_scale=1.0 / 16, normals=None, masks=None, points=None, stream=None, flags=0, weights=None):
         """Normals of a list of (H_i, W_i) device images (or an (N, H, W) stack) in one launch."""
-        n = len(inputs)
-        if isinstance(cams, dict):
-            cams = [cams] * n
         if normals is None:
             normals = [empty_normals(x.shape[0], x.shape[1], output, x.device) for x in inputs]
         if masks is None:
             masks = [empty_image(tuple(x.shape), _torch().uint8, x.device) for x in inputs]
-        frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output,
-                                              points[k] if points is not None else None) for k in range(n)])
+        keep, n, frames = make_frames(inputs, normals, masks, cams, disparity, disp_scale, output, points)
         m = make_method(grad, phi, output, flags, weights)
         check(tfn_normals_batch(self.handle, frames, n, ctypes.byref(m), _stream_handle(stream)), "tfn_normals_batch")
         return normals, masks
 
     def normals_batch_host(self, inputs, cams, normals, masks, *, grad="fd", phi="mean", output="f32",
                            disparity=False, disp_scale=1.0 / 16, points=None, stream=None, flags=0, weights=None):
-        """Like normals_batch, with every tensor in host memory (pinned is fastest); synchronous."""
-        n = len(inputs)
-        if isinstance(cams, dict):
-            cams = [cams] * n
-        frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output,
-                                              points[k] if points is not None else None) for k in range(n)])
+        """Like normals_batch, with every tensor in host memory (pinned is fastest); synchronous.  The tensors
+        may be lists of per-frame tensors or stacks with a leading frame dimension (see make_frames)."""
+        keep, n, frames = make_frames(inputs, normals, masks, cams, disparity, disp_scale, output, points)
         m = make_method(grad, phi, output, flags, weights)
         check(tfn_normals_batch_host(self.handle, frames, n, ctypes.byref(m), _stream_handle(stream)),
               "tfn_normals_batch_host")
@@ -371,15 +403,11 @@ class Context:
     def plan(self, inputs, cams, *, grad="fd", phi="mean", output="f32", disparity=False, disp_scale=1.0 / 16,
              normals=None, masks=None, points=None, flags=0, weights=None):
         """Freezes a batch into a Plan (descriptors uploaded once, launches captured in a CUDA graph)."""
-        n = len(inputs)
-        if isinstance(cams, dict):
-            cams = [cams] * n
         if normals is None:
             normals = [empty_normals(x.shape[0], x.shape[1], output, x.device) for x in inputs]
         if masks is None:
             masks = [empty_image(tuple(x.shape), _torch().uint8, x.device) for x in inputs]
-        frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output,
-                                              points[k] if points is not None else None) for k in range(n)])
+        keep, n, frames = make_frames(inputs, normals, masks, cams, disparity, disp_scale, output, points)
         m = make_method(grad, phi, output, flags, weights)
         h = ctypes.c_void_p()
         check(tfn_plan_create(self.handle, frames, n, ctypes.byref(m), ctypes.byref(h)), "tfn_plan_create")
@@ -392,15 +420,11 @@ class Context:
     def autotune(self, inputs, cams, *, grad="fd", phi="mean", output="f32", disparity=False, disp_scale=1.0 / 16,
                  normals=None, masks=None, reps=10, stream=None, weights=None):
         """Times every tile shape on this batch; returns (best index, [ms per run of each shape])."""
-        n = len(inputs)
-        if isinstance(cams, dict):
-            cams = [cams] * n
         if normals is None:
             normals = [empty_normals(x.shape[0], x.shape[1], output, x.device) for x in inputs]
         if masks is None:
             masks = [empty_image(tuple(x.shape), _torch().uint8, x.device) for x in inputs]
-        frames = (tfn_frame * n)(*[make_frame(inputs[k], normals[k], masks[k], cams[k], disparity, disp_scale, output)
-                                   for k in range(n)])
+        keep, n, frames = make_frames(inputs, normals, masks, cams, disparity, disp_scale, output)
         m = make_method(grad, phi, output, 0, weights)
         best = ctypes.c_int()
         ms = (ctypes.c_float * tfn_tile_shape_count())()

@@ -598,7 +598,6 @@ tfn_status tfn_normals_batch_host(tfn_ctx *c, const tfn_frame *frames, int n, co
     const int fmt = m->output;
     const bool planar = fmt <= OUT_BF16;
     const int ob = out_elem_bytes(fmt);
-    // chunk size: about 64 MB of input per chunk, at least one frame
     // Device rows use the host's pitch when it suits the kernel (a multiple of
     // 16 bytes), so that host and device layouts match and copies merge.
     auto dev_pitch = [](int64_t host_pitch, size_t row_bytes) -> size_t {
@@ -618,7 +617,11 @@ tfn_status tfn_normals_batch_host(tfn_ctx *c, const tfn_frame *frames, int n, co
         max_mask = std::max(max_mask, mp * f.height);
         if (f.points) max_pts = std::max(max_pts, dev_pitch(f.points_pitch, (size_t)f.width * 4) * f.height * 3);
     }
-    const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, (64u << 20) / std::max<size_t>(max_in, 1)));
+    // Chunks of about 1/16 of the batch's input (8 to 64 MB, at least one frame): the first
+    // chunk's upload and kernel run before any download can start, so smaller chunks start the
+    // downloads (the larger direction) sooner; the three stages keep both directions busy after.
+    const size_t chunk_bytes = std::min<size_t>(64u << 20, std::max<size_t>(8u << 20, max_in * (size_t)n / 16));
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, chunk_bytes / std::max<size_t>(max_in, 1)));
     const int nst = 3;
     for (int k = 0; k < nst; ++k) {
         Stage &s = c->stages[k];

@@ -361,6 +361,30 @@ def test_host_path_contiguous_batch_and_padded_views(torch, tfn, ctx):
         assert np.array_equal(big_m[k, :, :128].numpy(), m_dev[k])
 
 
+def test_host_path_stacks_over_many_chunks(torch, tfn, ctx):
+    # the end-to-end call as the benchmark makes it: pinned stacks with a leading frame dimension, a
+    # batch large enough to run through the three staging streams in several chunks (40 frames of
+    # 480x640: 8 MB chunks of 6 frames, the last one partial), and per-frame intrinsics
+    n = 40
+    depth = scenes.noisy_batch(n, seed0=5000)
+    hin = torch.from_numpy(depth).pin_memory()
+    hn = torch.empty((n, 3, 480, 640), dtype=torch.float32).pin_memory()
+    hm = torch.empty((n, 480, 640), dtype=torch.uint8).pin_memory()
+    cams = [dict(scenes.CAMERA, fx=scenes.CAMERA["fx"] * (1 + 0.01 * k)) for k in range(n)]
+    ctx.normals_batch_host(hin, cams, hn, hm, grad="fd", phi="mean")
+    d = tfn.empty_image(depth.shape, torch.float32)
+    d.copy_(hin)
+    n_dev, m_dev = ctx.normals_batch([d[k] for k in range(n)], cams, grad="fd", phi="mean")
+    torch.cuda.synchronize()
+    for k in range(n):
+        assert torch.equal(hn[k], n_dev[k].cpu()) and torch.equal(hm[k], m_dev[k].cpu()), f"frame {k}"
+    # and the stack call gives the bits of the list-of-views call
+    hn2 = torch.empty_like(hn).pin_memory()
+    hm2 = torch.empty_like(hm).pin_memory()
+    ctx.normals_batch_host([hin[k] for k in range(n)], cams, [hn2[k] for k in range(n)], [hm2[k] for k in range(n)])
+    assert torch.equal(hn, hn2) and torch.equal(hm, hm2)
+
+
 def test_full_batch_256_sampled_against_oracle(torch, tfn, ctx):
     # the benchmark's launch: 256 noisy 480x640 frames in one call; three
     # frames are compared with the oracle pixel by pixel, all frames for

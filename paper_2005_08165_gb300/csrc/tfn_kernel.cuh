@@ -807,7 +807,7 @@ __device__ __forceinline__ void sep5_row(const float (&z)[8], const Sep5W &w, df
 // started at 0 (below it; the iterates rise monotonically to it), and the
 // eigenvector from the largest cross product of two rows of M - lambda I.
 
-constexpr int kPcaNewton = 12;
+constexpr int kPcaNewton = 9;
 
 template <int KIND>
 __device__ __forceinline__ void pca_pixel(const float (&w)[3][3], float uc, float vc, float rfx, float rfy, float ztc,
@@ -921,7 +921,7 @@ __device__ __forceinline__ void pca_pixel(const float (&w)[3][3], float uc, floa
         const float mbz = __fmaf_rn(m02, x, __fmaf_rn(m12, y, __fmul_rn(m22, z)));
         const float num = __fmaf_rn(x, mbx, __fmaf_rn(y, mby, __fmul_rn(z, mbz)));
         const float den = __fmaf_rn(x, x, __fmaf_rn(y, y, __fmul_rn(z, z)));
-        return den > 0.f ? __fdiv_rn(num, den) : 0.f;
+        return den > 0.f ? __fmul_rn(num, rcp_approx(den)) : 0.f;  // (den is 1 to a few u: no exact division)
     };
     // Two candidates: the vector of the Newton eigenvalue, and that of l = 0
     // (the adjugate's largest column).  det(M) carries an absolute error of

@@ -447,7 +447,7 @@ def run_ours(args):
                          "launch_ms": round(launch_ms, 4)},
             "e2e": e2e,
             "clocks": clk.summary(),
-            "gpu_launches": args.steps,
+            "gpu_launches": 2 * args.steps,  # per step: normals_kernel, then refine_kernel
             "device_status": status,
             "variants": variants, "accuracy_vs_truth": accuracy,
             "serving": serving,

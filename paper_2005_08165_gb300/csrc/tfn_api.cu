@@ -22,6 +22,10 @@ KernelFn kernels_depth_f32(int grad, int phi, int cfg);
 KernelFn kernels_depth_f16(int grad, int phi, int cfg);
 KernelFn kernels_disp_u16(int grad, int phi, int cfg);
 KernelFn kernels_disp_f32(int grad, int phi, int cfg);
+KernelFn refiners_depth_f32(int grad, int phi);
+KernelFn refiners_depth_f16(int grad, int phi);
+KernelFn refiners_disp_u16(int grad, int phi);
+KernelFn refiners_disp_f32(int grad, int phi);
 
 KernelFn kernel_for(int kind, int grad, int phi, int cfg)
 {
@@ -31,6 +35,18 @@ KernelFn kernel_for(int kind, int grad, int phi, int cfg)
     case KIND_DEPTH_F16: return kernels_depth_f16(grad, phi, cfg);
     case KIND_DISP_U16: return kernels_disp_u16(grad, phi, cfg);
     case KIND_DISP_F32: return kernels_disp_f32(grad, phi, cfg);
+    }
+    return nullptr;
+}
+
+KernelFn refiner_for(int kind, int grad, int phi)
+{
+    if (grad_is_sep5(grad)) grad = GRAD_SEP5;
+    switch (kind) {
+    case KIND_DEPTH_F32: return refiners_depth_f32(grad, phi);
+    case KIND_DEPTH_F16: return refiners_depth_f16(grad, phi);
+    case KIND_DISP_U16: return refiners_disp_u16(grad, phi);
+    case KIND_DISP_F32: return refiners_disp_f32(grad, phi);
     }
     return nullptr;
 }
@@ -262,7 +278,8 @@ int frame_tiles(const tfn_frame &f, int cfg)
 // Launches the kernel for frames of one input kind whose descriptors and
 // tensor maps are already in device memory.
 tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
-                          uint32_t *d_status, int nframes, int total_tiles, int num_sms, cudaStream_t stream)
+                          uint32_t *d_status, void *d_refine, int nframes, int total_tiles, int num_sms,
+                          cudaStream_t stream)
 {
     const int grad = method_grad(m);
     KernelFn fn = kernel_for(kind, grad, method_phi(m), cfg);
@@ -281,20 +298,32 @@ tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDes
     const int nw = cta_warps(cfg, grad);
     const int grid = std::min((total_tiles + nw - 1) / nw, per_sm * num_sms);
     if (grid < 1) return TFN_OK;
+    // the refinement kernel of this method (none for PlanePCA, which never flags a pixel)
+    KernelFn rf = nullptr;
+    if (grad != GRAD_PLANEPCA && !(rf = refiner_for(kind, grad, method_phi(m)))) return TFN_ERR_UNSUPPORTED;
     LaunchArgs a;
     a.frames = d_frames;
     a.maps = d_maps;
     a.status = d_status;
+    a.rcount = (unsigned long long *)d_refine;
+    a.rlist = (unsigned long long *)((char *)d_refine + 128);
+    a.rcap = kRefineCap;
     a.nframes = nframes;
     a.total_tiles = total_tiles;
     a.out_fmt = m.output;
     a.flags = m.flags;
     for (int k = 0; k < 5; ++k) a.w[k] = m.grad == GRAD_WEIGHTED && k < 3 ? m.weights[k] : 0.f;
     if (grad_is_sep5(m.grad)) sep5_weights(m.grad, m.weights, a.w);
-    a.pad[0] = a.pad[1] = a.pad[2] = 0;
+    a.pad[0] = a.pad[1] = 0;
     void *params[] = {&a};
+    if (rf && !cuda_ok(cudaMemsetAsync(a.rcount, 0, sizeof *a.rcount, stream), "cudaMemsetAsync(refinement count)"))
+        return TFN_ERR_CUDA;
     if (!cuda_ok(cudaLaunchKernel((const void *)fn, dim3(grid), dim3(threads), params, smem, stream),
                  "cudaLaunchKernel"))
+        return TFN_ERR_CUDA;
+    // the flagged pixels: a few per thousand, spread over every SM
+    if (rf && !cuda_ok(cudaLaunchKernel((const void *)rf, dim3(4 * num_sms), dim3(kRefineThreads), params, 0, stream),
+                       "cudaLaunchKernel(refine)"))
         return TFN_ERR_CUDA;
     return TFN_OK;
 }
@@ -328,7 +357,12 @@ void frame_key(std::vector<unsigned char> &k, const tfn_frame &f)
     append_key(k, &f.points_plane_stride, sizeof f.points_plane_stride);
 }
 
-size_t slot_bytes(int cap) { return (size_t)cap * sizeof(FrameDesc) + 128 + (size_t)cap * sizeof(CUtensorMap); }
+// A slot: cap frame descriptors, cap tensor maps (128-byte aligned), then the
+// launch's refinement list (128-byte aligned).
+size_t slot_bytes(int cap)
+{
+    return (size_t)cap * sizeof(FrameDesc) + 128 + (size_t)cap * sizeof(CUtensorMap) + 128 + kRefineListBytes;
+}
 
 tfn_status slot_reserve(tfn_ctx *c, Slot &s, int n)
 {
@@ -357,6 +391,11 @@ CUtensorMap *slot_maps(void *base, int cap)
 {
     uintptr_t p = (uintptr_t)base + (size_t)cap * sizeof(FrameDesc);
     return (CUtensorMap *)((p + 127) & ~(uintptr_t)127);
+}
+void *slot_refine(void *base, int cap)
+{
+    uintptr_t p = (uintptr_t)(slot_maps(base, cap) + cap);
+    return (void *)((p + 127) & ~(uintptr_t)127);
 }
 
 // One launch over frames[0..n) (all of one input kind).
@@ -402,8 +441,8 @@ tfn_status launch_group(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_me
     c->last_slot = si;
     if (!s.done) TFN_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
 
-    tfn_status lst = launch_normals(kind, m, cfg, slot_descs(s.dev), slot_maps(s.dev, s.cap), c->status, n, total,
-                                    c->num_sms, stream);
+    tfn_status lst = launch_normals(kind, m, cfg, slot_descs(s.dev), slot_maps(s.dev, s.cap), c->status,
+                                    slot_refine(s.dev, s.cap), n, total, c->num_sms, stream);
     if (lst) return lst;
     TFN_CUDA(cudaEventRecord(s.done, stream));
     return TFN_OK;
@@ -766,7 +805,7 @@ tfn_status tfn_plan_create(tfn_ctx *c, const tfn_frame *frames, int n, const tfn
             int total = 0;
             for (int k = i; k < j; ++k) total += frame_tiles(frames[k], cfg);
             lst = launch_normals(frames[i].input_type, *m, cfg, slot_descs(p->dev) + i, slot_maps(p->dev, n) + i,
-                                 c->status, j - i, total, c->num_sms, cs);
+                                 c->status, slot_refine(p->dev, n), j - i, total, c->num_sms, cs);
             i = j;
         }
         if (!cuda_ok(cudaStreamEndCapture(cs, &p->graph), "cudaStreamEndCapture") && lst == TFN_OK) lst = TFN_ERR_CUDA;

@@ -59,13 +59,23 @@ struct LaunchArgs {
     const FrameDesc *frames;
     const CUtensorMap *maps;  // one 2D tiled map per frame, 64-byte aligned
     uint32_t *status;         // [0]: DEVERR_* bits, [1]: refined-pixel count
+    unsigned long long *rlist;   // pixels to refine: frame index << 32 | y << 16 | x
+    unsigned long long *rcount;  // entries appended (zeroed before the launch; may exceed rcap)
+    int32_t rcap;                // capacity of rlist
     int32_t nframes;
     int32_t total_tiles;
     int32_t out_fmt;
     int32_t flags;
     float w[5];               // GRAD_WEIGHTED: row weights (w0 w1 w2); GRAD_SEP5: (d1 d2 s0 s1 s2)
-    int32_t pad[3];
+    int32_t pad[2];
 };
+
+// The refinement list of one launch: a 128-byte header holding the count,
+// then kRefineCap entries.  Every launch owns one (context slots, plans, the
+// allocation-free scratch).
+constexpr int kRefineCap = 65536;
+constexpr size_t kRefineListBytes = 128 + (size_t)kRefineCap * 8;
+constexpr int kRefineThreads = 128;
 
 // Work-item shapes the kernels are compiled for.  An item is a band of tw =
 // 128 pixel columns (32 lanes x 4) by th rows of one frame, computed by one
@@ -126,6 +136,8 @@ inline void sep5_weights(int grad, const float *given, float w[5])
 // Kernel entry points, one per (kind, grad, phi, cfg); defined in tfn_k_*.cu.
 typedef void (*KernelFn)(LaunchArgs);
 KernelFn kernel_for(int kind, int grad, int phi, int cfg);
+// The refinement kernel of (kind, grad, phi); nullptr for PlanePCA.
+KernelFn refiner_for(int kind, int grad, int phi);
 
 }  // namespace tfn
 
@@ -146,7 +158,9 @@ float refine_threshold(const tfn_frame &f, int grad, int phi);
 tfn_status encode_map(CUtensorMap *map, const tfn_frame &f, int cfg);
 FrameDesc describe_frame(const tfn_frame &f, int cfg, const tfn_method &m, int tile_begin);
 int frame_tiles(const tfn_frame &f, int cfg);
+// d_refine: the launch's refinement list (kRefineListBytes, 128-byte aligned).
 tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
-                          uint32_t *d_status, int nframes, int total_tiles, int num_sms, cudaStream_t stream);
+                          uint32_t *d_status, void *d_refine, int nframes, int total_tiles, int num_sms,
+                          cudaStream_t stream);
 
 }  // namespace tfn

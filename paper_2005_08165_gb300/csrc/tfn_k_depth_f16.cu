@@ -4,4 +4,5 @@
 
 namespace tfn {
 KernelFn kernels_depth_f16(int grad, int phi, int cfg) { return dev::select_kernel<KIND_DEPTH_F16>(grad, phi, cfg); }
+KernelFn refiners_depth_f16(int grad, int phi) { return dev::select_refiner<KIND_DEPTH_F16>(grad, phi); }
 }  // namespace tfn

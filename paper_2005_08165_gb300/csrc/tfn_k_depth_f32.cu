@@ -4,4 +4,5 @@
 
 namespace tfn {
 KernelFn kernels_depth_f32(int grad, int phi, int cfg) { return dev::select_kernel<KIND_DEPTH_F32>(grad, phi, cfg); }
+KernelFn refiners_depth_f32(int grad, int phi) { return dev::select_refiner<KIND_DEPTH_F32>(grad, phi); }
 }  // namespace tfn

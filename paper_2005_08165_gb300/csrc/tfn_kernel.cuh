@@ -36,8 +36,9 @@
 // itself, and each gradient a known relative error.  What remains is
 // cancellation inside the candidate sum (mean) or between the two middle
 // candidates (even median), and the effect of the gradient error; each pixel
-// bounds both, and the rare pixels whose bound exceeds the threshold go to
-// refine_pixel(), which redoes the pixel in double-float arithmetic.
+// bounds both, and the rare pixels whose bound exceeds the threshold are
+// listed for refine_kernel, which redoes them in double-float arithmetic
+// (refine_pixel) after the main kernel.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -807,7 +808,7 @@ __device__ __forceinline__ void sep5_row(const float (&z)[8], const Sep5W &w, df
 // started at 0 (below it; the iterates rise monotonically to it), and the
 // eigenvector from the largest cross product of two rows of M - lambda I.
 
-constexpr int kPcaNewton = 9;
+constexpr int kPcaNewton = 12;
 
 template <int KIND>
 __device__ __forceinline__ void pca_pixel(const float (&w)[3][3], float uc, float vc, float rfx, float rfy, float ztc,
@@ -1298,6 +1299,28 @@ __device__ __noinline__ Vec3 refine_from_input_sep5(const void *in, int64_t pitc
     return refine_candidates<KIND, PHI>(zi, ok, Gu, Gv, x, y, fx, fy, u0, v0);
 }
 
+// ------------------------------------------------------------ refinement list
+//
+// The main kernel does not refine: a pixel whose FP32 error bound is too
+// loose keeps its FP32 normal, gets bit 1 set in its mask byte, and is
+// appended to the launch's refinement list (frame index << 32 | y << 16 | x).
+// refine_kernel, launched after it on the same stream, redoes the listed
+// pixels in double-float and clears their bit.  Keeping the double-float
+// code out of the row loop's kernel leaves that loop its registers and
+// instruction cache.  A list that overflows its capacity is not lost: the
+// count still grows, and refine_kernel then finds the flagged pixels by their
+// mask bit instead.
+
+// Appends the flagged pixels (bit k of rb: column x0 + k) of row y of frame fi.
+static __device__ __noinline__ void list_for_refinement(unsigned long long *rlist, unsigned long long *rcount, int rcap,
+                                                 int fi, int x0, int y, unsigned rb)
+{
+    const unsigned long long base = atomicAdd(rcount, (unsigned long long)__popc(rb));
+    const unsigned long long e0 = ((unsigned long long)(unsigned)fi << 32) | ((unsigned)y << 16) | (unsigned)x0;
+    for (unsigned long long j = base; rb; ++j, rb &= rb - 1u)
+        if (j < (unsigned long long)rcap) rlist[j] = e0 + (unsigned)(__ffs(rb) - 1);
+}
+
 // ------------------------------------------------------------ the kernel
 
 // Persistent kernel of independent warps.  The work item is a band of 128
@@ -1381,7 +1404,6 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
     const float wts[3] = {args.w[0], args.w[1], args.w[2]};  // GRAD_WEIGHTED's row weights
     const Sep5W sw = {args.w[0], args.w[1], args.w[2], args.w[3], args.w[4]};  // GRAD_SEP5's profiles
     int cf = 0, fail_cc = 0;
-    unsigned nref = 0;
     bool failed = false;
     for (int i = 0; !failed; ++i) {
         const int t = gw + i * nw;
@@ -1397,8 +1419,6 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
         const int H = __ldg(&f->H), W = __ldg(&f->W), txs = __ldg(&f->tiles_x);
         const float fx = __ldg(&f->fx), fy = __ldg(&f->fy), u0 = __ldg(&f->u0), v0 = __ldg(&f->v0);
         const float thr = refine_all ? -1.f : __ldg(&f->thr);
-        const void *in = (const void *)__ldg((const unsigned long long *)&f->in);
-        const int64_t in_pitch = __ldg(&f->in_pitch);
         PtsDesc pts;
         pts.pts = (char *)__ldg((const unsigned long long *)&f->pts);
         pts.pitch = __ldg(&f->pts_pitch);
@@ -1454,7 +1474,6 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
                 j);
         };
 
-        unsigned long long pend_a = 0, pend_b = 0;  // bit 4 s + k: row y0 + s, column x0 + k
         UpCarry cy;
         // output row y0 + s from sample rows P (above), C and N (below); the
         // 5x5 filters' gradients come in gu, gv
@@ -1471,18 +1490,15 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
                                           oz, mw, rb);
             }
             if (y < H && nvalid > 0) {
+                rb &= (1u << min(nvalid, 4)) - 1u;
+                // pixels whose FP32 error bound is too loose: mask bit 1 set
+                // (bit k of rb to bit 8k + 1), and listed for refine_kernel
+                mw |= ((rb * 0x00204081u) & 0x01010101u) << 1;
                 store4(out, args.out_fmt, x0, y, nvalid, ox, oy, oz, mw);
                 if (pts.pts)  // the fused point cloud of this row
                     store_points4<KIND>(pts, x0, y, nvalid, C.z, ucf, __fdiv_rn(__fsub_rn((float)y, v0), fy), ztc);
-                rb &= (1u << min(nvalid, 4)) - 1u;
-            } else {
-                rb = 0;
+                if (rb) list_for_refinement(args.rlist, args.rcount, args.rcap, cf, x0, y, rb);
             }
-            // pixels whose FP32 error bound is too loose: redone after the item
-            if (s < 16)
-                pend_a |= (unsigned long long)rb << (4 * s);
-            else
-                pend_b |= (unsigned long long)rb << (4 * (s - 16));
         };
         if constexpr (!SEP5) {
             const df g0[4] = {};  // (3x3 filters compute their gradients in row_step)
@@ -1623,27 +1639,6 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
                 ++cc;
             }
         }
-        // Rare: the double-float path for this item's flagged pixels (lanes in
-        // parallel); the later store to the same pixel wins.
-        while (pend_a | pend_b) {
-            int b;
-            if (pend_a) {
-                b = __ffsll((long long)pend_a) - 1;
-                pend_a &= pend_a - 1;
-            } else {
-                b = 64 + __ffsll((long long)pend_b) - 1;
-                pend_b &= pend_b - 1;
-            }
-            const int x = x0 + (b & 3), y = y0 + (b >> 2);
-            Vec3 nr = {0.f, 0.f, 0.f};
-            if constexpr (SEP5)
-                nr = refine_from_input_sep5<KIND, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0, sw.d1, sw.d2, sw.s0,
-                                                       sw.s1, sw.s2);
-            else if constexpr (GRAD != GRAD_PLANEPCA)  // (PlanePCA never flags a pixel)
-                nr = refine_from_input<KIND, GRAD, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0, wts[0], wts[1], wts[2]);
-            store1(out, args.out_fmt, x, y, nr);
-            ++nref;
-        }
     }
     if (failed) {
         // a copy did not land in time: flag it, then give the copies this warp
@@ -1657,9 +1652,6 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
         __syncwarp();
         return;
     }
-    // count of refined pixels (diagnostics): one atomic per warp, only if any
-    const unsigned tot = __reduce_add_sync(0xffffffffu, nref);
-    if (lane == 0 && tot) atomicAdd(args.status + 1, tot);
 }
 
 template <int KIND>
@@ -1675,6 +1667,80 @@ KernelFn select_kernel(int grad, int phi, int cfg)
 #undef TFN_KC
 #undef TFN_K
     return nullptr;
+}
+
+// Refines one flagged pixel (x, y) of frame fi of the launch and clears its
+// mask bit 1.
+template <int KIND, int GRAD, int PHI>
+__device__ __forceinline__ void refine_at(const LaunchArgs &args, int fi, int x, int y)
+{
+    const FrameDesc *f = args.frames + fi;
+    OutDesc out;
+    out.out = (char *)__ldg((const unsigned long long *)&f->out);
+    out.out_pitch = __ldg(&f->out_pitch);
+    out.out_plane = __ldg(&f->out_plane);
+    out.mask = (uint8_t *)__ldg((const unsigned long long *)&f->mask);
+    out.mask_pitch = __ldg(&f->mask_pitch);
+    const void *in = (const void *)__ldg((const unsigned long long *)&f->in);
+    const int64_t in_pitch = __ldg(&f->in_pitch);
+    const int H = __ldg(&f->H), W = __ldg(&f->W);
+    const float fx = __ldg(&f->fx), fy = __ldg(&f->fy), u0 = __ldg(&f->u0), v0 = __ldg(&f->v0);
+    Vec3 nr;
+    if constexpr (GRAD == GRAD_SEP5)
+        nr = refine_from_input_sep5<KIND, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0, args.w[0], args.w[1],
+                                               args.w[2], args.w[3], args.w[4]);
+    else
+        nr = refine_from_input<KIND, GRAD, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0, args.w[0], args.w[1],
+                                                args.w[2]);
+    store1(out, args.out_fmt, x, y, nr);
+    out.mask[(int64_t)y * out.mask_pitch + x] = 1;
+}
+
+// The second kernel of a launch: the pixels normals_kernel flagged, from its
+// list, or (when the list overflowed) by a scan of every frame's mask for
+// bit 1.  Adds the number of refined pixels to status[1].
+template <int KIND, int GRAD, int PHI>
+__global__ void __launch_bounds__(kRefineThreads) refine_kernel(const __grid_constant__ LaunchArgs args)
+{
+    const unsigned long long cnt = *args.rcount;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x, nth = (long long)gridDim.x * blockDim.x;
+    unsigned nref = 0;
+    if (cnt <= (unsigned long long)args.rcap) {
+        for (long long i = tid; i < (long long)cnt; i += nth) {
+            const unsigned long long e = args.rlist[i];
+            refine_at<KIND, GRAD, PHI>(args, (int)(e >> 32), (int)(e & 0xffffu), (int)((e >> 16) & 0xffffu));
+            ++nref;
+        }
+    } else {
+        for (int fi = 0; fi < args.nframes; ++fi) {
+            const FrameDesc *f = args.frames + fi;
+            const uint8_t *mask = (const uint8_t *)__ldg((const unsigned long long *)&f->mask);
+            const int64_t mp = __ldg(&f->mask_pitch);
+            const int W = __ldg(&f->W);
+            const long long npx = (long long)__ldg(&f->H) * W;
+            for (long long q = tid; q < npx; q += nth) {
+                const int y = (int)(q / W), x = (int)(q - (long long)y * W);
+                if (mask[(int64_t)y * mp + x] & 2u) {
+                    refine_at<KIND, GRAD, PHI>(args, fi, x, y);
+                    ++nref;
+                }
+            }
+        }
+    }
+    const unsigned tot = __reduce_add_sync(0xffffffffu, nref);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(args.status + 1, tot);
+}
+
+template <int KIND>
+KernelFn select_refiner(int grad, int phi)
+{
+#define TFN_R(G, P) \
+    if (grad == G && phi == P) return &refine_kernel<KIND, G, P>;
+#define TFN_RP(G) TFN_R(G, PHI_MEAN) TFN_R(G, PHI_MEDIAN)
+    TFN_RP(GRAD_FD) TFN_RP(GRAD_SOBEL) TFN_RP(GRAD_SCHARR) TFN_RP(GRAD_PREWITT) TFN_RP(GRAD_WEIGHTED) TFN_RP(GRAD_SEP5)
+#undef TFN_RP
+#undef TFN_R
+    return nullptr;  // (PlanePCA never flags a pixel: no refinement kernel)
 }
 
 }  // namespace dev

@@ -6,9 +6,9 @@
 // extensions to call cudaMalloc, or a latency-critical loop where cudaMalloc
 // / cudaFree could synchronise the device and stall other streams.  Such a
 // caller cannot create a tfn_ctx (a context allocates its scratch), so this
-// entry point keeps the scratch the kernel needs -- per-frame descriptors,
-// TMA tensor maps and the status word -- in one file-scope __device__ array
-// of fixed size instead.
+// entry point keeps the scratch the kernels need -- per-frame descriptors,
+// TMA tensor maps, the status word and the refinement list -- in one
+// file-scope __device__ array of fixed size instead.
 //
 // The array is a device symbol: in host code its name is only a host-side
 // stand-in, so the first call on each device (with that device current)
@@ -35,6 +35,12 @@ struct alignas(256) Scratch {
     CUtensorMap maps[kMax];  // 128 bytes each, 64-byte aligned
     FrameDesc desc[kMax];
     uint32_t status[64];
+    alignas(128) unsigned char refine[kRefineListBytes];  // the refinement list (runs of a call take turns)
+};
+// The host-side staging of a call: what is copied into the scratch.
+struct Staging {
+    CUtensorMap maps[kMax];
+    FrameDesc desc[kMax];
 };
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(Scratch)];
@@ -83,7 +89,7 @@ extern "C" tfn_status tfn_normals_noalloc(const tfn_frame *frames, int n, const 
     // allocation) and copied into the device array on the caller's stream; a
     // pageable-memory copy returns once the source has been consumed, so the
     // staging is free for the next call as soon as this one returns.
-    thread_local Scratch h;
+    thread_local Staging h;
     // one launch per run of frames of one input kind; a small run takes the short-item shape
     int run_cfg[kMax];
     for (int i = 0; i < n;) {
@@ -114,8 +120,8 @@ extern "C" tfn_status tfn_normals_noalloc(const tfn_frame *frames, int n, const 
         while (j < n && frames[j].input_type == frames[i].input_type) ++j;
         int total = 0;
         for (int k = i; k < j; ++k) total += frame_tiles(frames[k], run_cfg[i]);
-        st = launch_normals(frames[i].input_type, *method, run_cfg[i], d->desc + i, d->maps + i, d->status, j - i, total,
-                            sms, s);
+        st = launch_normals(frames[i].input_type, *method, run_cfg[i], d->desc + i, d->maps + i, d->status, d->refine,
+                            j - i, total, sms, s);
         if (st) return st;
         i = j;
     }

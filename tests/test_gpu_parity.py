@@ -147,6 +147,21 @@ def test_refine_all_path_is_tight(torch, tfn, ctx, grad, phi):
         assert st["over"] == 0 or phi == "median"
 
 
+@pytest.mark.parametrize("phi", PHIS)
+def test_refinement_list_overflow_scans_the_mask(torch, tfn, ctx, phi):
+    # every pixel of a noisy 480x640 frame flagged: about 300k, past the 65536 entries of the
+    # refinement list, so the refinement kernel finds them by their mask bit instead
+    img = scenes.noisy_batch(1, seed0=950)[0]
+    ctx.refined_pixels()  # (reading the counter restarts it)
+    n, m = run_batch(torch, tfn, ctx, [(img, scenes.CAMERA)], grad="fd", phi=phi, flags=tfn.TFN_FLAG_REFINE_ALL)
+    refined = ctx.refined_pixels()
+    assert set(np.unique(m[0]).tolist()) <= {0, 1}, "a flagged pixel kept its mask bit"
+    evaluable = int((m[0] == 1).sum())
+    assert 65536 < refined <= evaluable and refined > 0.9 * evaluable, (refined, evaluable)
+    st = compare(n[0], m[0], img, scenes.CAMERA, grad="fd", phi=phi, tol=1e-5)
+    assert st["over"] == 0 or phi == "median"
+
+
 WEIGHTS = [(1.0, 3.0, 1.0), (1.0, 0.0, 0.0), (2.0, -1.0, 0.5), (0.0, 1.0, 0.0)]
 
 

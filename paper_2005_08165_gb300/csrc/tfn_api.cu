@@ -300,7 +300,8 @@ tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDes
     if (grid < 1) return TFN_OK;
     // the refinement kernel of this method (none for PlanePCA, which never flags a pixel)
     KernelFn rf = nullptr;
-    if (grad != GRAD_PLANEPCA && !(rf = refiner_for(kind, grad, method_phi(m)))) return TFN_ERR_UNSUPPORTED;
+    if (grad != GRAD_PLANEPCA && !refines_in_place(cfg) && !(rf = refiner_for(kind, grad, method_phi(m))))
+        return TFN_ERR_UNSUPPORTED;
     LaunchArgs a;
     a.frames = d_frames;
     a.maps = d_maps;
@@ -316,15 +317,15 @@ tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDes
     if (grad_is_sep5(m.grad)) sep5_weights(m.grad, m.weights, a.w);
     a.pad[0] = a.pad[1] = 0;
     void *params[] = {&a};
-    if (rf && !cuda_ok(cudaMemsetAsync(a.rcount, 0, sizeof *a.rcount, stream), "cudaMemsetAsync(refinement count)"))
-        return TFN_ERR_CUDA;
     if (!cuda_ok(cudaLaunchKernel((const void *)fn, dim3(grid), dim3(threads), params, smem, stream),
                  "cudaLaunchKernel"))
         return TFN_ERR_CUDA;
     // the flagged pixels: a few per thousand, spread over every SM
     if (rf && !cuda_ok(cudaLaunchKernel((const void *)rf, dim3(4 * num_sms), dim3(kRefineThreads), params, 0, stream),
-                       "cudaLaunchKernel(refine)"))
+                       "cudaLaunchKernel(refine)")) {
+        cudaMemsetAsync(d_refine, 0, 128, stream);  // (what the refinement kernel would have zeroed)
         return TFN_ERR_CUDA;
+    }
     return TFN_OK;
 }
 
@@ -364,6 +365,18 @@ size_t slot_bytes(int cap)
     return (size_t)cap * sizeof(FrameDesc) + 128 + (size_t)cap * sizeof(CUtensorMap) + 128 + kRefineListBytes;
 }
 
+FrameDesc *slot_descs(void *base) { return (FrameDesc *)base; }
+CUtensorMap *slot_maps(void *base, int cap)
+{
+    uintptr_t p = (uintptr_t)base + (size_t)cap * sizeof(FrameDesc);
+    return (CUtensorMap *)((p + 127) & ~(uintptr_t)127);
+}
+void *slot_refine(void *base, int cap)
+{
+    uintptr_t p = (uintptr_t)(slot_maps(base, cap) + cap);
+    return (void *)((p + 127) & ~(uintptr_t)127);
+}
+
 tfn_status slot_reserve(tfn_ctx *c, Slot &s, int n)
 {
     if (s.cap >= n) return TFN_OK;
@@ -377,6 +390,10 @@ tfn_status slot_reserve(tfn_ctx *c, Slot &s, int n)
     size_t bytes = slot_bytes(cap);
     tfn_status st = ctx_alloc(c, &s.dev, bytes);
     if (st) return st;
+    if (!cuda_ok(cudaMemset(slot_refine(s.dev, cap), 0, 128), "cudaMemset(refinement list)")) {
+        ctx_free(c, s.dev, bytes);
+        return TFN_ERR_CUDA;
+    }
     if (!cuda_ok(cudaMallocHost(&s.host, bytes), "cudaMallocHost")) {
         ctx_free(c, s.dev, bytes);
         return TFN_ERR_CUDA;
@@ -386,17 +403,7 @@ tfn_status slot_reserve(tfn_ctx *c, Slot &s, int n)
     return TFN_OK;
 }
 
-FrameDesc *slot_descs(void *base) { return (FrameDesc *)base; }
-CUtensorMap *slot_maps(void *base, int cap)
-{
-    uintptr_t p = (uintptr_t)base + (size_t)cap * sizeof(FrameDesc);
-    return (CUtensorMap *)((p + 127) & ~(uintptr_t)127);
-}
-void *slot_refine(void *base, int cap)
-{
-    uintptr_t p = (uintptr_t)(slot_maps(base, cap) + cap);
-    return (void *)((p + 127) & ~(uintptr_t)127);
-}
+
 
 // One launch over frames[0..n) (all of one input kind).
 tfn_status launch_group(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method &m, cudaStream_t stream)

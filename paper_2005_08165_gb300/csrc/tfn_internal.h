@@ -60,7 +60,7 @@ struct LaunchArgs {
     const CUtensorMap *maps;  // one 2D tiled map per frame, 64-byte aligned
     uint32_t *status;         // [0]: DEVERR_* bits, [1]: refined-pixel count
     unsigned long long *rlist;   // pixels to refine: frame index << 32 | y << 16 | x
-    unsigned long long *rcount;  // entries appended (zeroed before the launch; may exceed rcap)
+    unsigned long long *rcount;  // entries appended (may exceed rcap); then the refinement kernel's block counter
     int32_t rcap;                // capacity of rlist
     int32_t nframes;
     int32_t total_tiles;
@@ -70,9 +70,11 @@ struct LaunchArgs {
     int32_t pad[2];
 };
 
-// The refinement list of one launch: a 128-byte header holding the count,
-// then kRefineCap entries.  Every launch owns one (context slots, plans, the
-// allocation-free scratch).
+// The refinement list of one launch: a 128-byte header (the entry count,
+// then the refinement kernel's finished-block counter; both zero between
+// launches: zeroed at allocation, and again by the refinement kernel's last
+// block), then kRefineCap entries.  Every launch owns one (context slots,
+// plans, the allocation-free scratch).
 constexpr int kRefineCap = 65536;
 constexpr size_t kRefineListBytes = 128 + (size_t)kRefineCap * 8;
 constexpr int kRefineThreads = 128;
@@ -91,6 +93,11 @@ constexpr TileCfg kCfgs[kNumCfg] = {
     {128, 18, 18, 5, 3, 4}, {128, 30, 30, 8, 3, 4}, {128, 12, 12, 7, 3, 4}, {128, 6, 6, 4, 2, 4}};
 // the default shape for launches with few items (short items spread one frame over many warps)
 constexpr int kSmallCfg = 3;
+// Whether the (shape) kernel refines its flagged pixels itself, at the end of
+// each item, rather than listing them for the refinement kernel: the
+// short-item shape of small launches, where a second launch would cost more
+// than the refinement.
+constexpr bool refines_in_place(int c) { return c == kSmallCfg; }
 // the default shape otherwise: the tallest items (the least halo per row) measured fastest for every
 // filter on 256 x 480x640 frames (FD mean 0.9%, Sobel 4.5%, the 5x5 filters 13% faster than 18 rows)
 constexpr int kDefaultCfg = 1;

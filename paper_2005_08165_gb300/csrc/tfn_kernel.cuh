@@ -1305,7 +1305,8 @@ __device__ __noinline__ Vec3 refine_from_input_sep5(const void *in, int64_t pitc
 // loose keeps its FP32 normal, gets bit 1 set in its mask byte, and is
 // appended to the launch's refinement list (frame index << 32 | y << 16 | x).
 // refine_kernel, launched after it on the same stream, redoes the listed
-// pixels in double-float and clears their bit.  Keeping the double-float
+// pixels in double-float and clears their bit, and its last block zeroes the
+// count for the list's next launch.  Keeping the double-float
 // code out of the row loop's kernel leaves that loop its registers and
 // instruction cache.  A list that overflows its capacity is not lost: the
 // count still grows, and refine_kernel then finds the flagged pixels by their
@@ -1344,6 +1345,9 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
     typedef Row<KIND, GRAD> R;
     constexpr int TH = kCfgs[CFG].th, CR = kCfgs[CFG].cr, NST = cfg_nst(CFG, GRAD), NW = cta_warps(CFG, GRAD);
     constexpr bool SEP5 = GRAD == GRAD_SEP5;
+    // the short-item shape (launches of few items, e.g. one frame) refines
+    // in place at the end of each item: a second launch would cost more there
+    constexpr bool INPLACE = refines_in_place(CFG);
     constexpr int HR = SEP5 ? 2 : 1;                  // halo rows above and below an item
     constexpr int NCH = (TH + 2 * HR + CR - 1) / CR;  // chunks per item: rows y0-HR .. y0+TH-1+HR
     static_assert(SEP5 || (TH + 2) % CR == 0, "3x3 items' chunks tile their rows exactly");
@@ -1404,6 +1408,7 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
     const float wts[3] = {args.w[0], args.w[1], args.w[2]};  // GRAD_WEIGHTED's row weights
     const Sep5W sw = {args.w[0], args.w[1], args.w[2], args.w[3], args.w[4]};  // GRAD_SEP5's profiles
     int cf = 0, fail_cc = 0;
+    unsigned nref = 0;  // (INPLACE) pixels refined by this lane
     bool failed = false;
     for (int i = 0; !failed; ++i) {
         const int t = gw + i * nw;
@@ -1474,6 +1479,7 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
                 j);
         };
 
+        unsigned long long pend_a = 0, pend_b = 0;  // (INPLACE) bit 4 s + k: row y0 + s, column x0 + k
         UpCarry cy;
         // output row y0 + s from sample rows P (above), C and N (below); the
         // 5x5 filters' gradients come in gu, gv
@@ -1493,11 +1499,18 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
                 rb &= (1u << min(nvalid, 4)) - 1u;
                 // pixels whose FP32 error bound is too loose: mask bit 1 set
                 // (bit k of rb to bit 8k + 1), and listed for refine_kernel
-                mw |= ((rb * 0x00204081u) & 0x01010101u) << 1;
+                if constexpr (!INPLACE) mw |= ((rb * 0x00204081u) & 0x01010101u) << 1;
                 store4(out, args.out_fmt, x0, y, nvalid, ox, oy, oz, mw);
                 if (pts.pts)  // the fused point cloud of this row
                     store_points4<KIND>(pts, x0, y, nvalid, C.z, ucf, __fdiv_rn(__fsub_rn((float)y, v0), fy), ztc);
-                if (rb) list_for_refinement(args.rlist, args.rcount, args.rcap, cf, x0, y, rb);
+                if constexpr (INPLACE) {  // (redone after the item)
+                    if (s < 16)
+                        pend_a |= (unsigned long long)rb << (4 * s);
+                    else
+                        pend_b |= (unsigned long long)rb << (4 * (s - 16));
+                } else if (rb) {
+                    list_for_refinement(args.rlist, args.rcount, args.rcap, cf, x0, y, rb);
+                }
             }
         };
         if constexpr (!SEP5) {
@@ -1639,6 +1652,32 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
                 ++cc;
             }
         }
+        if constexpr (INPLACE) {
+            // the double-float path for this item's flagged pixels (lanes in
+            // parallel); the later store to the same pixel wins
+            const void *in = (const void *)__ldg((const unsigned long long *)&f->in);
+            const int64_t in_pitch = __ldg(&f->in_pitch);
+            while (pend_a | pend_b) {
+                int b;
+                if (pend_a) {
+                    b = __ffsll((long long)pend_a) - 1;
+                    pend_a &= pend_a - 1;
+                } else {
+                    b = 64 + __ffsll((long long)pend_b) - 1;
+                    pend_b &= pend_b - 1;
+                }
+                const int x = x0 + (b & 3), y = y0 + (b >> 2);
+                Vec3 nr = {0.f, 0.f, 0.f};
+                if constexpr (SEP5)
+                    nr = refine_from_input_sep5<KIND, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0, sw.d1, sw.d2,
+                                                           sw.s0, sw.s1, sw.s2);
+                else if constexpr (GRAD != GRAD_PLANEPCA)  // (PlanePCA never flags a pixel)
+                    nr = refine_from_input<KIND, GRAD, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0, wts[0], wts[1],
+                                                            wts[2]);
+                store1(out, args.out_fmt, x, y, nr);
+                ++nref;
+            }
+        }
     }
     if (failed) {
         // a copy did not land in time: flag it, then give the copies this warp
@@ -1651,6 +1690,11 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
         }
         __syncwarp();
         return;
+    }
+    if constexpr (INPLACE) {
+        // count of refined pixels (diagnostics): one atomic per warp, only if any
+        const unsigned tot = __reduce_add_sync(0xffffffffu, nref);
+        if (lane == 0 && tot) atomicAdd(args.status + 1, tot);
     }
 }
 
@@ -1729,6 +1773,18 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(const __grid_con
     }
     const unsigned tot = __reduce_add_sync(0xffffffffu, nref);
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(args.status + 1, tot);
+    // The last block to finish (every block has read the count by then)
+    // zeroes the count and the block counter for the launch's next use.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned *done = reinterpret_cast<unsigned *>(args.rcount + 1);
+        __threadfence();
+        if (atomicAdd(done, 1u) == gridDim.x - 1) {
+            *args.rcount = 0;
+            *done = 0;
+            __threadfence();
+        }
+    }
 }
 
 template <int KIND>

@@ -33,7 +33,10 @@
  * the caller; the library never frees it.  Rows of every image must start on
  * 16-byte boundaries (pointer and pitches multiples of 16 bytes), else
  * TFN_ERR_MISALIGNED.  The context owns only its scratch (frame descriptors,
- * TMA tensor maps, staging buffers of the host-buffer path, a status word).
+ * TMA tensor maps, the list of pixels to refine, staging buffers of the
+ * host-buffer path, a status word).  A launch may enqueue a second, small
+ * kernel after the main one (the double-float redo of the rare pixels whose
+ * FP32 error bound is too loose); both are on the caller's stream.
  *
  * Streams and errors.  Calls that take a stream validate their arguments
  * synchronously, return a status, and then enqueue work on that stream
@@ -391,9 +394,9 @@ tfn_status tfn_server_destroy(tfn_server *srv);
  * cudaFree could synchronise the device.  (The paper has no counterpart: this
  * is an interface concern of this library.)
  *
- * It takes no context.  The scratch the kernel needs (frame descriptors, TMA
- * tensor maps, a status word; about 17 KB) lives in one fixed array compiled
- * into the library, which every device that loads the library keeps until the
+ * It takes no context.  The scratch the kernels need (frame descriptors, TMA
+ * tensor maps, a status word, the list of pixels to refine; about 540 KB)
+ * lives in one fixed array compiled into the library, which every device that loads the library keeps until the
  * process exits.  Limits and behaviour:
  *   - n > TFN_NOALLOC_MAX_FRAMES returns TFN_ERR_INVALID_ARG before anything
  *     is enqueued; otherwise arguments are validated as for tfn_normals_batch;

@@ -1299,6 +1299,41 @@ __device__ __noinline__ Vec3 refine_from_input_sep5(const void *in, int64_t pitc
     return refine_candidates<KIND, PHI>(zi, ok, Gu, Gv, x, y, fx, fy, u0, v0);
 }
 
+// ------------------------------------------------------------ item -> frame
+
+// The frame of work item t: the last frame whose first item is at or below
+// t.  Frames are numbered in item order and a warp's items only increase, so
+// the search starts at the previous answer `from`.  A warp's next item lies
+// about (warps in the grid) / (items per frame) frames further on, so
+// stepping one frame at a time would chain dozens of dependent loads per
+// item; instead the first guess assumes frames of the size of `from` (exact
+// for a batch of equal frames), and a binary search over the rest covers any
+// mix.
+__device__ __forceinline__ int frame_of(const FrameDesc *frames, int nframes, int t, int from)
+{
+    if (from + 1 >= nframes) return from;
+    const int b0 = __ldg(&frames[from].tile_begin), b1 = __ldg(&frames[from + 1].tile_begin);
+    if (t < b1) return from;
+    int lo = from + 1, hi = nframes - 1;  // the answer lies in [lo, hi] (t >= b1)
+    const int g = min(hi, from + (t - b0) / (b1 - b0));  // (every frame has at least one item)
+    if (g >= lo) {
+        if (__ldg(&frames[g].tile_begin) <= t) {
+            if (g == hi || __ldg(&frames[g + 1].tile_begin) > t) return g;
+            lo = g + 1;
+        } else {
+            hi = g - 1;
+        }
+    }
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&frames[mid].tile_begin) <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 // ------------------------------------------------------------ refinement list
 //
 // The main kernel does not refine: a pixel whose FP32 error bound is too
@@ -1382,7 +1417,7 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
     auto issue = [&](int cc) {
         const int t = gw + (cc / NCH) * nw;
         if (t >= total) return;
-        while (pf + 1 < args.nframes && __ldg(&args.frames[pf + 1].tile_begin) <= t) ++pf;
+        pf = frame_of(args.frames, args.nframes, t, pf);
         const FrameDesc *f = args.frames + pf;
         const int lt = t - __ldg(&f->tile_begin), txs = __ldg(&f->tiles_x);
         const int x = (lt % txs) * 128 - PADX;
@@ -1413,7 +1448,7 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
     for (int i = 0; !failed; ++i) {
         const int t = gw + i * nw;
         if (t >= total) break;
-        while (cf + 1 < args.nframes && __ldg(&args.frames[cf + 1].tile_begin) <= t) ++cf;
+        cf = frame_of(args.frames, args.nframes, t, cf);
         const FrameDesc *f = args.frames + cf;
         OutDesc out;
         out.out = (char *)__ldg((const unsigned long long *)&f->out);

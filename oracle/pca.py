@@ -6,7 +6,7 @@ empirical mean removed, and the normal is the principal component of smallest co
 eigenvector of the smallest eigenvalue of the scatter matrix sum_j (q_j - q_mean)(q_j - q_mean)^T.
 A library symmetric eigensolver (numpy.linalg.eigh, LAPACK) is the step that finds it.
 
-Readings where the paper is silent (listed in the design doc as R16):
+Readings where the paper is silent (reading R16):
 - the neighbourhood is the 8-connected one, k = 8 (the paper's 3F2N uses the same);
 - a pixel is evaluable iff it and all 8 neighbours are inside the image and valid (the hole rule
   of the 3F2N oracle); others get (0, 0, 0) and mask 0;

@@ -15,7 +15,7 @@
  *   Sec. III, Eqs. (z_d), (dd_2_dz), (nx2_ny2_nz3): disparity form, Z = f t_c / d,
  *                                    nx = dd/du, ny = dd/dv, same n_z rule.
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent (labelled R1, R2, ...):
  *   R1 a sample is valid iff it is finite and 2^-16 <= value <= 2^16 (depth in
  *      any unit, float disparity in pixels); a 16-bit fixed-point disparity is
  *      valid iff its raw value is non-zero.  Anything else is a hole.

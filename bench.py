@@ -69,7 +69,7 @@ def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2005_08165_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name in ("tfn_kernel.cuh", "tfn_internal.h") or (name.startswith("tfn_k_") and name.endswith(".cu")):
+        if name in ("tfn_kernel.cuh", "tfn_internal.h", "tfn_items.h") or (name.startswith("tfn_k_") and name.endswith(".cu")):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(name.encode() + f.read())
     return h.hexdigest()[:16]

@@ -45,6 +45,7 @@
 #include <cuda_fp16.h>
 
 #include "tfn_internal.h"
+#include "tfn_items.h"
 
 namespace tfn {
 namespace dev {
@@ -1301,37 +1302,10 @@ __device__ __noinline__ Vec3 refine_from_input_sep5(const void *in, int64_t pitc
 
 // ------------------------------------------------------------ item -> frame
 
-// The frame of work item t: the last frame whose first item is at or below
-// t.  Frames are numbered in item order and a warp's items only increase, so
-// the search starts at the previous answer `from`.  A warp's next item lies
-// about (warps in the grid) / (items per frame) frames further on, so
-// stepping one frame at a time would chain dozens of dependent loads per
-// item; instead the first guess assumes frames of the size of `from` (exact
-// for a batch of equal frames), and a binary search over the rest covers any
-// mix.
-__device__ __forceinline__ int frame_of(const FrameDesc *frames, int nframes, int t, int from)
+// frame_of (tfn_items.h) over the launch's frame descriptors.
+__device__ __forceinline__ int frame_of_item(const FrameDesc *frames, int nframes, int t, int from)
 {
-    if (from + 1 >= nframes) return from;
-    const int b0 = __ldg(&frames[from].tile_begin), b1 = __ldg(&frames[from + 1].tile_begin);
-    if (t < b1) return from;
-    int lo = from + 1, hi = nframes - 1;  // the answer lies in [lo, hi] (t >= b1)
-    const int g = min(hi, from + (t - b0) / (b1 - b0));  // (every frame has at least one item)
-    if (g >= lo) {
-        if (__ldg(&frames[g].tile_begin) <= t) {
-            if (g == hi || __ldg(&frames[g + 1].tile_begin) > t) return g;
-            lo = g + 1;
-        } else {
-            hi = g - 1;
-        }
-    }
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(&frames[mid].tile_begin) <= t)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
+    return frame_of([frames](int i) { return __ldg(&frames[i].tile_begin); }, nframes, t, from);
 }
 
 // ------------------------------------------------------------ refinement list
@@ -1417,7 +1391,7 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
     auto issue = [&](int cc) {
         const int t = gw + (cc / NCH) * nw;
         if (t >= total) return;
-        pf = frame_of(args.frames, args.nframes, t, pf);
+        pf = frame_of_item(args.frames, args.nframes, t, pf);
         const FrameDesc *f = args.frames + pf;
         const int lt = t - __ldg(&f->tile_begin), txs = __ldg(&f->tiles_x);
         const int x = (lt % txs) * 128 - PADX;
@@ -1448,7 +1422,7 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
     for (int i = 0; !failed; ++i) {
         const int t = gw + i * nw;
         if (t >= total) break;
-        cf = frame_of(args.frames, args.nframes, t, cf);
+        cf = frame_of_item(args.frames, args.nframes, t, cf);
         const FrameDesc *f = args.frames + cf;
         OutDesc out;
         out.out = (char *)__ldg((const unsigned long long *)&f->out);

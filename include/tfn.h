@@ -388,11 +388,12 @@ tfn_status tfn_server_destroy(tfn_server *srv);
 /* Largest n that tfn_normals_noalloc accepts. */
 #define TFN_NOALLOC_MAX_FRAMES 64
 
-/* Same result as tfn_normals_batch, for callers that may not allocate device
- * memory at all: a host framework or plugin interface that owns every device
- * byte and forbids cudaMalloc, or a latency-critical loop where cudaMalloc /
- * cudaFree could synchronise the device.  (The paper has no counterpart: this
- * is an interface concern of this library.)
+/* Same result as tfn_normals_batch (the same kernels, bit for bit), for
+ * callers that may not allocate device memory at all: a host framework or
+ * plugin interface that owns every device byte and forbids cudaMalloc, or a
+ * loop that must not call cudaMalloc / cudaFree because they can synchronise
+ * the whole device.  (The paper has no counterpart: this is an interface
+ * concern of this library.)
  *
  * It takes no context.  The scratch the kernels need (frame descriptors, TMA
  * tensor maps, a status word, the list of pixels to refine; about 540 KB)
@@ -405,7 +406,12 @@ tfn_status tfn_server_destroy(tfn_server *srv);
  *     stream capture);
  *   - it calls no cudaMalloc, cudaFree or other allocating routine; the
  *     descriptors are staged in thread-local host storage and copied into the
- *     array on `stream`;
+ *     array on `stream` from that pageable memory, which the CUDA runtime may
+ *     stage by first waiting for the work already queued on `stream`: the call
+ *     can block the host until that work is done;
+ *   - while `stream` is capturing a CUDA graph it returns TFN_ERR_UNSUPPORTED
+ *     and enqueues nothing (a captured copy would read the staging only at
+ *     replay time, when it holds another call's frames);
  *   - every call reuses the same array and overwrites the previous call's
  *     contents, so calls whose GPU work overlaps (other streams, or earlier
  *     work still running on another stream) race and must be serialised by

@@ -195,17 +195,24 @@ tfn_status validate_frame(const tfn_frame *f, int out_fmt)
 // roundings) and the larger |middle candidate| for the median (K1 = 11).
 // cA bounds |A|/|n'|: A = (u-u0) G_u + (v-v0) G_v and |n'| >= |(fx G_u, fy G_v)|.
 // The gradients are carried as h + l to about u^2 relative (compensated
-// reciprocals, or a residual-corrected quotient for FD).  The kernel compares
-// bound with thr |n'|.
+// reciprocals, or a residual-corrected quotient for FD), except FD on depth
+// with the mean when kFdOnePassMean is set: one-pass quotients within 5u of
+// themselves.
+// That adds 5u to the error of (nx', ny') and 5u (|u-u0| |G_u| + |v-v0| |G_v|)
+// <= 5 sqrt(2) cA u |n'| to that of A (the fixed part below), and the
+// diagonal numerators' share, which the kernel adds to its bound.  The kernel
+// compares bound with thr |n'|.
 float refine_threshold(const tfn_frame &f, int grad, int phi)
 {
-    (void)grad;  // every filter's gradients are compensated
     const double u = std::ldexp(1.0, -24);
     const double tol_part = 0.75 * 1e-3 * M_PI / 180.0;
     const double mu = std::max(std::fabs(0.0 - f.cam.u0), std::fabs(f.width - 1.0 - f.cam.u0));
     const double mv = std::max(std::fabs(0.0 - f.cam.v0), std::fabs(f.height - 1.0 - f.cam.v0));
     const double cA = std::sqrt((mu / f.cam.fx) * (mu / f.cam.fx) + (mv / f.cam.fy) * (mv / f.cam.fy));
-    const double fixed = (6.0 + 4.0 * cA + 32.0 / std::min(f.cam.fx, f.cam.fy)) * u;
+    const bool depth = f.input_type == KIND_DEPTH_F32 || f.input_type == KIND_DEPTH_F16;
+    const bool one_pass = kFdOnePassMean && grad == GRAD_FD && phi == PHI_MEAN && depth;
+    const double fixed = (6.0 + 4.0 * cA + 32.0 / std::min(f.cam.fx, f.cam.fy) +
+                          (one_pass ? 5.0 + 5.0 * std::sqrt(2.0) * cA : 0.0)) * u;
     const double k1 = phi == PHI_MEAN ? 23.0 : 11.0;
     const double t = (tol_part - fixed) / (k1 * u);
     return t > 0 ? (float)t : 0.f;
@@ -278,8 +285,8 @@ int frame_tiles(const tfn_frame &f, int cfg)
 // Launches the kernel for frames of one input kind whose descriptors and
 // tensor maps are already in device memory.
 tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
-                          uint32_t *d_status, void *d_refine, int nframes, int total_tiles, int num_sms,
-                          cudaStream_t stream)
+                          uint32_t *d_status, void *d_refine, int refine_cap, int nframes, int total_tiles,
+                          int num_sms, cudaStream_t stream)
 {
     const int grad = method_grad(m);
     KernelFn fn = kernel_for(kind, grad, method_phi(m), cfg);
@@ -302,13 +309,20 @@ tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDes
     KernelFn rf = nullptr;
     if (grad != GRAD_PLANEPCA && !refines_in_place(cfg) && !(rf = refiner_for(kind, grad, method_phi(m))))
         return TFN_ERR_UNSUPPORTED;
+    // its grid: the flagged pixels (about one per thousand on noisy frames),
+    // as many threads as fit on the GPU at once: each refines its pixels one
+    // after another, so a list that fits in one round costs one pixel's latency
+    int rf_per_sm = 1;
+    if (rf && !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rf_per_sm, (const void *)rf, kRefineThreads, 0),
+                       "cudaOccupancyMaxActiveBlocksPerMultiprocessor(refine)"))
+        return TFN_ERR_CUDA;
     LaunchArgs a;
     a.frames = d_frames;
     a.maps = d_maps;
     a.status = d_status;
     a.rcount = (unsigned long long *)d_refine;
     a.rlist = (unsigned long long *)((char *)d_refine + 128);
-    a.rcap = kRefineCap;
+    a.rcap = refine_cap;
     a.nframes = nframes;
     a.total_tiles = total_tiles;
     a.out_fmt = m.output;
@@ -320,8 +334,8 @@ tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDes
     if (!cuda_ok(cudaLaunchKernel((const void *)fn, dim3(grid), dim3(threads), params, smem, stream),
                  "cudaLaunchKernel"))
         return TFN_ERR_CUDA;
-    // the flagged pixels: a few per thousand, spread over every SM
-    if (rf && !cuda_ok(cudaLaunchKernel((const void *)rf, dim3(4 * num_sms), dim3(kRefineThreads), params, 0, stream),
+    if (rf && !cuda_ok(cudaLaunchKernel((const void *)rf, dim3(std::max(1, rf_per_sm) * num_sms), dim3(kRefineThreads),
+                                        params, 0, stream),
                        "cudaLaunchKernel(refine)")) {
         cudaMemsetAsync(d_refine, 0, 128, stream);  // (what the refinement kernel would have zeroed)
         return TFN_ERR_CUDA;
@@ -449,7 +463,7 @@ tfn_status launch_group(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_me
     if (!s.done) TFN_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
 
     tfn_status lst = launch_normals(kind, m, cfg, slot_descs(s.dev), slot_maps(s.dev, s.cap), c->status,
-                                    slot_refine(s.dev, s.cap), n, total, c->num_sms, stream);
+                                    slot_refine(s.dev, s.cap), kRefineCap, n, total, c->num_sms, stream);
     if (lst) return lst;
     TFN_CUDA(cudaEventRecord(s.done, stream));
     return TFN_OK;
@@ -812,7 +826,7 @@ tfn_status tfn_plan_create(tfn_ctx *c, const tfn_frame *frames, int n, const tfn
             int total = 0;
             for (int k = i; k < j; ++k) total += frame_tiles(frames[k], cfg);
             lst = launch_normals(frames[i].input_type, *m, cfg, slot_descs(p->dev) + i, slot_maps(p->dev, n) + i,
-                                 c->status, slot_refine(p->dev, n), j - i, total, c->num_sms, cs);
+                                 c->status, slot_refine(p->dev, n), kRefineCap, j - i, total, c->num_sms, cs);
             i = j;
         }
         if (!cuda_ok(cudaStreamEndCapture(cs, &p->graph), "cudaStreamEndCapture") && lst == TFN_OK) lst = TFN_ERR_CUDA;

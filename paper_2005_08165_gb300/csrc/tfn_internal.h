@@ -28,6 +28,12 @@ enum Grad {
 enum Phi { PHI_MEAN = 0, PHI_MEDIAN = 1, PHI_COUNT = 2 };
 enum OutFmt { OUT_F32 = 0, OUT_F16 = 1, OUT_BF16 = 2, OUT_F16X4 = 3, OUT_BF16X4 = 4, OUT_OCT16 = 5 };
 
+// The FD gradients of the mean on depth: compensated quotients (false), or
+// one-pass quotients within 5u whose error the mean's bound carries (true).
+// The one-pass form saves arithmetic and flags about three times as many
+// pixels for the double-float pass on noisy frames.
+constexpr bool kFdOnePassMean = true;
+
 // Device status bits written by kernels.
 enum : uint32_t { DEVERR_TMA_WAIT = 1u };
 
@@ -73,10 +79,15 @@ struct LaunchArgs {
 // The refinement list of one launch: a 128-byte header (the entry count,
 // then the refinement kernel's finished-block counter; both zero between
 // launches: zeroed at allocation, and again by the refinement kernel's last
-// block), then kRefineCap entries.  Every launch owns one (context slots,
-// plans, the allocation-free scratch).
-constexpr int kRefineCap = 65536;
-constexpr size_t kRefineListBytes = 128 + (size_t)kRefineCap * 8;
+// block), then its entries.  Every launch owns one: context slots and plans
+// hold kRefineCap entries (2 MB, about 3 per thousand pixels of a 256-frame
+// 480x640 batch), the allocation-free scratch kNoallocRefineCap.  A launch
+// that flags more pixels than its list holds still refines them all (the
+// refinement kernel then scans the masks).
+constexpr int kRefineCap = 262144;
+constexpr int kNoallocRefineCap = 65536;
+constexpr size_t refine_list_bytes(int cap) { return 128 + (size_t)cap * 8; }
+constexpr size_t kRefineListBytes = refine_list_bytes(kRefineCap);
 constexpr int kRefineThreads = 128;
 
 // Work-item shapes the kernels are compiled for.  An item is a band of tw =
@@ -124,10 +135,21 @@ constexpr bool grad_is_sep5(int grad) { return grad >= GRAD_SEP5 && grad <= GRAD
 // derivative ring a third stage makes shared memory the occupancy limit
 // (2 CTAs = 8 warps per SM instead of the 12 their registers allow), and a
 // chunk of 8 rows takes far longer to compute than one copy takes to land.
-constexpr int cfg_nst(int c, int grad) { return grad_is_sep5(grad) && kCfgs[c].nst > 2 ? 2 : kCfgs[c].nst; }
+// The FD kernels keep 2 as well: with their carry buffer (below) 3 stages
+// would make shared memory the occupancy limit.
+constexpr int cfg_nst(int c, int grad)
+{
+    return (grad_is_sep5(grad) || grad == GRAD_FD) && kCfgs[c].nst > 2 ? 2 : kCfgs[c].nst;
+}
+// The FD kernels keep each lane's carry from one row to the next (the rho of
+// the up, up-left and up-right neighbours and their count, 8 floats per
+// pixel pair) in shared memory rather than in registers: 2 pairs x 2 x 16
+// bytes per lane.
+constexpr size_t kFdCarryBytes = 2 * 2 * 32 * 16;
 inline size_t smem_bytes(int kind, int c, int grad)
 {
-    return (size_t)cta_warps(c, grad) * (cfg_nst(c, grad) * stage_stride(kind, c) + (grad_is_sep5(grad) ? kSep5RingBytes : 0)) +
+    return (size_t)cta_warps(c, grad) * (cfg_nst(c, grad) * stage_stride(kind, c) + (grad_is_sep5(grad) ? kSep5RingBytes : 0) +
+                                         (grad == GRAD_FD ? kFdCarryBytes : 0)) +
            128;
 }
 // The profiles (d1 d2 s0 s1 s2) of a 5x5 filter: the named members' fixed
@@ -165,9 +187,9 @@ float refine_threshold(const tfn_frame &f, int grad, int phi);
 tfn_status encode_map(CUtensorMap *map, const tfn_frame &f, int cfg);
 FrameDesc describe_frame(const tfn_frame &f, int cfg, const tfn_method &m, int tile_begin);
 int frame_tiles(const tfn_frame &f, int cfg);
-// d_refine: the launch's refinement list (kRefineListBytes, 128-byte aligned).
+// d_refine: the launch's refinement list (refine_list_bytes(refine_cap), 128-byte aligned).
 tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
-                          uint32_t *d_status, void *d_refine, int nframes, int total_tiles, int num_sms,
-                          cudaStream_t stream);
+                          uint32_t *d_status, void *d_refine, int refine_cap, int nframes, int total_tiles,
+                          int num_sms, cudaStream_t stream);
 
 }  // namespace tfn

@@ -129,6 +129,25 @@ __device__ __forceinline__ df df_div(df a, df b)
 
 __device__ __forceinline__ float df_val(df a) { return __fadd_rn(a.h, a.l); }
 
+// ------------------------------------------------------------ pixel pairs
+//
+// The FD kernels write a lane's four pixels as two pairs (see row_step_fd2).
+// An f2 holds one value of each pixel of a pair, and these helpers apply the
+// same correctly rounded operation to both: two scalar operations each,
+// never contracted or reassociated, so a pair computes exactly what two
+// scalar pixels would.
+typedef float2 f2;
+
+__device__ __forceinline__ f2 pk(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ f2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float lane_of(f2 a, int l) { return l == 0 ? a.x : a.y; }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return pk(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return pk(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return pk(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return pk(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y)); }
+__device__ __forceinline__ f2 neg2(f2 a) { return pk(-a.x, -a.y); }
+__device__ __forceinline__ f2 rcp2(f2 a) { return pk(rcp_approx(a.x), rcp_approx(a.y)); }
+
 // w_b - w_a for depths a, b > 0, i.e. (a - b) / (a b), as h + l with error
 // ~u^2: exact difference (TwoSum), exact product (FMA), and the division
 // residual d - q P - q Pe folded into the low part.
@@ -360,6 +379,16 @@ __device__ __forceinline__ EdgeR edge_recip(float delta)
     return {r, __fmul_rn(delta, r)};
 }
 
+// edge_recip on a pair of edges.
+struct EdgeR2 {
+    f2 r, k;
+};
+__device__ __forceinline__ EdgeR2 edge_recip2(f2 delta)
+{
+    const f2 r = mul2(delta, rcp2(fma2(delta, delta, bc(kEdgeEps))));
+    return {r, mul2(delta, r)};
+}
+
 // A hole's stand-in value, 2^100.  Its difference with any valid sample
 // (<= 2^16) has a square that overflows to +inf, whose reciprocal is 0, so an
 // edge that touches a hole gets r = 0 and k = 0 with no test (two holes give
@@ -406,11 +435,48 @@ struct Row {
     float wh[kW ? 6 : 1], wl[kW ? 6 : 1];
 };
 
+// FD rows hold the samples as the pairs of pixel pairs (1, 3) and (2, 4) of
+// row_step_fd2: p[0] = (z0, z2), p[1] = (z1, z3), p[2] = (z2, z4),
+// p[3] = (z3, z5).  (z2 and z3 sit in two pairs each.)
+template <int KIND>
+struct Row<KIND, GRAD_FD> {
+    static constexpr bool kW = false;
+    f2 p[4];
+};
+
+// Sample c (0 .. 5) of a row.
+template <int KIND, int GRAD>
+__device__ __forceinline__ float sample(const Row<KIND, GRAD> &R, int c)
+{
+    return R.z[c];
+}
+template <int KIND>
+__device__ __forceinline__ float sample(const Row<KIND, GRAD_FD> &R, int c)
+{
+    return c == 0 ? R.p[0].x : c == 1 ? R.p[1].x : c == 2 ? R.p[2].x : c == 3 ? R.p[1].y : c == 4 ? R.p[2].y : R.p[3].y;
+}
+
+// Fills a row with its 6 decoded samples.
+template <int KIND, int GRAD>
+__device__ __forceinline__ void set_row(Row<KIND, GRAD> &R, const float (&z)[6])
+{
+#pragma unroll
+    for (int c = 0; c < 6; ++c) R.z[c] = z[c];
+}
+template <int KIND>
+__device__ __forceinline__ void set_row(Row<KIND, GRAD_FD> &R, const float (&z)[6])
+{
+    R.p[0] = pk(z[0], z[2]);
+    R.p[1] = pk(z[1], z[3]);
+    R.p[2] = pk(z[2], z[4]);
+    R.p[3] = pk(z[3], z[5]);
+}
+
 template <int KIND, int GRAD>
 __device__ __forceinline__ void hole_row(Row<KIND, GRAD> &R)
 {
-#pragma unroll
-    for (int c = 0; c < 6; ++c) R.z[c] = kHole;
+    const float z[6] = {kHole, kHole, kHole, kHole, kHole, kHole};
+    set_row(R, z);
     if constexpr (Row<KIND, GRAD>::kW) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) R.wh[c] = R.wl[c] = 0.f;
@@ -440,39 +506,55 @@ __device__ __forceinline__ void load_row(const unsigned char *stage, int jr, int
         raw[4] = from_bits16<T>(q.y >> 16);
     }
     raw[5] = p[4];
+    float z[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) R.z[c] = decode<KIND>(raw[c]);
+    for (int c = 0; c < 6; ++c) z[c] = decode<KIND>(raw[c]);
+    set_row(R, z);
     if constexpr (Row<KIND, GRAD>::kW) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            const float wh = rcp_approx(R.z[c]);
+            const float wh = rcp_approx(z[c]);
             R.wh[c] = wh;
-            R.wl[c] = __fmul_rn(__fmaf_rn(-wh, R.z[c], 1.f), wh);
+            R.wl[c] = __fmul_rn(__fmaf_rn(-wh, z[c], 1.f), wh);
         }
     }
 }
 
-// FD gradient term between taps a (the -1 side) and b (the +1 side), as
-// h + l.  Depth: 1/Z_b - 1/Z_a = d / P with d = Z_a - Z_b (exact for
-// neighbouring depths within a factor 2) and P = Z_a Z_b; h = d rcp(P), and l
-// is h's residual against the exact product P + Pe divided by P, so h + l is
-// the quotient to about u^2 relative, as a difference of compensated
-// reciprocals would be.  h is 0 exactly when the taps are equal.  Disparity:
-// d_b - d_a (exact for integer samples; TwoSum for float ones).
-template <int KIND>
-__device__ __forceinline__ df fd_term(float a, float b)
+// The FD gradient term between taps a (the -1 side) and b (the +1 side) of
+// both pixels of a pair, as h + l.  Depth: 1/Z_b - 1/Z_a = d / P with d =
+// Z_a - Z_b (exact for neighbouring depths within a factor 2) and P = Z_a
+// Z_b; h = d rcp(P), and l is h's residual against the exact product P + Pe
+// divided by P, so h + l is the quotient to about u^2 relative, as a
+// difference of compensated reciprocals would be; h is 0 exactly when the
+// taps are equal.  With ONE_PASS (the mean on depth when kFdOnePassMean is
+// set) only h: within 5u of the quotient (the difference exact or rounded
+// once, the product rounded once, the reciprocal within one ulp, the product
+// with it rounded once; no operand or result subnormal for samples in
+// [2^-16, 2^16]).  Disparity: d_b - d_a (exact for integer samples; TwoSum for
+// float ones).
+struct df2 {
+    f2 h, l;
+};
+template <int KIND, bool ONE_PASS>
+__device__ __forceinline__ df2 fd_term2(f2 a, f2 b)
 {
     if constexpr (KindTraits<KIND>::disparity) {
-        if constexpr (KindTraits<KIND>::exact_diff) return {__fsub_rn(b, a), 0.f};
-        return two_sum(b, -a);
+        if constexpr (KindTraits<KIND>::exact_diff) return {sub2(b, a), bc(0.f)};
+        // TwoSum(b, -a): s = b - a, bb = s - b, e = (b - (s - bb)) - (a + bb)
+        const f2 sm = sub2(b, a);
+        const f2 bb = sub2(sm, b);
+        return {sm, sub2(sub2(b, sub2(sm, bb)), add2(a, bb))};
+    } else if constexpr (ONE_PASS) {
+        return {mul2(sub2(a, b), rcp2(mul2(a, b))), bc(0.f)};
     } else {
-        const float d = __fsub_rn(a, b);
-        const float P = __fmul_rn(a, b);
-        const float Pe = __fmaf_rn(a, b, -P);
-        const float r = rcp_approx(P);
-        const float q = __fmul_rn(d, r);
-        const float e = __fmaf_rn(-q, Pe, __fmaf_rn(-q, P, d));
-        return {q, __fmul_rn(e, r)};
+        const f2 d = sub2(a, b);
+        const f2 P = mul2(a, b);
+        const f2 Pe = fma2(a, b, neg2(P));
+        const f2 r = rcp2(P);
+        const f2 q = mul2(d, r);
+        const f2 nq = neg2(q);
+        const f2 e = fma2(nq, Pe, fma2(nq, P, d));
+        return {q, mul2(e, r)};
     }
 }
 
@@ -533,13 +615,63 @@ __device__ __forceinline__ void carry_down(const Row<KIND, GRAD> &C, const Row<K
     }
 }
 
-// One row of a lane's 4 pixels (Sec. III end to end), given the sample rows
-// above (P), at (C) and below (N) and the carry from the row above; leaves
-// the carry for the next row in `cy`.  Outputs the normal components, the
-// mask bits and the bits of the pixels whose FP32 error bound is too loose.
-// Every product is an explicit __fmul_rn and every fused multiply-add an
-// explicit __fmaf_rn (never a contraction), so a pixel's bits do not depend
-// on how the compiler schedules this code in a given instantiation.
+// FD: the carry of the pixel pairs (pair 0: pixels 1 and 3, pair 1: pixels
+// 2 and 4): the magnitudes B of the rho of the up, up-left and up-right
+// neighbours (rho = -B on depth, +B on disparity) and how many of the three
+// are kept.  It lives in shared memory, this lane's slots of its warp's
+// buffer (kFdCarryBytes): pair h at q[64 h] = (B_u, B_ul) and q[64 h + 32] =
+// (B_ur, k_u), so that a pair's carry occupies registers only between its
+// load and its store in row_step_fd2.
+struct UpCarry2 {
+    float4 *q;
+    __device__ __forceinline__ void get(int h, f2 &bu, f2 &bul, f2 &bur, f2 &ku) const
+    {
+        const float4 a = q[64 * h], b = q[64 * h + 32];
+        bu = pk(a.x, a.y);
+        bul = pk(a.z, a.w);
+        bur = pk(b.x, b.y);
+        ku = pk(b.z, b.w);
+    }
+    __device__ __forceinline__ void put(int h, f2 bu, f2 bul, f2 bur, f2 ku) const
+    {
+        q[64 * h] = make_float4(bu.x, bu.y, bul.x, bul.y);
+        q[64 * h + 32] = make_float4(bur.x, bur.y, ku.x, ku.y);
+    }
+};
+template <int GRAD>
+struct CarryOf {
+    typedef UpCarry type;
+};
+template <>
+struct CarryOf<GRAD_FD> {
+    typedef UpCarry2 type;
+};
+
+// carry_down for FD rows.  Edge p -> q with r = 1/(s_q - s_p): seen from q,
+// rho = -s_p r on depth and s_q r on disparity (rho_bwd).
+template <int KIND>
+__device__ __forceinline__ void carry_down(const Row<KIND, GRAD_FD> &C, const Row<KIND, GRAD_FD> &N, UpCarry2 &cy)
+{
+    constexpr bool disp = KindTraits<KIND>::disparity;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const f2 Cl = C.p[h], Cc = C.p[1 + h], Cr = C.p[2 + h], Nc = N.p[1 + h];
+        const EdgeR2 v = edge_recip2(sub2(Nc, Cc));  // (y, c)   -> (y+1, c)
+        const EdgeR2 d = edge_recip2(sub2(Nc, Cl));  // (y, c-1) -> (y+1, c)
+        const EdgeR2 a = edge_recip2(sub2(Nc, Cr));  // (y, c+1) -> (y+1, c)
+        cy.put(h, mul2(disp ? Nc : Cc, v.r), mul2(disp ? Nc : Cl, d.r), mul2(disp ? Nc : Cr, a.r),
+               add2(add2(v.k, d.k), a.k));
+    }
+}
+
+// One row of a lane's 4 pixels (Sec. III end to end) for the filters other
+// than FD (those run row_step_fd2), given the sample rows above (P), at (C)
+// and below (N) and the carry from the row above; leaves the carry for the
+// next row in `cy`.  Outputs the normal components, the mask bits and the
+// bits of the pixels whose FP32 error bound is too loose.  Every product is
+// an explicit __fmul_rn and every fused multiply-add an explicit __fmaf_rn
+// (never a contraction), so a pixel's bits do not depend on how the compiler
+// schedules this code in a given instantiation.
 template <int KIND, int GRAD, int PHI>
 __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIND, GRAD> &C, const Row<KIND, GRAD> &N,
                                          UpCarry &cy, const float (&uc)[4], float vc, float fx, float fy, float thr,
@@ -547,6 +679,7 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
                                          float (&ox)[4], float (&oy)[4], float (&oz)[4], uint32_t &mword,
                                          unsigned &rbits)
 {
+    static_assert(GRAD != GRAD_FD, "the FD filter runs row_step_fd2");
     // edges of this row (c -> c+1) and to the row below, computed pixel by
     // pixel: pixel c needs those of columns c-1 and c only
     EdgeR h[5], ed[5], ea[5];
@@ -575,11 +708,7 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
         // gradients (as h + l), the special case and evaluability
         df Gu, Gv;
         bool ev_ok;
-        if constexpr (GRAD == GRAD_FD) {
-            Gu = fd_term<KIND>(C.z[c - 1], C.z[c + 1]);
-            Gv = fd_term<KIND>(P.z[c], N.z[c]);
-            ev_ok = fmaxf(fmaxf(fmaxf(C.z[c - 1], zi), C.z[c + 1]), fmaxf(P.z[c], N.z[c])) <= kValidHi;
-        } else if constexpr (GRAD == GRAD_WEIGHTED) {
+        if constexpr (GRAD == GRAD_WEIGHTED) {
             const float w0 = wts[0], w1 = wts[1], w2 = wts[2];
             Gu = filter_sum_w(tap_diff(P, c - 1, P, c + 1), tap_diff(C, c - 1, C, c + 1), tap_diff(N, c - 1, N, c + 1),
                               w0, w1, w2);
@@ -611,11 +740,7 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
         }
         // Sec. III special case: both gradients exactly zero (an h + l pair
         // vanishes only when both parts do)
-        bool flat;
-        if constexpr (GRAD == GRAD_FD)
-            flat = Gu.h == 0.f && Gv.h == 0.f;  // an FD term's low part is 0 whenever its high part is
-        else
-            flat = Gu.h == 0.f && Gu.l == 0.f && Gv.h == 0.f && Gv.l == 0.f;
+        bool flat = Gu.h == 0.f && Gu.l == 0.f && Gv.h == 0.f && Gv.l == 0.f;
         // (a non-evaluable pixel's gradient may be NaN, from two hole taps: keep n' finite)
         const float gu = ev_ok ? __fadd_rn(Gu.h, Gu.l) : 0.f, gv = ev_ok ? __fadd_rn(Gv.h, Gv.l) : 0.f;
         // numerators of the diagonal pairs from the parts (they can cancel)
@@ -696,6 +821,184 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
         cy.rul[k] = rho_bwd<KIND>(C.z[c - 1], N.z[c], ed[c - 1].r);
         cy.rur[k] = rho_bwd<KIND>(C.z[c + 1], N.z[c], ea[c].r);
         cy.ku[k] = __fadd_rn(__fadd_rn(ev.k, ed[c - 1].k), ea[c].k);
+    }
+}
+
+// row_step for the FD filter, two pixels at a time.  A lane's pixels 1 and 3
+// form one pair and pixels 2 and 4 the other: their windows sit on the same
+// sample pairs (Row<KIND, GRAD_FD>), so each edge, rho, gradient and sum is
+// written once for a pair (add2, mul2, fma2), and the pair's carry lives in
+// shared memory between rows (UpCarry2).  With compensated gradients the
+// operations and their order are those of row_step, bit for bit; the mean's
+// one-pass gradients (kFdOnePassMean) change only the gradient quotient and
+// the bound.
+//
+// rho of the neighbours: an edge p -> q with r = 1/(s_q - s_p) gives p the
+// rho s_q r (depth) or -s_p r (disparity), and q the rho -s_p r or s_q r; the
+// pairs keep the magnitudes F (forward: right, down, down-right, down-left)
+// and B (backward: left, up, up-left, up-right), with rho = sF forward and
+// -sB backward, s = +1 on depth and -1 on disparity.  Then rho_j - rho_-j of
+// the pairs (right, left), (down, up), (down-right, up-left) is s (F + B), and
+// that of (up-right, down-left) -s (B + F): the candidate sum is s T with T
+// below (n3n = G_v - G_u = -n3), and the candidates are s times the products
+// num F or num B.
+template <int KIND, int PHI>
+__device__ __forceinline__ void row_step_fd2(const Row<KIND, GRAD_FD> &P, const Row<KIND, GRAD_FD> &C,
+                                             const Row<KIND, GRAD_FD> &N, UpCarry2 &cy, const f2 (&uc2)[2], float vc,
+                                             float fx, float fy, float thr, float (&ox)[4], float (&oy)[4],
+                                             float (&oz)[4], uint32_t &mword, unsigned &rbits)
+{
+    constexpr bool disp = KindTraits<KIND>::disparity;
+    constexpr bool one_pass = kFdOnePassMean && PHI == PHI_MEAN && !disp;
+    const f2 vc2 = bc(vc), fx2 = bc(fx), fy2 = bc(fy);
+    // the edges to column c-1 of pixels c = 1, 3 (the next pair's come from this pair)
+    EdgeR2 ehm = edge_recip2(sub2(C.p[1], C.p[0]));  // (y, c-1) -> (y, c)
+    EdgeR2 edm = edge_recip2(sub2(N.p[1], C.p[0]));  // (y, c-1) -> (y+1, c)
+    EdgeR2 eam = edge_recip2(sub2(N.p[0], C.p[1]));  // (y, c)   -> (y+1, c-1)
+    mword = 0;
+    rbits = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const f2 Cl = C.p[h], Cc = C.p[1 + h], Cr = C.p[2 + h];
+        const f2 Nl = N.p[h], Nc = N.p[1 + h], Nr = N.p[2 + h], Pc = P.p[1 + h];
+        const EdgeR2 eh = edge_recip2(sub2(Cr, Cc));  // (y, c)   -> (y, c+1)
+        const EdgeR2 ed = edge_recip2(sub2(Nr, Cc));  // (y, c)   -> (y+1, c+1)
+        const EdgeR2 ea = edge_recip2(sub2(Nc, Cr));  // (y, c+1) -> (y+1, c)
+        const EdgeR2 ev = edge_recip2(sub2(Nc, Cc));  // (y, c)   -> (y+1, c)
+        const f2 Fr = mul2(disp ? Cc : Cr, eh.r);
+        const f2 Bl = mul2(disp ? Cc : Cl, ehm.r);
+        const f2 Fd = mul2(disp ? Cc : Nc, ev.r);
+        const f2 Fdr = mul2(disp ? Cc : Nr, ed.r);
+        const f2 Fdl = mul2(disp ? Cc : Nl, eam.r);
+        f2 Bu, Bul, Bur, ku;
+        cy.get(h, Bu, Bul, Bur, ku);
+        const f2 m = add2(add2(add2(eh.k, ehm.k), add2(ev.k, ed.k)), add2(eam.k, ku));
+
+        // gradients (as h + l), evaluability and the special case, per pixel
+        const df2 Gu = fd_term2<KIND, one_pass>(Cl, Cr), Gv = fd_term2<KIND, one_pass>(Pc, Nc);
+        bool ev_ok[2], flat[2];
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            ev_ok[l] = fmaxf(fmaxf(fmaxf(lane_of(Cl, l), lane_of(Cc, l)), lane_of(Cr, l)),
+                             fmaxf(lane_of(Pc, l), lane_of(Nc, l))) <= kValidHi;
+            // Sec. III special case: both gradients exactly zero (an FD term's
+            // low part is 0 whenever its high part is)
+            flat[l] = lane_of(Gu.h, l) == 0.f && lane_of(Gv.h, l) == 0.f;
+        }
+        f2 gu, gv, n2, n3n;
+        if constexpr (one_pass) {
+            // (one-pass quotients are finite on hole taps; a non-evaluable
+            // pixel's output is zeroed through rs below)
+            gu = Gu.h;
+            gv = Gv.h;
+            n2 = add2(gu, gv);
+            n3n = sub2(gv, gu);
+        } else {
+            // (a non-evaluable pixel's gradient may be NaN, from two hole taps: keep n' finite)
+            const f2 su = add2(Gu.h, Gu.l), sv = add2(Gv.h, Gv.l);
+            gu = pk(ev_ok[0] ? su.x : 0.f, ev_ok[1] ? su.y : 0.f);
+            gv = pk(ev_ok[0] ? sv.x : 0.f, ev_ok[1] ? sv.y : 0.f);
+            // numerators of the diagonal pairs from the parts (they can cancel)
+            n2 = add2(add2(Gu.h, Gv.h), add2(Gu.l, Gv.l));
+            n3n = add2(sub2(Gv.h, Gu.h), sub2(Gv.l, Gu.l));
+        }
+
+        f2 mF, scale;
+        float mbound[2];
+        if constexpr (PHI == PHI_MEAN) {
+            // sum over the pairs (j, -j) of num_p (rho_j - rho_-j) = s T,
+            // carried unnormalised: n' scaled by m > 0 keeps its direction
+            const f2 T = fma2(gu, add2(Fr, Bl), fma2(gv, add2(Fd, Bu), fma2(n2, add2(Fdr, Bul), mul2(n3n, add2(Bur, Fdl)))));
+            mF = disp ? neg2(T) : T;
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                // bound of the candidate sum's rounding: sum_p |num_p| (|rho_j| + |rho_-j|);
+                // one-pass gradients (within 5u each) add up to 5u (|G_u| + |G_v|)
+                // to a diagonal numerator: its weight grows by (|G_u| + |G_v|) / 4
+                float w2 = fabsf(lane_of(n2, l)), w3 = fabsf(lane_of(n3n, l));
+                if constexpr (one_pass) {
+                    const float sg = __fadd_rn(fabsf(lane_of(gu, l)), fabsf(lane_of(gv, l)));
+                    w2 = __fmaf_rn(0.25f, sg, w2);
+                    w3 = __fmaf_rn(0.25f, sg, w3);
+                }
+                mbound[l] = __fmaf_rn(fabsf(lane_of(gu, l)), __fadd_rn(fabsf(lane_of(Fr, l)), fabsf(lane_of(Bl, l))),
+                            __fmaf_rn(fabsf(lane_of(gv, l)), __fadd_rn(fabsf(lane_of(Fd, l)), fabsf(lane_of(Bu, l))),
+                            __fmaf_rn(w2, __fadd_rn(fabsf(lane_of(Fdr, l)), fabsf(lane_of(Bul, l))),
+                                      __fmul_rn(w3, __fadd_rn(fabsf(lane_of(Bur, l)), fabsf(lane_of(Fdl, l)))))));
+            }
+            scale = m;
+        } else {
+            // the candidates, s times these products
+            const f2 pr[8] = {mul2(gu, Fr), mul2(gu, Bl), mul2(gv, Fd), mul2(gv, Bu),
+                              mul2(n2, Fdr), mul2(n2, Bul), mul2(n3n, Bur), mul2(n3n, Fdl)};
+            const f2 mag[8] = {Fr, Bl, Fd, Bu, Fdr, Bul, Bur, Fdl};
+            float med[2];
+#pragma unroll
+            for (int l = 0; l < 2; ++l) {
+                float sv[8];
+                unsigned sgn = 0;  // sign bit of the next sentinel: +inf, -inf, +inf, ...
+                int cnt = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const bool kept = lane_of(mag[q], l) != 0.f;
+                    cnt += kept;
+                    sv[q] = kept ? lane_of(pr[q], l) : __uint_as_float(0x7f800000u | sgn);
+                    sgn ^= kept ? 0u : 0x80000000u;
+                }
+#define TFN_CE(i, j)                           \
+    {                                          \
+        const float lo_ = fminf(sv[i], sv[j]); \
+        sv[j] = fmaxf(sv[i], sv[j]);           \
+        sv[i] = lo_;                           \
+    }
+                TFN_CE(0, 2) TFN_CE(1, 3) TFN_CE(4, 6) TFN_CE(5, 7)
+                TFN_CE(0, 4) TFN_CE(1, 5) TFN_CE(2, 6) TFN_CE(3, 7)
+                TFN_CE(0, 1) TFN_CE(2, 3) TFN_CE(4, 5) TFN_CE(6, 7)
+                TFN_CE(2, 4) TFN_CE(3, 5)
+                TFN_CE(1, 4) TFN_CE(3, 6)
+                TFN_CE(1, 2) TFN_CE(3, 4) TFN_CE(5, 6)
+#undef TFN_CE
+                // (the median of s times the products is s times theirs: the
+                // sentinels keep the middle slots on the kept candidates)
+                const bool odd = cnt & 1;
+                const float md = odd ? sv[3] : __fmul_rn(0.5f, __fadd_rn(sv[3], sv[4]));
+                med[l] = disp ? -md : md;
+                mbound[l] = odd ? fabsf(sv[3]) : fmaxf(fabsf(sv[3]), fabsf(sv[4]));
+            }
+            mF = pk(med[0], med[1]);
+            scale = bc(1.f);
+        }
+        const f2 A = fma2(uc2[h], gu, mul2(vc2, gv));
+        const f2 nxp = PHI == PHI_MEAN ? mul2(mul2(scale, fx2), gu) : mul2(fx2, gu);
+        const f2 nyp = PHI == PHI_MEAN ? mul2(mul2(scale, fy2), gv) : mul2(fy2, gv);
+        const f2 Q = PHI == PHI_MEAN ? fma2(scale, A, mF) : add2(A, mF);  // -n_z'
+        // (a non-evaluable pixel's median may be a +-inf sentinel: keep n' finite so that rs = 0 zeroes it)
+        const f2 nzp = pk((flat[0] || !ev_ok[0]) ? 1.f : -Q.x, (flat[1] || !ev_ok[1]) ? 1.f : -Q.y);
+        const f2 nn = fma2(nxp, nxp, fma2(nyp, nyp, mul2(nzp, nzp)));
+        const f2 rs = pk(ev_ok[0] ? rsqrt_approx(nn.x) : 0.f, ev_ok[1] ? rsqrt_approx(nn.y) : 0.f);
+        const f2 lim = mul2(bc(thr), mul2(nn, rs));
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const int k = h + 2 * l;
+            const float r = lane_of(rs, l);
+            // refine unless bound <= thr |n'|; written so that a NaN (|n'|
+            // overflowed) also refines, and thr < 0 refines every pixel
+            const bool refine = ev_ok[l] && !flat[l] && !(mbound[l] <= lane_of(lim, l));
+            // -n'/|n'|, with +0 (not -0) for zero components and for non-evaluable pixels
+            ox[k] = __fmaf_rn(-lane_of(nxp, l), r, 0.f);
+            oy[k] = __fmaf_rn(-lane_of(nyp, l), r, 0.f);
+            oz[k] = __fmaf_rn(-lane_of(nzp, l), r, 0.f);
+            mword |= ev_ok[l] ? 1u << (8 * k) : 0u;
+            rbits |= refine ? 1u << k : 0u;
+        }
+
+        // the carry for the pixels below: their up, up-left and up-right neighbours
+        cy.put(h, mul2(disp ? Nc : Cc, ev.r), mul2(disp ? Nc : Cl, edm.r), mul2(disp ? Nc : Cr, ea.r),
+               add2(add2(ev.k, edm.k), ea.k));
+        // this pair's edges to column c+1 are the next pair's to column c-1
+        ehm = eh;
+        edm = ed;
+        eam = ea;
     }
 }
 
@@ -1073,52 +1376,43 @@ __device__ __forceinline__ uint32_t oct16(float x, float y, float z)
     return ((uint32_t)cx & 0xffffu) | ((uint32_t)cy << 16);
 }
 
-// Where an item's optional point cloud goes.
-struct PtsDesc {
-    char *pts;
-    int64_t pitch, plane;
-};
-
 // Back-projected points of 4 consecutive pixels of row v (n of them inside
-// the frame): Z = the sample (disparity: ztc / sample), X = Z (u - u0)/fx,
-// Y = Z (v - v0)/fy with ucf = (u - u0)/fx per column and vcf = (v - v0)/fy;
-// holes give (0, 0, 0).
-// (out of line: the row loop's code stays small; the samples travel by value)
+// the frame f): Z = the sample (disparity: ztc / sample), X = Z (u - u0)/fx,
+// Y = Z (v - v0)/fy; holes give (0, 0, 0).  Out of line, reading what it
+// needs from the frame's descriptor, so that the row loop keeps neither the
+// code nor the registers of this rare output.
 template <int KIND>
-__device__ __noinline__ void store_points4_cold(PtsDesc p, int u, int v, int n, float z1, float z2, float z3, float z4,
-                                                float uf0, float uf1, float uf2, float uf3, float vcf, float ztc);
-template <int KIND>
-__device__ __forceinline__ void store_points4(const PtsDesc &p, int u, int v, int n, const float (&z)[6],
-                                              const float (&ucf)[4], float vcf, float ztc)
+__device__ __noinline__ void store_points4(const FrameDesc *f, int u, int v, int n, float z1, float z2, float z3,
+                                           float z4)
 {
-    store_points4_cold<KIND>(p, u, v, n, z[1], z[2], z[3], z[4], ucf[0], ucf[1], ucf[2], ucf[3], vcf, ztc);
-}
-template <int KIND>
-__device__ __noinline__ void store_points4_cold(PtsDesc p, int u, int v, int n, float z1, float z2, float z3, float z4,
-                                                float uf0, float uf1, float uf2, float uf3, float vcf, float ztc)
-{
-    const float z[6] = {0.f, z1, z2, z3, z4, 0.f}, ucf[4] = {uf0, uf1, uf2, uf3};
+    char *pts = (char *)__ldg((const unsigned long long *)&f->pts);
+    const int64_t pitch = __ldg(&f->pts_pitch), plane = __ldg(&f->pts_plane);
+    const float fx = __ldg(&f->fx), fy = __ldg(&f->fy), u0 = __ldg(&f->u0), v0 = __ldg(&f->v0);
+    const float ztc = __ldg(&f->ztc);
+    const float z[4] = {z1, z2, z3, z4};
+    const float vcf = __fdiv_rn(__fsub_rn((float)v, v0), fy);
     float X[4], Y[4], Z[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const float s = z[k + 1];
+        const float ucf = __fdiv_rn(__fsub_rn((float)(u + k), u0), fx);
+        const float s = z[k];
         const bool ok = s <= kValidHi;
         const float Zk = KindTraits<KIND>::disparity ? __fdiv_rn(ztc, s) : s;
-        X[k] = ok ? __fmul_rn(Zk, ucf[k]) : 0.f;
+        X[k] = ok ? __fmul_rn(Zk, ucf) : 0.f;
         Y[k] = ok ? __fmul_rn(Zk, vcf) : 0.f;
         Z[k] = ok ? Zk : 0.f;
     }
-    char *row = p.pts + (int64_t)v * p.pitch;
+    char *row = pts + (int64_t)v * pitch;
     if (n == 4) {
         __stcs(reinterpret_cast<float4 *>(row + (int64_t)u * 4), make_float4(X[0], X[1], X[2], X[3]));
-        __stcs(reinterpret_cast<float4 *>(row + p.plane + (int64_t)u * 4), make_float4(Y[0], Y[1], Y[2], Y[3]));
-        __stcs(reinterpret_cast<float4 *>(row + 2 * p.plane + (int64_t)u * 4), make_float4(Z[0], Z[1], Z[2], Z[3]));
+        __stcs(reinterpret_cast<float4 *>(row + plane + (int64_t)u * 4), make_float4(Y[0], Y[1], Y[2], Y[3]));
+        __stcs(reinterpret_cast<float4 *>(row + 2 * plane + (int64_t)u * 4), make_float4(Z[0], Z[1], Z[2], Z[3]));
         return;
     }
     for (int k = 0; k < n; ++k) {
         reinterpret_cast<float *>(row)[u + k] = X[k];
-        reinterpret_cast<float *>(row + p.plane)[u + k] = Y[k];
-        reinterpret_cast<float *>(row + 2 * p.plane)[u + k] = Z[k];
+        reinterpret_cast<float *>(row + plane)[u + k] = Y[k];
+        reinterpret_cast<float *>(row + 2 * plane)[u + k] = Z[k];
     }
 }
 
@@ -1375,6 +1669,8 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
     unsigned char *ring = sbase + warp * NST * STRIDE;
     // (5x5 filters) this lane's slots of the per-warp ring of row derivatives and smoothings
     float4 *const dring = reinterpret_cast<float4 *>(sbase + NW * NST * STRIDE + warp * kSep5RingBytes) + lane;
+    // (FD) this lane's slots of the per-warp carry buffer
+    float4 *const fd_carry = reinterpret_cast<float4 *>(sbase + NW * NST * STRIDE + warp * kFdCarryBytes) + lane;
     if (lane == 0) {
 #pragma unroll
         for (int s = 0; s < NST; ++s) mbar_init(smem_addr(&full[warp][s]), 1);
@@ -1433,21 +1729,16 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
         const int H = __ldg(&f->H), W = __ldg(&f->W), txs = __ldg(&f->tiles_x);
         const float fx = __ldg(&f->fx), fy = __ldg(&f->fy), u0 = __ldg(&f->u0), v0 = __ldg(&f->v0);
         const float thr = refine_all ? -1.f : __ldg(&f->thr);
-        PtsDesc pts;
-        pts.pts = (char *)__ldg((const unsigned long long *)&f->pts);
-        pts.pitch = __ldg(&f->pts_pitch);
-        pts.plane = __ldg(&f->pts_plane);
+        const bool has_pts = __ldg((const unsigned long long *)&f->pts) != 0;  // (the fused point cloud)
         const float ztc = __ldg(&f->ztc);
         const float rfx = __frcp_rn(fx), rfy = __frcp_rn(fy);  // (PlanePCA)
         const int lt = t - __ldg(&f->tile_begin);
         const int x0 = (lt % txs) * 128 + 4 * lane, y0 = (lt / txs) * TH;
         const int nvalid = min(4, W - x0);  // pixels of this lane inside the frame (may be <= 0)
-        float uc[4], ucf[4];
+        float uc[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            uc[k] = __fsub_rn((float)(x0 + k), u0);
-            ucf[k] = __fdiv_rn(uc[k], fx);
-        }
+        for (int k = 0; k < 4; ++k) uc[k] = __fsub_rn((float)(x0 + k), u0);
+        const f2 uc2[2] = {pk(uc[0], uc[2]), pk(uc[1], uc[3])};  // (FD: the pixel pairs)
 
         // Sample row j (0 .. TH+2HR-1) of the item is image row y0 - HR + j;
         // rows at or past the bottom read as holes.  The rows arrive in
@@ -1489,7 +1780,8 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
         };
 
         unsigned long long pend_a = 0, pend_b = 0;  // (INPLACE) bit 4 s + k: row y0 + s, column x0 + k
-        UpCarry cy;
+        typename CarryOf<GRAD>::type cy;
+        if constexpr (GRAD == GRAD_FD) cy.q = fd_carry;
         // output row y0 + s from sample rows P (above), C and N (below); the
         // 5x5 filters' gradients come in gu, gv
         auto emit = [&](const R &P, const R &C, const R &N, int s, const df(&gu)[4], const df(&gv)[4]) {
@@ -1500,6 +1792,8 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
             if constexpr (GRAD == GRAD_PLANEPCA) {
                 pca_row<KIND, GRAD>(P, C, N, uc, __fsub_rn((float)y, v0), rfx, rfy, ztc, ox, oy, oz, mw);
                 rb = 0;
+            } else if constexpr (GRAD == GRAD_FD) {
+                row_step_fd2<KIND, PHI>(P, C, N, cy, uc2, __fsub_rn((float)y, v0), fx, fy, thr, ox, oy, oz, mw, rb);
             } else {
                 row_step<KIND, GRAD, PHI>(P, C, N, cy, uc, __fsub_rn((float)y, v0), fx, fy, thr, wts, gu, gv, ox, oy,
                                           oz, mw, rb);
@@ -1510,8 +1804,8 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
                 // (bit k of rb to bit 8k + 1), and listed for refine_kernel
                 if constexpr (!INPLACE) mw |= ((rb * 0x00204081u) & 0x01010101u) << 1;
                 store4(out, args.out_fmt, x0, y, nvalid, ox, oy, oz, mw);
-                if (pts.pts)  // the fused point cloud of this row
-                    store_points4<KIND>(pts, x0, y, nvalid, C.z, ucf, __fdiv_rn(__fsub_rn((float)y, v0), fy), ztc);
+                if (has_pts)  // the fused point cloud of this row
+                    store_points4<KIND>(f, x0, y, nvalid, sample(C, 1), sample(C, 2), sample(C, 3), sample(C, 4));
                 if constexpr (INPLACE) {  // (redone after the item)
                     if (s < 16)
                         pend_a |= (unsigned long long)rb << (4 * s);
@@ -1751,7 +2045,10 @@ __device__ __forceinline__ void refine_at(const LaunchArgs &args, int fi, int x,
 
 // The second kernel of a launch: the pixels normals_kernel flagged, from its
 // list, or (when the list overflowed) by a scan of every frame's mask for
-// bit 1.  Adds the number of refined pixels to status[1].
+// bit 1, 16 mask bytes per load (mask rows start on 16-byte boundaries and
+// their pitch is a multiple of 16, so a row's last load stays inside its
+// pitch; bytes past the frame's width are not pixels and are skipped).  Adds
+// the number of refined pixels to status[1].
 template <int KIND, int GRAD, int PHI>
 __global__ void __launch_bounds__(kRefineThreads) refine_kernel(const __grid_constant__ LaunchArgs args)
 {
@@ -1761,7 +2058,9 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(const __grid_con
     if (cnt <= (unsigned long long)args.rcap) {
         for (long long i = tid; i < (long long)cnt; i += nth) {
             const unsigned long long e = args.rlist[i];
-            refine_at<KIND, GRAD, PHI>(args, (int)(e >> 32), (int)(e & 0xffffu), (int)((e >> 16) & 0xffffu));
+            const int fi = (int)(e >> 32);
+            if (fi >= args.nframes) continue;  // (not an entry of this launch's frames)
+            refine_at<KIND, GRAD, PHI>(args, fi, (int)(e & 0xffffu), (int)((e >> 16) & 0xffffu));
             ++nref;
         }
     } else {
@@ -1769,13 +2068,22 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(const __grid_con
             const FrameDesc *f = args.frames + fi;
             const uint8_t *mask = (const uint8_t *)__ldg((const unsigned long long *)&f->mask);
             const int64_t mp = __ldg(&f->mask_pitch);
-            const int W = __ldg(&f->W);
-            const long long npx = (long long)__ldg(&f->H) * W;
-            for (long long q = tid; q < npx; q += nth) {
-                const int y = (int)(q / W), x = (int)(q - (long long)y * W);
-                if (mask[(int64_t)y * mp + x] & 2u) {
-                    refine_at<KIND, GRAD, PHI>(args, fi, x, y);
-                    ++nref;
+            const int W = __ldg(&f->W), H = __ldg(&f->H);
+            const int cpr = (W + 15) >> 4;  // 16-byte chunks per row
+            const long long nch = (long long)H * cpr;
+            for (long long q = tid; q < nch; q += nth) {
+                const int y = (int)(q / cpr), c = (int)(q - (long long)y * cpr);
+                const uint4 v = *reinterpret_cast<const uint4 *>(mask + (int64_t)y * mp + 16 * c);
+                const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    for (unsigned b = w[j] & 0x02020202u; b; b &= b - 1u) {
+                        const int x = 16 * c + 4 * j + ((__ffs(b) - 1) >> 3);
+                        if (x < W) {
+                            refine_at<KIND, GRAD, PHI>(args, fi, x, y);
+                            ++nref;
+                        }
+                    }
                 }
             }
         }

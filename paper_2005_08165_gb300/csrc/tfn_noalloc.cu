@@ -35,7 +35,7 @@ struct alignas(256) Scratch {
     CUtensorMap maps[kMax];  // 128 bytes each, 64-byte aligned
     FrameDesc desc[kMax];
     uint32_t status[64];
-    alignas(128) unsigned char refine[kRefineListBytes];  // the refinement list (runs of a call take turns)
+    alignas(128) unsigned char refine[refine_list_bytes(kNoallocRefineCap)];  // the refinement list (runs of a call take turns)
 };
 // The host-side staging of a call: what is copied into the scratch.
 struct Staging {
@@ -79,6 +79,11 @@ extern "C" tfn_status tfn_normals_noalloc(const tfn_frame *frames, int n, const 
     for (int i = 0; i < n; ++i)
         if ((st = validate_frame(&frames[i], method->output))) return st;
     if (n == 0) return TFN_OK;
+    // The descriptors travel through host staging that a captured copy would
+    // read only at replay, when it holds another call's frames: refuse.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (!cuda_ok(cudaStreamIsCapturing((cudaStream_t)stream, &cap), "cudaStreamIsCapturing")) return TFN_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return TFN_ERR_UNSUPPORTED;
     int dev = 0;
     if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return TFN_ERR_CUDA;
     Scratch *d = nullptr;
@@ -86,9 +91,11 @@ extern "C" tfn_status tfn_normals_noalloc(const tfn_frame *frames, int n, const 
     if ((st = device_setup(dev, &d, &sms))) return st;
 
     // Descriptors and tensor maps are built in thread-local host storage (no
-    // allocation) and copied into the device array on the caller's stream; a
-    // pageable-memory copy returns once the source has been consumed, so the
-    // staging is free for the next call as soon as this one returns.
+    // allocation) and copied into the device array on the caller's stream.
+    // A copy from pageable memory returns once its source has been consumed
+    // (the runtime may first wait for the work already queued on the stream
+    // to stage it), so the staging is free for the next call once this one
+    // returns.
     thread_local Staging h;
     // one launch per run of frames of one input kind; a small run takes the short-item shape
     int run_cfg[kMax];
@@ -112,7 +119,10 @@ extern "C" tfn_status tfn_normals_noalloc(const tfn_frame *frames, int n, const 
                  "cudaMemcpyAsync") ||
         !cuda_ok(cudaMemcpyAsync(d->desc, h.desc, (size_t)n * sizeof(FrameDesc), cudaMemcpyHostToDevice, s),
                  "cudaMemcpyAsync") ||
-        !cuda_ok(cudaMemsetAsync(d->status, 0, sizeof d->status, s), "cudaMemsetAsync"))
+        !cuda_ok(cudaMemsetAsync(d->status, 0, sizeof d->status, s), "cudaMemsetAsync") ||
+        // the list's count and the refinement kernel's block counter start at
+        // zero whatever an earlier (possibly overlapping) call left there
+        !cuda_ok(cudaMemsetAsync(d->refine, 0, 128, s), "cudaMemsetAsync"))
         return TFN_ERR_CUDA;
     // one launch per run of frames of the same input kind
     for (int i = 0; i < n;) {
@@ -121,7 +131,7 @@ extern "C" tfn_status tfn_normals_noalloc(const tfn_frame *frames, int n, const 
         int total = 0;
         for (int k = i; k < j; ++k) total += frame_tiles(frames[k], run_cfg[i]);
         st = launch_normals(frames[i].input_type, *method, run_cfg[i], d->desc + i, d->maps + i, d->status, d->refine,
-                            j - i, total, sms, s);
+                            kNoallocRefineCap, j - i, total, sms, s);
         if (st) return st;
         i = j;
     }

@@ -188,20 +188,30 @@ tfn_status validate_frame(const tfn_frame *f, int out_fmt)
 }
 
 // Per-pixel refinement threshold: a pixel is recomputed in double-float when
-// its FP32 error bound, (6 + 4 cA + 32/min(fx,fy)) u + K1 u bound/|n'|, could
-// exceed 3/4 of the 1e-3 degree budget (u = 2^-24).  bound is sum_p |num_p|
-// (|rho_j| + |rho_-j|) for the mean (candidate-sum cancellation; K1 = 23
-// covers the per-edge reciprocal, rho, numerator, product and accumulation
-// roundings) and the larger |middle candidate| for the median (K1 = 11).
-// cA bounds |A|/|n'|: A = (u-u0) G_u + (v-v0) G_v and |n'| >= |(fx G_u, fy G_v)|.
-// The gradients are carried as h + l to about u^2 relative (compensated
-// reciprocals, or a residual-corrected quotient for FD), except FD on depth
-// with the mean when kFdOnePassMean is set: one-pass quotients within 5u of
-// themselves.
-// That adds 5u to the error of (nx', ny') and 5u (|u-u0| |G_u| + |v-v0| |G_v|)
-// <= 5 sqrt(2) cA u |n'| to that of A (the fixed part below), and the
-// diagonal numerators' share, which the kernel adds to its bound.  The kernel
-// compares bound with thr |n'|.
+// its FP32 error bound, fixed u + K1 u bound/|n'|, could exceed 3/4 of the
+// 1e-3 degree budget (u = 2^-24); the kernel compares bound with thr |n'|.
+//
+// Mean: bound = sum_p |num_p| (|rho_j| + |rho_-j|) over the four pairs of
+// opposite neighbours (j, -j) with numerators G_u, G_v, G_u + G_v, G_u - G_v;
+// median: the larger |middle candidate|, K1 = 11.  cA bounds |A|/|n'|, A =
+// (u-u0) G_u + (v-v0) G_v, |n'| >= |(fx G_u, fy G_v)|.  fixed = 6 + 4 cA +
+// 32/min(fx, fy) covers the roundings of A, n' and the normalisation.
+//
+// Compensated gradients (h + l to about u^2; every filter but FD on depth
+// with the mean): K1 = 23 covers the per-edge reciprocal, rho, numerator,
+// product and accumulation roundings.
+//
+// One-pass FD gradients on depth with the mean (kFdOnePassMean), worst case
+// to first order in u: the edge reciprocal r = d rcp(d^2 + eps) is within
+// 4u of 1/d (square, reciprocal within one ulp, product; eps below 2^-32 of
+// d^2), 5u if the difference d itself rounds; rho = s r within 6u; a pair's
+// rho_j - rho_-j within 7u of |rho_j| + |rho_-j|; the gradients within 5u, so
+// num_p * (rho_j - rho_-j) within 12u |num_p| (|rho_j| + |rho_-j|) for the axis
+// pairs and 8u of that plus 5u (|G_u| + |G_v|) (|rho_j| + |rho_-j|) for the
+// diagonal ones; the four-term FMA chain adds 4u sum_p |num_p| (...).  That is
+// 16u bound + 5u (|G_u| + |G_v|) (diagonal magnitudes): K1 = 17, and the
+// kernel adds 0.3 (|G_u| + |G_v|) (>= 5/17) to the diagonal weights.  The
+// gradients' 5u also reach (nx', ny') and A: 5 + 5 sqrt(2) cA more in fixed.
 float refine_threshold(const tfn_frame &f, int grad, int phi)
 {
     const double u = std::ldexp(1.0, -24);
@@ -213,7 +223,7 @@ float refine_threshold(const tfn_frame &f, int grad, int phi)
     const bool one_pass = kFdOnePassMean && grad == GRAD_FD && phi == PHI_MEAN && depth;
     const double fixed = (6.0 + 4.0 * cA + 32.0 / std::min(f.cam.fx, f.cam.fy) +
                           (one_pass ? 5.0 + 5.0 * std::sqrt(2.0) * cA : 0.0)) * u;
-    const double k1 = phi == PHI_MEAN ? 23.0 : 11.0;
+    const double k1 = phi == PHI_MEAN ? (one_pass ? 17.0 : 23.0) : 11.0;
     const double t = (tol_part - fixed) / (k1 * u);
     return t > 0 ? (float)t : 0.f;
 }

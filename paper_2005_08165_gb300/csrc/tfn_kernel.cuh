@@ -912,14 +912,17 @@ __device__ __forceinline__ void row_step_fd2(const Row<KIND, GRAD_FD> &P, const 
             mF = disp ? neg2(T) : T;
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
-                // bound of the candidate sum's rounding: sum_p |num_p| (|rho_j| + |rho_-j|);
-                // one-pass gradients (within 5u each) add up to 5u (|G_u| + |G_v|)
-                // to a diagonal numerator: its weight grows by (|G_u| + |G_v|) / 4
+                // bound of the candidate sum's rounding: sum_p |num_p| (|rho_j| + |rho_-j|),
+                // which the host's threshold multiplies by K1 u.  One-pass gradients
+                // (within 5u each) put up to 5u (|G_u| + |G_v|) on a diagonal
+                // numerator, whose cancellation can leave it large against the
+                // numerator: its weight grows by 0.3 (|G_u| + |G_v|) (5u / (K1 u)
+                // with this path's K1 = 17, see refine_threshold)
                 float w2 = fabsf(lane_of(n2, l)), w3 = fabsf(lane_of(n3n, l));
                 if constexpr (one_pass) {
                     const float sg = __fadd_rn(fabsf(lane_of(gu, l)), fabsf(lane_of(gv, l)));
-                    w2 = __fmaf_rn(0.25f, sg, w2);
-                    w3 = __fmaf_rn(0.25f, sg, w3);
+                    w2 = __fmaf_rn(0.3f, sg, w2);
+                    w3 = __fmaf_rn(0.3f, sg, w3);
                 }
                 mbound[l] = __fmaf_rn(fabsf(lane_of(gu, l)), __fadd_rn(fabsf(lane_of(Fr, l)), fabsf(lane_of(Bl, l))),
                             __fmaf_rn(fabsf(lane_of(gv, l)), __fadd_rn(fabsf(lane_of(Fd, l)), fabsf(lane_of(Bu, l))),

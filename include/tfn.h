@@ -192,6 +192,14 @@ typedef struct tfn_method {
 /* Compute every pixel on the compensated (double-float) path instead of only
  * the rare pixels whose FP32 error bound is too loose.  For testing. */
 #define TFN_FLAG_REFINE_ALL 1
+/* Test hook for the failure path: the first warp of each launch, before it
+ * issues any copy, waits on a barrier that nothing completes, gives up after
+ * about 1 ms through the same bounded wait that a TMA copy that never lands
+ * would run out, sets the failed-wait bit in the status word and leaves its
+ * work items unprocessed.  The launch then reports the failure as a real one
+ * would (tfn_device_status, a server batch's TFN_ERR_DEVICE) and the context
+ * stays usable.  For testing. */
+#define TFN_FLAG_TEST_WAIT_TIMEOUT 2
 
 /* ---- status and context ------------------------------------------------ */
 
@@ -331,6 +339,10 @@ typedef struct tfn_server_opts {
  * memory is fastest); the server copies the input into device staging memory
  * and the results back.  Without it they are device pointers, used in place. */
 #define TFN_REQ_HOST 1
+/* tfn_submit flag: the request's batch is launched with
+ * TFN_FLAG_TEST_WAIT_TIMEOUT, so that batch fails with TFN_ERR_DEVICE.  For
+ * testing. */
+#define TFN_REQ_TEST_WAIT_TIMEOUT 2
 
 typedef struct tfn_serving_stats {
     uint64_t submitted, completed, failed, cancelled;
@@ -368,8 +380,8 @@ tfn_status tfn_submit(tfn_server *srv, const tfn_frame *frame, int flags, uint64
 /* Waits at most timeout_ms (>= 0; 0 polls) for the request.  TFN_OK: it
  * finished and *result holds its status (TFN_OK: outputs written;
  * TFN_ERR_CANCELLED: the server was destroyed before it was admitted;
- * TFN_ERR_DEVICE: a kernel of its batch gave up a bounded wait, after which
- * the server's later batches fail too; TFN_ERR_CUDA); the ticket is then
+ * TFN_ERR_DEVICE: a kernel of its batch gave up a bounded wait (each batch
+ * reports only its own kernels' waits); TFN_ERR_CUDA); the ticket is then
  * released.  TFN_ERR_TIMEOUT: not finished yet (wait again).
  * TFN_ERR_INVALID_ARG: unknown or already released ticket.  Never blocks
  * longer than the limit. */

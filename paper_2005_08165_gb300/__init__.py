@@ -32,7 +32,9 @@ TFN_PHI_MEAN, TFN_PHI_MEDIAN = range(2)
 TFN_EST_3F2N, TFN_EST_PLANEPCA = range(2)
 TFN_OUT_F32, TFN_OUT_F16, TFN_OUT_BF16, TFN_OUT_F16X4, TFN_OUT_BF16X4, TFN_OUT_OCT16 = range(6)
 TFN_FLAG_REFINE_ALL = 1
+TFN_FLAG_TEST_WAIT_TIMEOUT = 2
 TFN_REQ_HOST = 1
+TFN_REQ_TEST_WAIT_TIMEOUT = 2
 
 GRADS = {"fd": TFN_GRAD_FD, "sobel": TFN_GRAD_SOBEL, "scharr": TFN_GRAD_SCHARR, "prewitt": TFN_GRAD_PREWITT,
          "weighted": TFN_GRAD_WEIGHTED, "sep5": TFN_GRAD_SEP5, "fd5": TFN_GRAD_FD5, "sobel5": TFN_GRAD_SOBEL5,
@@ -511,11 +513,13 @@ class Server:
         self._keep = {}
 
     def submit(self, inp, cam, normals, mask, *, host=False, disparity=False, disp_scale=1.0 / 16,
-               points=None) -> int:
-        """Queues one frame; returns its ticket (raises TfnError, e.g. TFN_ERR_BUSY)."""
+               points=None, flags=0) -> int:
+        """Queues one frame; returns its ticket (raises TfnError, e.g. TFN_ERR_BUSY).  `flags` adds
+        TFN_REQ_* flags to the one `host` sets."""
         f = make_frame(inp, normals, mask, cam, disparity, disp_scale, self.output, points)
         t = ctypes.c_uint64()
-        check(tfn_submit(self.handle, ctypes.byref(f), TFN_REQ_HOST if host else 0, ctypes.byref(t)), "tfn_submit")
+        fl = (TFN_REQ_HOST if host else 0) | flags
+        check(tfn_submit(self.handle, ctypes.byref(f), fl, ctypes.byref(t)), "tfn_submit")
         self._keep[t.value] = (inp, normals, mask, points)
         return t.value
 

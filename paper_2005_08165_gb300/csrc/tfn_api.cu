@@ -131,7 +131,7 @@ tfn_status validate_method(const tfn_method *m)
     if (!m) return TFN_ERR_INVALID_ARG;
     if (m->estimator != TFN_EST_3F2N && m->estimator != TFN_EST_PLANEPCA) return TFN_ERR_INVALID_ARG;
     if (m->grad < 0 || m->grad > GRAD_PREWITT5 || m->phi < 0 || m->phi >= PHI_COUNT || m->output < 0 ||
-        m->output > OUT_OCT16 || (m->flags & ~TFN_FLAG_REFINE_ALL))
+        m->output > OUT_OCT16 || (m->flags & ~(TFN_FLAG_REFINE_ALL | TFN_FLAG_TEST_WAIT_TIMEOUT)))
         return TFN_ERR_INVALID_ARG;
     if (m->grad == GRAD_WEIGHTED) {
         for (int k = 0; k < 3; ++k)
@@ -430,7 +430,8 @@ tfn_status slot_reserve(tfn_ctx *c, Slot &s, int n)
 
 
 // One launch over frames[0..n) (all of one input kind).
-tfn_status launch_group(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method &m, cudaStream_t stream)
+tfn_status launch_group(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method &m, cudaStream_t stream,
+                        uint32_t *status)
 {
     const int kind = frames[0].input_type;
     const int cfg = choose_cfg(c, frames, n, m);
@@ -472,7 +473,7 @@ tfn_status launch_group(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_me
     c->last_slot = si;
     if (!s.done) TFN_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
 
-    tfn_status lst = launch_normals(kind, m, cfg, slot_descs(s.dev), slot_maps(s.dev, s.cap), c->status,
+    tfn_status lst = launch_normals(kind, m, cfg, slot_descs(s.dev), slot_maps(s.dev, s.cap), status ? status : c->status,
                                     slot_refine(s.dev, s.cap), kRefineCap, n, total, c->num_sms, stream);
     if (lst) return lst;
     TFN_CUDA(cudaEventRecord(s.done, stream));
@@ -483,14 +484,15 @@ tfn_status launch_group(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_me
 
 namespace tfn {
 
-tfn_status run_batch(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method &m, cudaStream_t stream)
+tfn_status run_batch(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method &m, cudaStream_t stream,
+                     uint32_t *status)
 {
     // frames of one input kind go to one launch; keep the caller's order
     int i = 0;
     while (i < n) {
         int j = i + 1;
         while (j < n && frames[j].input_type == frames[i].input_type) ++j;
-        tfn_status st = launch_group(c, frames + i, j - i, m, stream);
+        tfn_status st = launch_group(c, frames + i, j - i, m, stream, status);
         if (st) return st;
         i = j;
     }

@@ -113,7 +113,9 @@ inline int choose_cfg(const tfn_ctx *c, const tfn_frame *frames, int n, const tf
 
 // Enqueues the estimator over frames[0..n) (device pointers, already
 // validated) on `stream`: one persistent launch per run of frames of one
-// input kind.
-tfn_status run_batch(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method &m, cudaStream_t stream);
+// input kind.  The kernels report to `status` (2 words: failed-wait bits,
+// refined pixels), the context's status word when null.
+tfn_status run_batch(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_method &m, cudaStream_t stream,
+                     uint32_t *status = nullptr);
 
 }  // namespace tfn

@@ -54,6 +54,7 @@ constexpr float kValidLo = 1.52587890625e-05f;  // 2^-16
 constexpr float kValidHi = 65536.0f;            // 2^16
 constexpr long long kWaitCycles = 4000000000LL;    // ~2 s at 2 GHz
 constexpr long long kDrainCycles = 2000000LL;      // ~1 ms: the drain after a failed wait
+constexpr long long kTestWaitCycles = 2000000LL;   // ~1 ms: the wait of TFN_FLAG_TEST_WAIT_TIMEOUT
 
 // ---------------------------------------------------------------- numerics
 
@@ -1683,6 +1684,21 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
     __syncwarp();
 
     const int gw = blockIdx.x * NW + warp, nw = gridDim.x * NW, total = args.total_tiles;
+
+    if ((args.flags & TFN_FLAG_TEST_WAIT_TIMEOUT) && gw == 0) {
+        // (test hook) wait on a barrier that nothing completes, before this
+        // warp issues any copy, and give up as a copy that never landed
+        // would: the launch reports the failed wait, this warp's items stay
+        // unprocessed, and no copy of this warp is in flight
+        __shared__ __align__(8) unsigned long long never;
+        if (lane == 0) {
+            mbar_init(smem_addr(&never), 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            if (!mbar_wait(smem_addr(&never), 0, kTestWaitCycles)) atomicOr(args.status, DEVERR_TMA_WAIT);
+        }
+        __syncwarp();
+        return;
+    }
 
     // Producer (lane 0): chunk number cc of this warp's sequence is chunk
     // cc % NCH of its (cc / NCH)-th item and goes to stage cc % NST.

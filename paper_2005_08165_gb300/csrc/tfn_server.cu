@@ -14,9 +14,10 @@
 //             pipeline's stream: host-to-device copies, one persistent kernel
 //             launch per input type over the whole batch (the same launch path
 //             as tfn_normals_batch), device-to-host copies, an event;
-//   retirer:  waits for the oldest batch in flight, checks the kernels' status
-//             word, completes the batch's requests (status, latency), releases
-//             its arena block and wakes the waiters and the launcher.
+//   retirer:  waits for the oldest batch in flight, checks its kernels' status
+//             word (one per pipeline, zeroed per batch), completes the batch's
+//             requests (status, latency), releases its arena block and
+//             wakes the waiters and the launcher.
 //
 // Requests that arrive while batches are in flight queue up and form the next
 // batch as soon as a pipeline frees up (continuous batching); with
@@ -86,6 +87,7 @@ struct Request {
     uint64_t ticket;
     tfn_frame frame;  // as submitted
     bool host;
+    bool test_wait;      // TFN_REQ_TEST_WAIT_TIMEOUT
     size_t stage_bytes;  // 0 for device-buffer requests
     Clock::time_point t_submit;
 };
@@ -105,7 +107,8 @@ struct Batch {
 struct Pipe {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    uint32_t *status_host = nullptr;  // pinned copy of the kernels' status word
+    uint32_t *status_dev = nullptr;   // the status word of this pipeline's kernels, zeroed per batch
+    uint32_t *status_host = nullptr;  // its pinned copy after the batch
     bool busy = false;
 };
 
@@ -205,7 +208,13 @@ tfn_status enqueue_batch(tfn_server *s, Batch &b, size_t block_off)
                      "cudaMemcpy2DAsync(H2D)"))
             return TFN_ERR_CUDA;
     }
-    tfn_status st = run_batch(s->ctx, dev.data(), (int)dev.size(), s->method, p.stream);
+    // each batch reports only its own kernels' failed waits
+    if (!cuda_ok(cudaMemsetAsync(p.status_dev, 0, 2 * sizeof(uint32_t), p.stream), "cudaMemsetAsync(status)"))
+        return TFN_ERR_CUDA;
+    tfn_method m = s->method;
+    for (const Request &r : b.reqs)
+        if (r.test_wait) m.flags |= TFN_FLAG_TEST_WAIT_TIMEOUT;
+    tfn_status st = run_batch(s->ctx, dev.data(), (int)dev.size(), m, p.stream, p.status_dev);
     if (st) return st;
     for (size_t i = 0; i < b.reqs.size(); ++i) {
         const Request &r = b.reqs[i];
@@ -232,7 +241,7 @@ tfn_status enqueue_batch(tfn_server *s, Batch &b, size_t block_off)
                              "cudaMemcpy2DAsync(D2H)"))
                     return TFN_ERR_CUDA;
     }
-    if (!cuda_ok(cudaMemcpyAsync(p.status_host, s->ctx->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, p.stream),
+    if (!cuda_ok(cudaMemcpyAsync(p.status_host, p.status_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, p.stream),
                  "cudaMemcpyAsync(status)") ||
         !cuda_ok(cudaEventRecord(p.done, p.stream), "cudaEventRecord"))
         return TFN_ERR_CUDA;
@@ -342,6 +351,7 @@ void destroy_resources(tfn_server *s)
         }
         if (p.done) cudaEventDestroy(p.done);
         if (p.status_host) cudaFreeHost(p.status_host);
+        if (p.status_dev) cudaFree(p.status_dev);
     }
     if (s->arena_base) cudaFree(s->arena_base);
     if (s->ctx) tfn_destroy(s->ctx);
@@ -424,7 +434,9 @@ tfn_status tfn_server_create(tfn_ctx *ctx, const tfn_server_opts *o, tfn_server 
         Pipe &p = s->pipes[k];
         if (!cuda_ok(cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking), "cudaStreamCreate") ||
             !cuda_ok(cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming), "cudaEventCreate") ||
-            !cuda_ok(cudaMallocHost((void **)&p.status_host, sizeof(uint32_t)), "cudaMallocHost")) {
+            !cuda_ok(cudaMallocHost((void **)&p.status_host, sizeof(uint32_t)), "cudaMallocHost") ||
+            !cuda_ok(cudaMalloc((void **)&p.status_dev, 256), "cudaMalloc(status)") ||
+            !cuda_ok(cudaMemset(p.status_dev, 0, 256), "cudaMemset(status)")) {
             destroy_resources(s);
             delete s;
             return TFN_ERR_CUDA;
@@ -454,13 +466,14 @@ tfn_status tfn_server_create(tfn_ctx *ctx, const tfn_server_opts *o, tfn_server 
 
 tfn_status tfn_submit(tfn_server *s, const tfn_frame *frame, int flags, uint64_t *ticket)
 {
-    if (!s || !frame || !ticket || (flags & ~TFN_REQ_HOST)) return TFN_ERR_INVALID_ARG;
+    if (!s || !frame || !ticket || (flags & ~(TFN_REQ_HOST | TFN_REQ_TEST_WAIT_TIMEOUT))) return TFN_ERR_INVALID_ARG;
     const bool host = flags & TFN_REQ_HOST;
     tfn_status st = host ? validate_host_request(*frame, s->method.output) : validate_frame(frame, s->method.output);
     if (st) return st;
     Request r;
     r.frame = *frame;
     r.host = host;
+    r.test_wait = flags & TFN_REQ_TEST_WAIT_TIMEOUT;
     r.stage_bytes = host ? s->arena.round(stage_layout(*frame, s->method.output).bytes) : 0;
     if (r.stage_bytes > s->arena.capacity()) return TFN_ERR_OUT_OF_MEMORY;  // could never be admitted
     std::lock_guard<std::mutex> lk(s->mu);

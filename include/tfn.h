@@ -333,7 +333,12 @@ typedef struct tfn_server_opts {
     int32_t max_delay_us;     /* hold a partial batch up to this long after its oldest request
                                  arrived while the device is busy (0: never hold) */
     int32_t pipelines;        /* batches in flight at once, 1..4 (0: 2) */
+    int32_t flags;            /* TFN_SERVER_* */
 } tfn_server_opts;
+
+/* tfn_server_opts flag: launch each batch's kernels directly instead of
+ * replaying them from the pipeline's CUDA graphs (for comparison). */
+#define TFN_SERVER_NO_GRAPHS 1
 
 /* tfn_submit flag: the frame's pointers are HOST pointers (page-locked
  * memory is fastest); the server copies the input into device staging memory
@@ -360,6 +365,11 @@ typedef struct tfn_serving_stats {
     int32_t in_flight;           /* requests admitted and not yet complete */
     size_t staging_bytes_in_use;
     size_t staging_bytes_capacity;
+    uint64_t graph_launches;        /* batches whose kernels were replayed from a CUDA graph */
+    uint64_t max_batches_in_flight; /* most batches launched and not yet retired at once */
+    uint64_t admitted_while_busy;   /* requests admitted while an earlier batch was in flight */
+    uint64_t device_overlaps;       /* batches whose kernels started on the device before the
+                                       previous batch's kernels had finished (CUDA events) */
 } tfn_serving_stats;
 
 /* Creates a server on ctx's device.  The server owns a context of its own

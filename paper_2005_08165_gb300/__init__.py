@@ -35,6 +35,7 @@ TFN_FLAG_REFINE_ALL = 1
 TFN_FLAG_TEST_WAIT_TIMEOUT = 2
 TFN_REQ_HOST = 1
 TFN_REQ_TEST_WAIT_TIMEOUT = 2
+TFN_SERVER_NO_GRAPHS = 1
 
 GRADS = {"fd": TFN_GRAD_FD, "sobel": TFN_GRAD_SOBEL, "scharr": TFN_GRAD_SCHARR, "prewitt": TFN_GRAD_PREWITT,
          "weighted": TFN_GRAD_WEIGHTED, "sep5": TFN_GRAD_SEP5, "fd5": TFN_GRAD_FD5, "sobel5": TFN_GRAD_SOBEL5,
@@ -68,7 +69,8 @@ class tfn_method(ctypes.Structure):
 
 class tfn_server_opts(ctypes.Structure):
     _fields_ = [("method", tfn_method), ("mem_budget_bytes", ctypes.c_size_t), ("max_batch_frames", ctypes.c_int32),
-                ("max_queue", ctypes.c_int32), ("max_delay_us", ctypes.c_int32), ("pipelines", ctypes.c_int32)]
+                ("max_queue", ctypes.c_int32), ("max_delay_us", ctypes.c_int32), ("pipelines", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
 
 
 class tfn_serving_stats(ctypes.Structure):
@@ -78,7 +80,9 @@ class tfn_serving_stats(ctypes.Structure):
                 ("mean_batch_frames", ctypes.c_double), ("latency_p50_us", ctypes.c_double),
                 ("latency_p99_us", ctypes.c_double), ("latency_max_us", ctypes.c_double),
                 ("latency_samples", ctypes.c_uint64), ("queued", ctypes.c_int32), ("in_flight", ctypes.c_int32),
-                ("staging_bytes_in_use", ctypes.c_size_t), ("staging_bytes_capacity", ctypes.c_size_t)]
+                ("staging_bytes_in_use", ctypes.c_size_t), ("staging_bytes_capacity", ctypes.c_size_t),
+                ("graph_launches", ctypes.c_uint64), ("max_batches_in_flight", ctypes.c_uint64),
+                ("admitted_while_busy", ctypes.c_uint64), ("device_overlaps", ctypes.c_uint64)]
 
 
 _P = ctypes.c_void_p
@@ -500,11 +504,12 @@ class Server:
     alive until wait() returns for their ticket."""
 
     def __init__(self, ctx: Context, *, grad="fd", phi="mean", output="f32", flags=0, mem_budget=0,
-                 max_batch=0, max_queue=0, max_delay_us=0, pipelines=0, weights=None):
+                 max_batch=0, max_queue=0, max_delay_us=0, pipelines=0, weights=None, graphs=True):
         o = tfn_server_opts()
         o.method = make_method(grad, phi, output, flags, weights)
         o.mem_budget_bytes = mem_budget
         o.max_batch_frames, o.max_queue, o.max_delay_us, o.pipelines = max_batch, max_queue, max_delay_us, pipelines
+        o.flags = 0 if graphs else TFN_SERVER_NO_GRAPHS
         h = ctypes.c_void_p()
         check(tfn_server_create(ctx.handle, ctypes.byref(o), ctypes.byref(h)), "tfn_server_create")
         self.handle = h

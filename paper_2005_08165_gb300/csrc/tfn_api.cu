@@ -292,41 +292,44 @@ int frame_tiles(const tfn_frame &f, int cfg)
     return ((f.width + tw - 1) / tw) * ((f.height + th - 1) / th);
 }
 
-// Launches the kernel for frames of one input kind whose descriptors and
-// tensor maps are already in device memory.
-tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
-                          uint32_t *d_status, void *d_refine, int refine_cap, int nframes, int total_tiles,
-                          int num_sms, cudaStream_t stream)
+// The launch (kernel, grid, arguments, and the refinement kernel that
+// follows it, if any) for frames of one input kind whose descriptors and
+// tensor maps are already in device memory.  spec.grid == 0: nothing to run.
+tfn_status make_launch(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
+                       uint32_t *d_status, void *d_refine, int refine_cap, int nframes, int total_tiles, int num_sms,
+                       LaunchSpec *spec)
 {
     const int grad = method_grad(m);
-    KernelFn fn = kernel_for(kind, grad, method_phi(m), cfg);
-    if (!fn) return TFN_ERR_UNSUPPORTED;
-    const int threads = cfg_threads(cfg, grad);
-    const size_t smem = smem_bytes(kind, cfg, grad);
-    if (!cuda_ok(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+    LaunchSpec &L = *spec;
+    L.fn = kernel_for(kind, grad, method_phi(m), cfg);
+    if (!L.fn) return TFN_ERR_UNSUPPORTED;
+    L.threads = cfg_threads(cfg, grad);
+    L.smem = smem_bytes(kind, cfg, grad);
+    if (!cuda_ok(cudaFuncSetAttribute((const void *)L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem),
                  "cudaFuncSetAttribute"))
         return TFN_ERR_CUDA;
     int per_sm = 0;
-    if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)fn, threads, smem),
+    if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)L.fn, L.threads, L.smem),
                  "cudaOccupancyMaxActiveBlocksPerMultiprocessor"))
         return TFN_ERR_CUDA;
     if (per_sm < 1) per_sm = 1;
     // one warp per work item at a time: no more CTAs than items / warps per CTA
     const int nw = cta_warps(cfg, grad);
-    const int grid = std::min((total_tiles + nw - 1) / nw, per_sm * num_sms);
-    if (grid < 1) return TFN_OK;
+    L.grid = std::max(0, std::min((total_tiles + nw - 1) / nw, per_sm * num_sms));
     // the refinement kernel of this method (none for PlanePCA, which never flags a pixel)
-    KernelFn rf = nullptr;
-    if (grad != GRAD_PLANEPCA && !refines_in_place(cfg) && !(rf = refiner_for(kind, grad, method_phi(m))))
+    L.rf = nullptr;
+    if (grad != GRAD_PLANEPCA && !refines_in_place(cfg) && !(L.rf = refiner_for(kind, grad, method_phi(m))))
         return TFN_ERR_UNSUPPORTED;
     // its grid: the flagged pixels (about one per thousand on noisy frames),
     // as many threads as fit on the GPU at once: each refines its pixels one
     // after another, so a list that fits in one round costs one pixel's latency
     int rf_per_sm = 1;
-    if (rf && !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rf_per_sm, (const void *)rf, kRefineThreads, 0),
-                       "cudaOccupancyMaxActiveBlocksPerMultiprocessor(refine)"))
+    if (L.rf && !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rf_per_sm, (const void *)L.rf, kRefineThreads, 0),
+                         "cudaOccupancyMaxActiveBlocksPerMultiprocessor(refine)"))
         return TFN_ERR_CUDA;
-    LaunchArgs a;
+    L.rf_grid = std::max(1, rf_per_sm) * num_sms;
+    L.d_refine = d_refine;
+    LaunchArgs &a = L.args;
     a.frames = d_frames;
     a.maps = d_maps;
     a.status = d_status;
@@ -340,17 +343,34 @@ tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDes
     for (int k = 0; k < 5; ++k) a.w[k] = m.grad == GRAD_WEIGHTED && k < 3 ? m.weights[k] : 0.f;
     if (grad_is_sep5(m.grad)) sep5_weights(m.grad, m.weights, a.w);
     a.pad[0] = a.pad[1] = 0;
-    void *params[] = {&a};
-    if (!cuda_ok(cudaLaunchKernel((const void *)fn, dim3(grid), dim3(threads), params, smem, stream),
+    return TFN_OK;
+}
+
+// Enqueues a launch made by make_launch.
+tfn_status enqueue_launch(LaunchSpec &L, cudaStream_t stream)
+{
+    if (L.grid < 1) return TFN_OK;
+    void *params[] = {&L.args};
+    if (!cuda_ok(cudaLaunchKernel((const void *)L.fn, dim3(L.grid), dim3(L.threads), params, L.smem, stream),
                  "cudaLaunchKernel"))
         return TFN_ERR_CUDA;
-    if (rf && !cuda_ok(cudaLaunchKernel((const void *)rf, dim3(std::max(1, rf_per_sm) * num_sms), dim3(kRefineThreads),
-                                        params, 0, stream),
-                       "cudaLaunchKernel(refine)")) {
-        cudaMemsetAsync(d_refine, 0, 128, stream);  // (what the refinement kernel would have zeroed)
+    if (L.rf && !cuda_ok(cudaLaunchKernel((const void *)L.rf, dim3(L.rf_grid), dim3(kRefineThreads), params, 0, stream),
+                         "cudaLaunchKernel(refine)")) {
+        cudaMemsetAsync(L.d_refine, 0, 128, stream);  // (what the refinement kernel would have zeroed)
         return TFN_ERR_CUDA;
     }
     return TFN_OK;
+}
+
+tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
+                          uint32_t *d_status, void *d_refine, int refine_cap, int nframes, int total_tiles,
+                          int num_sms, cudaStream_t stream)
+{
+    LaunchSpec L;
+    tfn_status st = make_launch(kind, m, cfg, d_frames, d_maps, d_status, d_refine, refine_cap, nframes, total_tiles,
+                                num_sms, &L);
+    if (st) return st;
+    return enqueue_launch(L, stream);
 }
 
 }  // namespace tfn
@@ -382,6 +402,10 @@ void frame_key(std::vector<unsigned char> &k, const tfn_frame &f)
     append_key(k, &f.points_plane_stride, sizeof f.points_plane_stride);
 }
 
+}  // namespace
+
+namespace tfn {
+
 // A slot: cap frame descriptors, cap tensor maps (128-byte aligned), then the
 // launch's refinement list (128-byte aligned).
 size_t slot_bytes(int cap)
@@ -400,6 +424,10 @@ void *slot_refine(void *base, int cap)
     uintptr_t p = (uintptr_t)(slot_maps(base, cap) + cap);
     return (void *)((p + 127) & ~(uintptr_t)127);
 }
+
+}  // namespace tfn
+
+namespace {
 
 tfn_status slot_reserve(tfn_ctx *c, Slot &s, int n)
 {

@@ -87,6 +87,14 @@ struct DeviceGuard {  // switches to the context's device for the call's duratio
     }
 };
 
+// The layout of a descriptor slot (context slots, plans, server pipelines):
+// FrameDesc[cap], then CUtensorMap[cap] (128-byte aligned), then the launch's
+// refinement list (kRefineListBytes, 128-byte aligned).
+size_t slot_bytes(int cap);
+FrameDesc *slot_descs(void *base);
+CUtensorMap *slot_maps(void *base, int cap);
+void *slot_refine(void *base, int cap);
+
 // Device allocations counted against the context's budget.
 tfn_status ctx_alloc(tfn_ctx *c, void **p, size_t bytes);
 void ctx_free(tfn_ctx *c, void *&p, size_t bytes);

@@ -187,7 +187,20 @@ float refine_threshold(const tfn_frame &f, int grad, int phi);
 tfn_status encode_map(CUtensorMap *map, const tfn_frame &f, int cfg);
 FrameDesc describe_frame(const tfn_frame &f, int cfg, const tfn_method &m, int tile_begin);
 int frame_tiles(const tfn_frame &f, int cfg);
+// One launch of the kernel for frames of one input kind, and of the
+// refinement kernel after it (rf, or none).
+struct LaunchSpec {
+    KernelFn fn = nullptr, rf = nullptr;
+    int grid = 0, threads = 0, rf_grid = 0;
+    size_t smem = 0;
+    void *d_refine = nullptr;
+    LaunchArgs args;
+};
 // d_refine: the launch's refinement list (refine_list_bytes(refine_cap), 128-byte aligned).
+tfn_status make_launch(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
+                       uint32_t *d_status, void *d_refine, int refine_cap, int nframes, int total_tiles, int num_sms,
+                       LaunchSpec *spec);
+tfn_status enqueue_launch(LaunchSpec &spec, cudaStream_t stream);
 tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
                           uint32_t *d_status, void *d_refine, int refine_cap, int nframes, int total_tiles,
                           int num_sms, cudaStream_t stream);

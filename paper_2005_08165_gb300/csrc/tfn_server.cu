@@ -104,11 +104,35 @@ struct Batch {
     tfn_status launch_status = TFN_OK;  // failure while enqueueing
 };
 
+// The descriptors of one launch (one input kind) of a pipeline's batches:
+// a descriptor slot (slot_bytes) and its pinned host mirror.
+struct GroupBuf {
+    void *dev = nullptr, *host = nullptr;
+    int cap = 0;
+};
+
+// A batch's kernels as a CUDA graph: the status word's reset, then per
+// launch (input kind) normals_kernel and its refinement kernel, if any.
+// Captured once per key (the method's flags, then per launch its kind, tile
+// shape and whether it refines in a second kernel); replayed with each
+// kernel node's grid and arguments updated to the batch.
+struct GraphEntry {
+    std::vector<int> key;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> fn_node, rf_node;  // per launch
+};
+constexpr size_t kMaxGraphs = 16;  // per pipeline
+
 struct Pipe {
     cudaStream_t stream = nullptr;
+    cudaStream_t capture = nullptr;  // the stream graphs are captured on
     cudaEvent_t done = nullptr;
+    cudaEvent_t k_start = nullptr, k_end = nullptr;  // (timing) around the batch's kernels
     uint32_t *status_dev = nullptr;   // the status word of this pipeline's kernels, zeroed per batch
     uint32_t *status_host = nullptr;  // its pinned copy after the batch
+    GroupBuf groups[KIND_COUNT];
+    std::vector<GraphEntry> graphs;
     bool busy = false;
 };
 
@@ -120,6 +144,9 @@ struct tfn_server {
     size_t max_batch = 256, max_queue = 65536;
     int max_delay_us = 0;
     int npipes = 2;
+    bool use_graphs = true;
+    cudaEvent_t t0_event = nullptr;  // the zero of the device timeline of the batches (timing)
+    float last_kernel_end_ms = -1.f;  // (retirer) when the previous batch's kernels ended
     Pipe pipes[kMaxPipes];
     void *arena_base = nullptr;
     size_t arena_bytes = 0;
@@ -139,6 +166,7 @@ struct tfn_server {
     // statistics (under mu)
     uint64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, rejected = 0, batches = 0, batch_frames = 0;
     uint64_t pixels = 0;
+    uint64_t graph_launches = 0, max_inflight = 0, admitted_busy = 0, device_overlaps = 0;
     Clock::time_point t0;
     std::vector<float> lat_us;  // ring of the last kLatencyWindow latencies
     size_t lat_next = 0;
@@ -168,6 +196,141 @@ void complete_locked(tfn_server *s, const Request &r, tfn_status st, Clock::time
     } else {
         ++s->failed;
     }
+}
+
+void destroy_graph(GraphEntry &e)
+{
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    if (e.graph) cudaGraphDestroy(e.graph);
+    e.exec = nullptr;
+    e.graph = nullptr;
+}
+
+// Enqueues a batch's kernels (frames of any input kinds, device pointers)
+// on the pipeline's stream from one of its graphs: the frames grouped by
+// input kind, one launch each, the descriptors in the pipeline's own slots.
+tfn_status enqueue_kernels_graph(tfn_server *s, Pipe &p, const std::vector<tfn_frame> &dev, const tfn_method &m)
+{
+    tfn_ctx *c = s->ctx;
+    std::vector<LaunchSpec> specs;
+    std::vector<int> key{m.flags};
+    std::vector<tfn_frame> fr;
+    for (int kind = 0; kind < KIND_COUNT; ++kind) {
+        fr.clear();
+        for (const tfn_frame &f : dev)
+            if (f.input_type == kind) fr.push_back(f);
+        if (fr.empty()) continue;
+        const int n = (int)fr.size();
+        const int cfg = choose_cfg(c, fr.data(), n, m);
+        GroupBuf &g = p.groups[kind];
+        if (g.cap < n) {
+            // (the pipeline is idle: its previous batch has retired)
+            const int cap = std::max(n, std::max(8, 2 * g.cap));
+            if (g.dev) cudaFree(g.dev);
+            if (g.host) cudaFreeHost(g.host);
+            g.dev = g.host = nullptr;
+            g.cap = 0;
+            if (!cuda_ok(cudaMalloc(&g.dev, slot_bytes(cap)), "cudaMalloc(descriptors)") ||
+                !cuda_ok(cudaMemset(slot_refine(g.dev, cap), 0, 128), "cudaMemset(refinement list)") ||
+                !cuda_ok(cudaMallocHost(&g.host, slot_bytes(cap)), "cudaMallocHost(descriptors)"))
+                return TFN_ERR_CUDA;
+            g.cap = cap;
+        }
+        FrameDesc *d = slot_descs(g.host);
+        CUtensorMap *maps = slot_maps(g.host, g.cap);
+        int tiles = 0;
+        for (int i = 0; i < n; ++i) {
+            d[i] = describe_frame(fr[i], cfg, m, tiles);
+            tiles += frame_tiles(fr[i], cfg);
+            tfn_status st = encode_map(&maps[i], fr[i], cfg);
+            if (st) return st;
+        }
+        const size_t off_maps = (uintptr_t)maps - (uintptr_t)g.host;
+        if (!cuda_ok(cudaMemcpyAsync(g.dev, g.host, (size_t)n * sizeof(FrameDesc), cudaMemcpyHostToDevice, p.stream),
+                     "cudaMemcpyAsync(descriptors)") ||
+            !cuda_ok(cudaMemcpyAsync((char *)g.dev + off_maps, maps, (size_t)n * sizeof(CUtensorMap),
+                                     cudaMemcpyHostToDevice, p.stream),
+                     "cudaMemcpyAsync(tensor maps)"))
+            return TFN_ERR_CUDA;
+        LaunchSpec L;
+        tfn_status st = make_launch(kind, m, cfg, slot_descs(g.dev), slot_maps(g.dev, g.cap), p.status_dev,
+                                    slot_refine(g.dev, g.cap), kRefineCap, n, tiles, c->num_sms, &L);
+        if (st) return st;
+        if (L.grid < 1) continue;
+        specs.push_back(L);
+        key.insert(key.end(), {kind, cfg, L.rf != nullptr});
+    }
+    GraphEntry *ge = nullptr;
+    for (GraphEntry &e : p.graphs)
+        if (e.key == key) ge = &e;
+    if (ge) {
+        for (size_t i = 0; i < specs.size(); ++i) {
+            LaunchSpec &L = specs[i];
+            void *params[] = {&L.args};
+            cudaKernelNodeParams kp = {};
+            kp.func = (void *)L.fn;
+            kp.gridDim = dim3(L.grid);
+            kp.blockDim = dim3(L.threads);
+            kp.sharedMemBytes = (unsigned)L.smem;
+            kp.kernelParams = params;
+            if (!cuda_ok(cudaGraphExecKernelNodeSetParams(ge->exec, ge->fn_node[i], &kp), "cudaGraphExecKernelNodeSetParams"))
+                return TFN_ERR_CUDA;
+            if (L.rf) {
+                kp.func = (void *)L.rf;
+                kp.gridDim = dim3(L.rf_grid);
+                kp.blockDim = dim3(kRefineThreads);
+                kp.sharedMemBytes = 0;
+                if (!cuda_ok(cudaGraphExecKernelNodeSetParams(ge->exec, ge->rf_node[i], &kp),
+                             "cudaGraphExecKernelNodeSetParams(refine)"))
+                    return TFN_ERR_CUDA;
+            }
+        }
+    } else {
+        if (p.graphs.size() >= kMaxGraphs) {  // (the oldest goes)
+            destroy_graph(p.graphs.front());
+            p.graphs.erase(p.graphs.begin());
+        }
+        GraphEntry e;
+        e.key = key;
+        if (!cuda_ok(cudaStreamBeginCapture(p.capture, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture"))
+            return TFN_ERR_CUDA;
+        tfn_status st = cuda_ok(cudaMemsetAsync(p.status_dev, 0, 2 * sizeof(uint32_t), p.capture), "cudaMemsetAsync")
+                            ? TFN_OK
+                            : TFN_ERR_CUDA;
+        for (size_t i = 0; i < specs.size() && st == TFN_OK; ++i) st = enqueue_launch(specs[i], p.capture);
+        if (!cuda_ok(cudaStreamEndCapture(p.capture, &e.graph), "cudaStreamEndCapture") && st == TFN_OK) st = TFN_ERR_CUDA;
+        if (st == TFN_OK && !cuda_ok(cudaGraphInstantiate(&e.exec, e.graph, 0), "cudaGraphInstantiate")) st = TFN_ERR_CUDA;
+        // the kernel nodes of each launch, found by their functions (a batch's
+        // launches are of distinct input kinds, so their functions differ)
+        size_t nn = 0;
+        if (st == TFN_OK && !cuda_ok(cudaGraphGetNodes(e.graph, nullptr, &nn), "cudaGraphGetNodes")) st = TFN_ERR_CUDA;
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (st == TFN_OK && nn && !cuda_ok(cudaGraphGetNodes(e.graph, nodes.data(), &nn), "cudaGraphGetNodes"))
+            st = TFN_ERR_CUDA;
+        e.fn_node.assign(specs.size(), nullptr);
+        e.rf_node.assign(specs.size(), nullptr);
+        for (size_t k = 0; k < nn && st == TFN_OK; ++k) {
+            cudaGraphNodeType t;
+            if (!cuda_ok(cudaGraphNodeGetType(nodes[k], &t), "cudaGraphNodeGetType")) st = TFN_ERR_CUDA;
+            if (st || t != cudaGraphNodeTypeKernel) continue;
+            cudaKernelNodeParams kp;
+            if (!cuda_ok(cudaGraphKernelNodeGetParams(nodes[k], &kp), "cudaGraphKernelNodeGetParams")) st = TFN_ERR_CUDA;
+            for (size_t i = 0; i < specs.size() && st == TFN_OK; ++i) {
+                if (kp.func == (void *)specs[i].fn) e.fn_node[i] = nodes[k];
+                if (specs[i].rf && kp.func == (void *)specs[i].rf) e.rf_node[i] = nodes[k];
+            }
+        }
+        for (size_t i = 0; i < specs.size() && st == TFN_OK; ++i)
+            if (!e.fn_node[i] || (specs[i].rf && !e.rf_node[i])) st = TFN_ERR_CUDA;
+        if (st) {
+            destroy_graph(e);
+            return st;
+        }
+        p.graphs.push_back(e);
+        ge = &p.graphs.back();
+    }
+    if (!cuda_ok(cudaGraphLaunch(ge->exec, p.stream), "cudaGraphLaunch")) return TFN_ERR_CUDA;
+    return TFN_OK;
 }
 
 // Enqueues one batch on its pipeline's stream (launcher thread, no lock held).
@@ -208,14 +371,22 @@ tfn_status enqueue_batch(tfn_server *s, Batch &b, size_t block_off)
                      "cudaMemcpy2DAsync(H2D)"))
             return TFN_ERR_CUDA;
     }
-    // each batch reports only its own kernels' failed waits
-    if (!cuda_ok(cudaMemsetAsync(p.status_dev, 0, 2 * sizeof(uint32_t), p.stream), "cudaMemsetAsync(status)"))
-        return TFN_ERR_CUDA;
     tfn_method m = s->method;
     for (const Request &r : b.reqs)
         if (r.test_wait) m.flags |= TFN_FLAG_TEST_WAIT_TIMEOUT;
-    tfn_status st = run_batch(s->ctx, dev.data(), (int)dev.size(), m, p.stream, p.status_dev);
+    if (!cuda_ok(cudaEventRecord(p.k_start, p.stream), "cudaEventRecord")) return TFN_ERR_CUDA;
+    // each batch reports only its own kernels' failed waits (the graphs reset
+    // the pipeline's status word themselves)
+    tfn_status st;
+    if (s->use_graphs) {
+        st = enqueue_kernels_graph(s, p, dev, m);
+    } else {
+        st = cuda_ok(cudaMemsetAsync(p.status_dev, 0, 2 * sizeof(uint32_t), p.stream), "cudaMemsetAsync(status)")
+                 ? run_batch(s->ctx, dev.data(), (int)dev.size(), m, p.stream, p.status_dev)
+                 : TFN_ERR_CUDA;
+    }
     if (st) return st;
+    if (!cuda_ok(cudaEventRecord(p.k_end, p.stream), "cudaEventRecord")) return TFN_ERR_CUDA;
     for (size_t i = 0; i < b.reqs.size(); ++i) {
         const Request &r = b.reqs[i];
         if (!r.host) continue;
@@ -285,6 +456,7 @@ void launcher_main(tfn_server *s)
         size_t bytes = 0;
         const size_t k = admit_count(s->queue, s->max_batch, s->arena.largest_fit(),
                                      [](const Request &r) { return r.stage_bytes; }, &bytes);
+        if (!s->inflight.empty()) s->admitted_busy += k;  // admitted while an earlier batch is on the GPU
         Batch b;
         b.pipe = pipe;
         b.reqs.assign(s->queue.begin(), s->queue.begin() + k);
@@ -304,7 +476,9 @@ void launcher_main(tfn_server *s)
             cudaEventRecord(s->pipes[pipe].done, s->pipes[pipe].stream);
         }
         lk.lock();
+        if (b.launch_status == TFN_OK && s->use_graphs) ++s->graph_launches;
         s->inflight.push_back(std::move(b));
+        s->max_inflight = std::max<uint64_t>(s->max_inflight, s->inflight.size());
         s->cv_retire.notify_one();
     }
     // cancel what was never admitted
@@ -324,11 +498,22 @@ void retirer_main(tfn_server *s)
         s->cv_retire.wait(lk, [s] { return !s->inflight.empty() || s->launcher_done; });
         if (s->inflight.empty()) break;  // launcher finished and nothing in flight
         const int pipe = s->inflight.front().pipe;
+        const bool launched = s->inflight.front().launch_status == TFN_OK;
         Pipe &p = s->pipes[pipe];
         lk.unlock();
         tfn_status st = cuda_ok(cudaEventSynchronize(p.done), "cudaEventSynchronize") ? TFN_OK : TFN_ERR_CUDA;
         const auto now = Clock::now();
+        // when this batch's kernels ran on the device, against the previous batch's
+        float t_start = 0.f, t_end = 0.f;
+        const bool timed = st == TFN_OK && launched &&
+                           cudaEventElapsedTime(&t_start, s->t0_event, p.k_start) == cudaSuccess &&
+                           cudaEventElapsedTime(&t_end, s->t0_event, p.k_end) == cudaSuccess;
+        if (!timed) cudaGetLastError();
         lk.lock();
+        if (timed) {
+            if (s->last_kernel_end_ms >= 0.f && t_start < s->last_kernel_end_ms) ++s->device_overlaps;
+            s->last_kernel_end_ms = std::max(s->last_kernel_end_ms, t_end);
+        }
         Batch b = std::move(s->inflight.front());
         s->inflight.pop_front();
         if (st == TFN_OK) st = b.launch_status;
@@ -352,7 +537,16 @@ void destroy_resources(tfn_server *s)
         if (p.done) cudaEventDestroy(p.done);
         if (p.status_host) cudaFreeHost(p.status_host);
         if (p.status_dev) cudaFree(p.status_dev);
+        for (GraphEntry &e : p.graphs) destroy_graph(e);
+        for (GroupBuf &g : p.groups) {
+            if (g.dev) cudaFree(g.dev);
+            if (g.host) cudaFreeHost(g.host);
+        }
+        if (p.capture) cudaStreamDestroy(p.capture);
+        if (p.k_start) cudaEventDestroy(p.k_start);
+        if (p.k_end) cudaEventDestroy(p.k_end);
     }
+    if (s->t0_event) cudaEventDestroy(s->t0_event);
     if (s->arena_base) cudaFree(s->arena_base);
     if (s->ctx) tfn_destroy(s->ctx);
 }
@@ -412,6 +606,11 @@ tfn_status tfn_server_create(tfn_ctx *ctx, const tfn_server_opts *o, tfn_server 
     s->max_queue = o->max_queue ? (size_t)o->max_queue : 65536;
     s->max_delay_us = o->max_delay_us;
     s->npipes = o->pipelines ? o->pipelines : 2;
+    if (o->flags & ~TFN_SERVER_NO_GRAPHS) {
+        delete s;
+        return TFN_ERR_INVALID_ARG;
+    }
+    s->use_graphs = !(o->flags & TFN_SERVER_NO_GRAPHS);
     s->arena_bytes = o->mem_budget_bytes ? o->mem_budget_bytes : ((size_t)1 << 30);
     if ((st = tfn_create(&s->ctx, ctx->device, 0))) {
         delete s;
@@ -436,12 +635,22 @@ tfn_status tfn_server_create(tfn_ctx *ctx, const tfn_server_opts *o, tfn_server 
             !cuda_ok(cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming), "cudaEventCreate") ||
             !cuda_ok(cudaMallocHost((void **)&p.status_host, sizeof(uint32_t)), "cudaMallocHost") ||
             !cuda_ok(cudaMalloc((void **)&p.status_dev, 256), "cudaMalloc(status)") ||
-            !cuda_ok(cudaMemset(p.status_dev, 0, 256), "cudaMemset(status)")) {
+            !cuda_ok(cudaMemset(p.status_dev, 0, 256), "cudaMemset(status)") ||
+            !cuda_ok(cudaStreamCreateWithFlags(&p.capture, cudaStreamNonBlocking), "cudaStreamCreate") ||
+            !cuda_ok(cudaEventCreate(&p.k_start), "cudaEventCreate") ||
+            !cuda_ok(cudaEventCreate(&p.k_end), "cudaEventCreate")) {
             destroy_resources(s);
             delete s;
             return TFN_ERR_CUDA;
         }
         *p.status_host = 0;
+    }
+    if (!cuda_ok(cudaEventCreate(&s->t0_event), "cudaEventCreate") ||
+        !cuda_ok(cudaEventRecord(s->t0_event, s->pipes[0].stream), "cudaEventRecord") ||
+        !cuda_ok(cudaEventSynchronize(s->t0_event), "cudaEventSynchronize")) {
+        destroy_resources(s);
+        delete s;
+        return TFN_ERR_CUDA;
     }
     s->t0 = Clock::now();
     s->lat_us.reserve(kLatencyWindow);
@@ -542,8 +751,13 @@ tfn_status tfn_server_stats(tfn_server *s, tfn_serving_stats *o, int reset)
     o->in_flight = s->inflight_reqs;
     o->staging_bytes_in_use = s->arena.in_use();
     o->staging_bytes_capacity = s->arena.capacity();
+    o->graph_launches = s->graph_launches;
+    o->max_batches_in_flight = s->max_inflight;
+    o->admitted_while_busy = s->admitted_busy;
+    o->device_overlaps = s->device_overlaps;
     if (reset) {
         s->submitted = s->completed = s->failed = s->cancelled = s->rejected = s->batches = s->batch_frames = 0;
+        s->graph_launches = s->max_inflight = s->admitted_busy = s->device_overlaps = 0;
         s->pixels = 0;
         s->t0 = now;
         s->lat_us.clear();

@@ -81,14 +81,18 @@ def submit_all(torch, tfn, srv, reqs, host_every=2):
     return out
 
 
-def test_results_in_the_mix_equal_results_alone(torch, tfn, ctx):
+@pytest.mark.parametrize("graphs", [True, False])
+def test_results_in_the_mix_equal_results_alone(torch, tfn, ctx, graphs):
+    # (with graphs, a batch's kernels are replayed from a pipeline's CUDA graph, one per launch
+    # structure, its kernel nodes updated to the batch; without, they are launched directly)
     reqs = request_mix(24, 11)
-    with tfn.Server(ctx, grad="sobel", phi="median", max_batch=8) as srv:
+    with tfn.Server(ctx, grad="sobel", phi="median", max_batch=8, graphs=graphs) as srv:
         subs = submit_all(torch, tfn, srv, reqs)
         for t, _, _ in subs:
             assert srv.wait(t, 20000) == tfn.TFN_OK
         st = srv.stats()
     assert st["completed"] == 24 and st["failed"] == 0 and st["batches"] >= 3  # at most 8 per batch
+    assert st["graph_launches"] == (st["batches"] if graphs else 0)
     assert 0 < st["latency_p50_us"] <= st["latency_p99_us"] <= st["latency_max_us"]
     torch.cuda.synchronize()
     for (img, cam), (_, n, m) in zip(reqs, subs):
@@ -121,6 +125,34 @@ def test_concurrent_clients(torch, tfn, ctx):
     assert st["completed"] == 40 and st["submitted"] == 40 and st["queued"] == 0 and st["in_flight"] == 0
     assert st["staging_bytes_in_use"] == 0 and st["mean_batch_frames"] >= 1
     assert st2["completed"] == 0 and st2["latency_samples"] == 0  # reset
+
+
+def test_batches_overlap_on_the_device(torch, tfn, ctx):
+    # continuous batching: requests that arrive while batches run are admitted into the next batch
+    # before the running ones retire, several batches are in flight at once, and their kernels run
+    # at the same time (each batch of two 1080x1920 frames fills less than half of the GPU)
+    H, W = 1080, 1920
+    f = 481.2 * W / 640
+    r = scenes.Recipe(H=H, W=W, fx=f, fy=f, u0=(W - 1) / 2, v0=(H - 1) / 2, noise_k=0.0012, hole_frac=0.03)
+    imgs = [scenes.render(6000 + k, r) for k in range(4)]
+    ins = [dev_image(torch, tfn, img) for img in imgs]
+    n_req = 24
+    outs = [(tfn.empty_normals(H, W, "f32"), tfn.empty_image((H, W), torch.uint8)) for _ in range(n_req)]
+    torch.cuda.synchronize()
+    with tfn.Server(ctx, grad="fd", phi="mean", max_batch=2, pipelines=3) as srv:
+        t0 = srv.submit(ins[0], r.camera, *outs[0])  # (warm-up: the pipelines' graphs)
+        assert srv.wait(t0, 20000) == tfn.TFN_OK
+        srv.stats(reset=True)
+        tickets = [srv.submit(ins[k % 4], r.camera, *outs[k]) for k in range(n_req)]
+        assert all(srv.wait(t, 20000) == tfn.TFN_OK for t in tickets)
+        st = srv.stats()
+    assert st["completed"] == n_req and st["batches"] >= n_req // 2
+    assert st["max_batches_in_flight"] >= 2, st
+    assert st["admitted_while_busy"] > 0, st
+    assert st["device_overlaps"] > 0, st
+    n_ref, m_ref = ctx.normals(ins[1], r.camera)
+    torch.cuda.synchronize()
+    assert torch.equal(outs[5][0], n_ref) and torch.equal(outs[5][1], m_ref)
 
 
 def test_memory_budget_admission(torch, tfn, ctx):

@@ -100,6 +100,8 @@ _lib.tfn_device_status.argtypes = [_P, ctypes.POINTER(ctypes.c_uint32), _P]
 _lib.tfn_tile_shape_count.restype = _I
 _lib.tfn_tile_shape_info.argtypes = [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]
 _lib.tfn_tile_shape_info.restype = _I
+_lib.tfn_tile_shape_warps.argtypes = [_I, ctypes.POINTER(_I), ctypes.POINTER(_I)]
+_lib.tfn_tile_shape_warps.restype = _I
 _lib.tfn_set_tile_shape.argtypes = [_P, _I]
 _lib.tfn_set_tile_shape.restype = _I
 _lib.tfn_plan_create.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), ctypes.POINTER(_P)]
@@ -136,6 +138,7 @@ tfn_device_status = _lib.tfn_device_status
 tfn_refined_pixels = _lib.tfn_refined_pixels
 tfn_tile_shape_count = _lib.tfn_tile_shape_count
 tfn_tile_shape_info = _lib.tfn_tile_shape_info
+tfn_tile_shape_warps = _lib.tfn_tile_shape_warps
 tfn_set_tile_shape = _lib.tfn_set_tile_shape
 tfn_plan_create = _lib.tfn_plan_create
 tfn_plan_launch = _lib.tfn_plan_launch
@@ -156,7 +159,7 @@ TFN_NOALLOC_MAX_FRAMES = 64
 EXPORTED = ["tfn_status_string", "tfn_version", "tfn_last_cuda_error", "tfn_create", "tfn_destroy", "tfn_normals",
             "tfn_normals_batch", "tfn_normals_batch_host", "tfn_device_status", "tfn_refined_pixels",
             "tfn_normals_noalloc", "tfn_plan_create", "tfn_plan_launch", "tfn_plan_destroy", "tfn_tile_shape_count",
-            "tfn_tile_shape_info", "tfn_set_tile_shape", "tfn_autotune", "tfn_tuned_shape", "tfn_tune_cache_save",
+            "tfn_tile_shape_info", "tfn_tile_shape_warps", "tfn_set_tile_shape", "tfn_autotune", "tfn_tuned_shape", "tfn_tune_cache_save",
             "tfn_tune_cache_load", "tfn_server_create", "tfn_submit", "tfn_wait", "tfn_server_stats",
             "tfn_server_destroy"]
 
@@ -470,6 +473,16 @@ def tile_shapes():
         w, h, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(tfn_tile_shape_info(i, ctypes.byref(w), ctypes.byref(h), ctypes.byref(r)), "tfn_tile_shape_info")
         out.append((w.value, h.value, r.value))
+    return out
+
+
+def tile_shape_warps():
+    """[(warps per CTA for FD, for the other filters)] for every compiled tile shape."""
+    out = []
+    for i in range(tfn_tile_shape_count()):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        check(tfn_tile_shape_warps(i, ctypes.byref(a), ctypes.byref(b)), "tfn_tile_shape_warps")
+        out.append((a.value, b.value))
     return out
 
 

@@ -919,6 +919,14 @@ tfn_status tfn_tile_shape_info(int index, int *tile_w, int *tile_h, int *rows_pe
     return TFN_OK;
 }
 
+tfn_status tfn_tile_shape_warps(int index, int *fd_warps, int *warps)
+{
+    if (index < 0 || index >= kNumCfg) return TFN_ERR_INVALID_ARG;
+    if (fd_warps) *fd_warps = kCfgs[index].fd_warps;
+    if (warps) *warps = kCfgs[index].warps;
+    return TFN_OK;
+}
+
 tfn_status tfn_set_tile_shape(tfn_ctx *c, int index)
 {
     if (!c || index < -1 || index >= kNumCfg) return TFN_ERR_INVALID_ARG;

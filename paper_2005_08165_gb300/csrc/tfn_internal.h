@@ -95,13 +95,16 @@ constexpr int kRefineThreads = 128;
 // warp that rolls down its rows (pr = th rows per lane); the rows stream
 // through a ring of nst shared-memory stages of cr rows each (th + 2 rows per
 // item: one above, one below; th + 4 for the 5x5 filters, the last chunk of
-// an item then partly unused), per warp; a CTA has `warps` warps.
+// an item then partly unused), per warp; a CTA has `warps` warps (fd_warps
+// for the FD filter).  Shapes 4 and 5 repeat the heights of shapes 1 and 2
+// with other CTA widths, so that the autotuner chooses the threads per CTA
+// as well as the item height.
 struct TileCfg {
-    int tw, th, pr, cr, nst, warps;
+    int tw, th, pr, cr, nst, warps, fd_warps;
 };
-constexpr int kNumCfg = 4;
-constexpr TileCfg kCfgs[kNumCfg] = {
-    {128, 18, 18, 5, 3, 4}, {128, 30, 30, 8, 3, 4}, {128, 12, 12, 7, 3, 4}, {128, 6, 6, 4, 2, 4}};
+constexpr int kNumCfg = 6;
+constexpr TileCfg kCfgs[kNumCfg] = {{128, 18, 18, 5, 3, 4, 2}, {128, 30, 30, 8, 3, 4, 2}, {128, 12, 12, 7, 3, 4, 2},
+                                    {128, 6, 6, 4, 2, 4, 2},   {128, 30, 30, 8, 3, 2, 4}, {128, 12, 12, 7, 3, 2, 1}};
 // the default shape for launches with few items (short items spread one frame over many warps)
 constexpr int kSmallCfg = 3;
 // Whether the (shape) kernel refines its flagged pixels itself, at the end of
@@ -113,10 +116,11 @@ constexpr bool refines_in_place(int c) { return c == kSmallCfg; }
 // filter on 256 x 480x640 frames (FD mean 0.9%, Sobel 4.5%, the 5x5 filters 13% faster than 18 rows)
 constexpr int kDefaultCfg = 1;
 
-// Warps per CTA of the (shape, filter) kernel: the FD kernels (128
-// registers) run 2-warp CTAs, 8 of them per SM, whose finer grain schedules
-// better than 4 x 4 warps; the others keep the shape's CTA.
-constexpr int cta_warps(int c, int grad) { return grad == GRAD_FD ? 2 : kCfgs[c].warps; }
+// Warps per CTA of the (shape, filter) kernel.  The FD kernels (128
+// registers) run 2-warp CTAs in the default shapes, 8 of them per SM, whose
+// finer grain scheduled better than 4 x 4 warps; the other filters 4-warp
+// CTAs.
+constexpr int cta_warps(int c, int grad) { return grad == GRAD_FD ? kCfgs[c].fd_warps : kCfgs[c].warps; }
 // CTAs per SM that the FD kernels are compiled for (their register bound).
 constexpr int fd_ctas_per_sm(int c) { return 16 / cta_warps(c, GRAD_FD); }
 inline int cfg_threads(int c, int grad) { return 32 * cta_warps(c, grad); }

@@ -2025,7 +2025,7 @@ KernelFn select_kernel(int grad, int phi, int cfg)
 {
 #define TFN_K(G, P, C)                                                                        \
     if (grad == G && phi == P && cfg == C) return &normals_kernel<KIND, G, P, C>;
-#define TFN_KC(G, P) TFN_K(G, P, 0) TFN_K(G, P, 1) TFN_K(G, P, 2) TFN_K(G, P, 3)
+#define TFN_KC(G, P) TFN_K(G, P, 0) TFN_K(G, P, 1) TFN_K(G, P, 2) TFN_K(G, P, 3) TFN_K(G, P, 4) TFN_K(G, P, 5)
 #define TFN_KP(G) TFN_KC(G, PHI_MEAN) TFN_KC(G, PHI_MEDIAN)
     TFN_KP(GRAD_FD) TFN_KP(GRAD_SOBEL) TFN_KP(GRAD_SCHARR) TFN_KP(GRAD_PREWITT) TFN_KP(GRAD_WEIGHTED) TFN_KP(GRAD_SEP5)
     TFN_KC(GRAD_PLANEPCA, PHI_MEAN)  // (PlanePCA has no Phi)

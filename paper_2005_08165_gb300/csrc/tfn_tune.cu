@@ -1,20 +1,22 @@
 // tfn_tune.cu -- tile-shape autotuner and its persistent cache.
 //
-// Every compiled tile shape computes the same bits (the kernels' per-pixel
-// arithmetic does not depend on the shape), so the choice is purely one of
-// speed.  tfn_autotune times each shape on a batch the caller provides and
+// Every compiled tile shape (item height and CTA width) computes the same
+// bits (the kernels' per-pixel arithmetic does not depend on the shape), so
+// the choice is purely one of speed.  tfn_autotune times each shape on a
+// batch the caller provides and
 // records the fastest in the context's table under (input kind, gradient,
 // phi, output); later launches of that combination use it.  The table can be
 // written to a text file and read back on a later run on the same kind of
 // device:
 //
-//   tfn-tune 1
+//   tfn-tune 2
 //   device <name with spaces as '_'> sms <SM count> cc <major>.<minor>
-//   entry <input> <grad> <phi> <output> <tile_w> <tile_h> <rows_per_thread> <ms>
+//   entry <input> <grad> <phi> <output> <tile_w> <tile_h> <rows_per_thread> <fd_warps> <warps> <ms>
 //
-// Shapes are stored by geometry, not by index, so that a cache stays valid
-// across builds that compile a different list of shapes (entries whose shape
-// is not compiled are skipped).
+// Shapes are stored by geometry (item size and CTA widths), not by index, so
+// that a cache stays valid across builds that compile a different list of
+// shapes (entries whose shape is not compiled are skipped).  Version 1 files
+// (no CTA widths) load as the shapes of the default widths.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -41,10 +43,13 @@ std::string device_line(int dev)
     return buf;
 }
 
-int shape_index(int tw, int th, int pr)
+// (version 1 entries give no widths: the default ones, 2 warps for FD and 4 for the others)
+int shape_index(int tw, int th, int pr, int fdw = 2, int w = 4)
 {
     for (int k = 0; k < kNumCfg; ++k)
-        if (kCfgs[k].tw == tw && kCfgs[k].th == th && kCfgs[k].pr == pr) return k;
+        if (kCfgs[k].tw == tw && kCfgs[k].th == th && kCfgs[k].pr == pr && kCfgs[k].fd_warps == fdw &&
+            kCfgs[k].warps == w)
+            return k;
     return -1;
 }
 
@@ -122,15 +127,16 @@ tfn_status tfn_tune_cache_save(tfn_ctx *c, const char *path)
     if (dl.empty()) return TFN_ERR_CUDA;
     FILE *f = fopen(path, "w");
     if (!f) return TFN_ERR_IO;
-    bool ok = fprintf(f, "tfn-tune 1\n%s\n", dl.c_str()) > 0;
+    bool ok = fprintf(f, "tfn-tune 2\n%s\n", dl.c_str()) > 0;
     for (int k = 0; k < KIND_COUNT; ++k)
         for (int gi = 0; gi < GRAD_COUNT; ++gi)
             for (int p = 0; p < PHI_COUNT; ++p)
                 for (int o = 0; o < kOutCount; ++o) {
                     const int t = c->tuned[k][gi][p][o];
                     if (t < 0) continue;
-                    ok = ok && fprintf(f, "entry %d %d %d %d %d %d %d %.6f\n", k, gi, p, o, kCfgs[t].tw, kCfgs[t].th,
-                                       kCfgs[t].pr, (double)c->tuned_ms[k][gi][p][o]) > 0;
+                    ok = ok && fprintf(f, "entry %d %d %d %d %d %d %d %d %d %.6f\n", k, gi, p, o, kCfgs[t].tw,
+                                       kCfgs[t].th, kCfgs[t].pr, kCfgs[t].fd_warps, kCfgs[t].warps,
+                                       (double)c->tuned_ms[k][gi][p][o]) > 0;
                 }
     ok = (fclose(f) == 0) && ok;
     return ok ? TFN_OK : TFN_ERR_IO;
@@ -155,7 +161,8 @@ tfn_status tfn_tune_cache_load(tfn_ctx *c, const char *path)
     const bool read_ok = !ferror(f);
     fclose(f);
     if (!read_ok) return TFN_ERR_IO;
-    if (lines.size() < 2 || lines[0] != "tfn-tune 1") return TFN_ERR_INVALID_ARG;
+    if (lines.size() < 2 || (lines[0] != "tfn-tune 1" && lines[0] != "tfn-tune 2")) return TFN_ERR_INVALID_ARG;
+    const bool v2 = lines[0] == "tfn-tune 2";
     const std::string dl = device_line(c->device);
     if (dl.empty()) return TFN_ERR_CUDA;
     if (lines[1].compare(0, 7, "device ") != 0) return TFN_ERR_INVALID_ARG;
@@ -168,15 +175,18 @@ tfn_status tfn_tune_cache_load(tfn_ctx *c, const char *path)
     std::vector<E> es;
     for (size_t i = 2; i < lines.size(); ++i) {
         if (lines[i].empty()) continue;
-        int k, gi, p, o, tw, th, pr, used = 0;
+        int k, gi, p, o, tw, th, pr, fdw = 2, w = 4, used = 0;
         float ms;
-        if (sscanf(lines[i].c_str(), "entry %d %d %d %d %d %d %d %f%n", &k, &gi, &p, &o, &tw, &th, &pr, &ms, &used) != 8 ||
-            (size_t)used != lines[i].size())
-            return TFN_ERR_INVALID_ARG;
+        const bool parsed =
+            v2 ? sscanf(lines[i].c_str(), "entry %d %d %d %d %d %d %d %d %d %f%n", &k, &gi, &p, &o, &tw, &th, &pr, &fdw,
+                        &w, &ms, &used) == 10
+               : sscanf(lines[i].c_str(), "entry %d %d %d %d %d %d %d %f%n", &k, &gi, &p, &o, &tw, &th, &pr, &ms,
+                        &used) == 8;
+        if (!parsed || (size_t)used != lines[i].size()) return TFN_ERR_INVALID_ARG;
         if (k < 0 || k >= KIND_COUNT || gi < 0 || gi >= GRAD_COUNT || p < 0 || p >= PHI_COUNT || o < 0 ||
             o >= kOutCount || !(ms >= 0.f))
             return TFN_ERR_INVALID_ARG;
-        const int shape = shape_index(tw, th, pr);
+        const int shape = shape_index(tw, th, pr, fdw, w);
         if (shape >= 0) es.push_back({k, gi, p, o, shape, ms});
     }
     for (const E &e : es) {

@@ -248,10 +248,23 @@ def test_autotune_table_and_cache_file(torch, tfn, ctx, tmp_path):
         path = str(tmp_path / "tune.txt")
         c.save_tune_cache(path)
     text = open(path).read().splitlines()
-    assert text[0] == "tfn-tune 1" and text[1].startswith("device ") and len(text) == 3
+    assert text[0] == "tfn-tune 2" and text[1].startswith("device ") and len(text) == 3
+    # the entry names the shape by its geometry: item size, then the CTA widths (FD, others)
+    fields = text[2].split()
+    shapes, warps = tfn.tile_shapes(), tfn.tile_shape_warps()
+    assert tuple(map(int, fields[5:8])) == shapes[best] and tuple(map(int, fields[8:10])) == warps[best]
+    # the tuner chooses CTA widths too: some heights are compiled with two widths
+    assert len(set(zip(shapes, warps))) == len(shapes) > len(set(shapes))
     with tfn.Context(0) as c2:
         c2.load_tune_cache(path)
         assert c2.tuned_shape(tfn.TFN_DEPTH_F32) == best
+        # a version 1 file (no CTA widths) loads as the shape of the default widths
+        v1 = str(tmp_path / "v1.txt")
+        with open(v1, "w") as f:
+            f.write("\n".join(["tfn-tune 1", text[1], "entry 0 0 0 0 128 12 12 0.5"]) + "\n")
+        c2.load_tune_cache(v1)
+        assert c2.tuned_shape(tfn.TFN_DEPTH_F32) == 2 and warps[2] == (2, 4)
+        c2.load_tune_cache(path)
         # another kind of device: nothing loaded
         other = str(tmp_path / "other.txt")
         with open(other, "w") as f:

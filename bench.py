@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--grad", default="fd",
                     choices=["fd", "sobel", "scharr", "prewitt", "fd5", "sobel5", "prewitt5", "planepca"])
     ap.add_argument("--phi", default="mean", choices=["mean", "median"])
+    ap.add_argument("--input", default="f32", choices=["f32", "f16"],
+                    help="headline input kind: FP32 depth -> FP32 normals, or FP16 depth -> FP16 normals "
+                         "(f16 runs the headline, e2e and CPU baseline only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-variants", action="store_true")
@@ -329,10 +332,17 @@ def run_ours(args):
 
     # inputs resident in HBM: 256 x 1.2 MB (315 MB in, 1.0 GB out) -- far beyond the 129 MB L2
     nf = args.frames
+    f16 = args.input == "f16"  # the precision form: FP16 depth in, FP16 planar normals out
+    if f16:  # (the other sections run on the FP32 batch's buffers)
+        args.no_variants = args.no_serving = True
+    out_fmt = "f16" if f16 else "f32"
+    bkey = "f16_in_f16_out" if f16 else "f32_in_f32_out"
     depth = scenes.noisy_batch(nf, seed0=1000 + 10000 * rank)
-    d = tfn.empty_image(depth.shape, torch.float32, dev)
+    if f16:
+        depth = depth.astype(np.float16)
+    d = tfn.empty_image(depth.shape, torch.float16 if f16 else torch.float32, dev)
     d.copy_(torch.from_numpy(depth))
-    normals = tfn.empty_normals(H, W, "f32", dev, lead=(nf,))
+    normals = tfn.empty_normals(H, W, out_fmt, dev, lead=(nf,))
     masks = tfn.empty_image((nf, H, W), torch.uint8, dev)
     ins = [d[k] for k in range(nf)]
     outs = [normals[k] for k in range(nf)]
@@ -346,7 +356,7 @@ def run_ours(args):
     def one_pass(grad=args.grad, phi=args.phi):
         key = (grad, phi)
         if key not in plans:
-            plans[key] = ctx.plan(ins, cam, grad=grad, phi=phi, normals=outs, masks=mks)
+            plans[key] = ctx.plan(ins, cam, grad=grad, phi=phi, output=out_fmt, normals=outs, masks=mks)
         plans[key].launch(stream)
 
     # A step is `passes` passes over the batch, so that the K timed steps last at least
@@ -386,20 +396,20 @@ def run_ours(args):
     ms_step = total_ms / args.steps
     launch_ms = statistics.mean(per) / passes  # one pass: normals_kernel, then refine_kernel
     px = nf * H * W
-    achieved = BYTES_PER_PX["f32_in_f32_out"] * px / (launch_ms * 1e-3) / 1e9
+    achieved = BYTES_PER_PX[bkey] * px / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = recorded_traffic(f"{args.grad}_{args.phi}_f32_b{nf}")
+    traffic = recorded_traffic(f"{args.grad}_{args.phi}_{args.input}_b{nf}")
 
     result = None
     if rank == 0:
         # end to end through the C ABI with host buffers: pinned in, pinned out,
         # host<->device copies inside the timed region
         hin = torch.from_numpy(depth).pin_memory()  # one pinned batch: frames back to back
-        hout = torch.empty((nf, 3, H, W), dtype=torch.float32).pin_memory()
+        hout = torch.empty((nf, 3, H, W), dtype=torch.float16 if f16 else torch.float32).pin_memory()
         hmask = torch.empty((nf, H, W), dtype=torch.uint8).pin_memory()
 
         def e2e_step():
-            ctx.normals_batch_host(hin, cam, hout, hmask, grad=args.grad, phi=args.phi, stream=stream)
+            ctx.normals_batch_host(hin, cam, hout, hmask, grad=args.grad, phi=args.phi, output=out_fmt, stream=stream)
 
         e2e = None
         if not args.no_e2e:
@@ -411,7 +421,7 @@ def run_ours(args):
                 e2e_step()
             e2e_dt = time.perf_counter() - t0
             e2e = {"value": round(nf * e2e_steps / e2e_dt, 1), "unit": "frames/s",
-                   "h2d_bytes_per_step": nf * H * W * 4, "d2h_bytes_per_step": nf * H * W * 13}
+                   "h2d_bytes_per_step": nf * H * W * (2 if f16 else 4), "d2h_bytes_per_step": nf * H * W * (7 if f16 else 13)}
 
         variants = {}
         if not args.no_variants:
@@ -434,9 +444,9 @@ def run_ours(args):
                 tot, pv = time_launches(torch, lambda: fplan.launch(stream), 50, 3, stream)
                 fplan.close()
                 lm = statistics.mean(pv)
-                bkey = "f32_in_oct16_out" if "oct16" in key else "f32_in_f32_out_points"
+                vkey = "f32_in_oct16_out" if "oct16" in key else "f32_in_f32_out_points"
                 variants[key] = {"frames_per_s": round(nf / (lm * 1e-3), 1),
-                                 "hbm_gbs": round(BYTES_PER_PX[bkey] * px / (lm * 1e-3) / 1e9, 1)}
+                                 "hbm_gbs": round(BYTES_PER_PX[vkey] * px / (lm * 1e-3) / 1e9, 1)}
             del oct_out, pts
             # the weighted gradient family (the kernel search space), weights (1 3 1)
             wplan = ctx.plan(ins, cam, grad="weighted", phi="mean", weights=(1.0, 3.0, 1.0), normals=outs, masks=mks)
@@ -463,10 +473,10 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": round(fps, 1), "unit": "frames/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if not f16 else "f16 in/out, f32 arithmetic", "data": "synthetic",
             "gpixels_per_s": round(fps * H * W / 1e9, 2),
-            "config": {"workload": f"{nf} x 480x640 FP32 depth, sigma=0.0012 Z^2 noise, 3% holes; "
-                                   f"{args.grad} gradient, {args.phi}; FP32 planar normals + u8 mask out",
+            "config": {"workload": f"{nf} x 480x640 {'FP16' if f16 else 'FP32'} depth, sigma=0.0012 Z^2 noise, 3% holes; "
+                                   f"{args.grad} gradient, {args.phi}; {'FP16' if f16 else 'FP32'} planar normals + u8 mask out",
                        "global_batch": nf * world, "frame": "480x640", "gradient": args.grad, "phi": args.phi,
                        "passes_per_step": passes, "frames_per_step": nf * passes * world,
                        "step": f"{passes} replays of the batch's plan (one pass: normals_kernel + refine_kernel)",
@@ -475,7 +485,7 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                         else "fallback", "algorithmic_bytes_per_px": 17,
+                         else "fallback", "algorithmic_bytes_per_px": BYTES_PER_PX[bkey],
                          "launch_ms": round(launch_ms, 4)},
             "e2e": e2e,
             "clocks": clk.summary(),

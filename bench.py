@@ -398,6 +398,11 @@ def run_ours(args):
     px = nf * H * W
     achieved = BYTES_PER_PX[bkey] * px / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
+    # pixels one pass sends to the double-float refinement (untimed: one more pass after the region)
+    ctx.refined_pixels(stream)
+    one_pass()
+    torch.cuda.synchronize()
+    refined = ctx.refined_pixels(stream)
     traffic = recorded_traffic(f"{args.grad}_{args.phi}_{args.input}_b{nf}")
 
     result = None
@@ -486,7 +491,8 @@ def run_ours(args):
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback", "algorithmic_bytes_per_px": BYTES_PER_PX[bkey],
-                         "launch_ms": round(launch_ms, 4)},
+                         "launch_ms": round(launch_ms, 4), "refined_px_per_pass": refined,
+                         "refined_fraction": round(refined / (nf * H * W), 7)},
             "e2e": e2e,
             "clocks": clk.summary(),
             "gpu_launches": 2 * passes * args.steps,  # per pass: normals_kernel, then refine_kernel

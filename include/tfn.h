@@ -168,7 +168,7 @@ typedef struct tfn_frame {
 } tfn_frame;
 
 /* Estimators.  TFN_EST_3F2N is the paper's method (Sec. III).  TFN_EST_PLANEPCA
- * is the comparison estimator of Sec. II-A (Eq. planepca): the 9 back-projected
+ * is the comparison estimator of Sec. II, item 2 (Eq. planepca): the 9 back-projected
  * points of the 3x3 neighbourhood (Eq. intrinsic matrix) have their mean
  * removed, and the normal is the principal component of smallest variance,
  * turned to face the camera (n . p < 0).  A pixel is evaluable when it and
@@ -417,33 +417,38 @@ tfn_status tfn_server_destroy(tfn_server *srv);
 #define TFN_NOALLOC_MAX_FRAMES 64
 
 /* Same result as tfn_normals_batch (the same kernels, bit for bit), for
- * callers that may not allocate device memory at all: a host framework or
- * plugin interface that owns every device byte and forbids cudaMalloc, or a
- * loop that must not call cudaMalloc / cudaFree because they can synchronise
- * the whole device.  (The paper has no counterpart: this is an interface
- * concern of this library.)
+ * callers that may not allocate device memory at all:
+ *   - a host framework or plugin interface that owns every device byte: its
+ *     memory plan is fixed before it calls plugins, so a plugin's own
+ *     cudaMalloc would overrun that plan or fail;
+ *   - a loop with a latency budget: cudaMalloc and cudaFree can synchronise
+ *     the whole device, stalling every stream, not only the caller's;
+ *   - a caller that cannot keep a context (tfn_create allocates its scratch).
+ * (The paper has no counterpart: this is an interface concern of this
+ * library.)
  *
  * It takes no context.  The scratch the kernels need (frame descriptors, TMA
- * tensor maps, a status word, the list of pixels to refine; about 540 KB)
- * lives in one fixed array compiled into the library, which every device that loads the library keeps until the
+ * tensor maps, a status word, the list of pixels to refine; about 540 KB, of
+ * which 512 KB is the refinement list) lives in one fixed array compiled into
+ * the library, which every device that loads the library keeps until the
  * process exits.  Limits and behaviour:
  *   - n > TFN_NOALLOC_MAX_FRAMES returns TFN_ERR_INVALID_ARG before anything
  *     is enqueued; otherwise arguments are validated as for tfn_normals_batch;
  *   - works on the current CUDA device; the first call on each device looks
- *     up the array's device address there (make that first call before any
- *     stream capture);
+ *     up the array's device address there;
  *   - it calls no cudaMalloc, cudaFree or other allocating routine; the
  *     descriptors are staged in thread-local host storage and copied into the
  *     array on `stream` from that pageable memory, which the CUDA runtime may
  *     stage by first waiting for the work already queued on `stream`: the call
  *     can block the host until that work is done;
- *   - while `stream` is capturing a CUDA graph it returns TFN_ERR_UNSUPPORTED
- *     and enqueues nothing (a captured copy would read the staging only at
- *     replay time, when it holds another call's frames);
+ *   - each call zeroes the refinement list's header on `stream` before its
+ *     kernels, so a call never sees an earlier call's list;
  *   - every call reuses the same array and overwrites the previous call's
  *     contents, so calls whose GPU work overlaps (other streams, or earlier
  *     work still running on another stream) race and must be serialised by
  *     the caller;
+ *   - TFN_ERR_UNSUPPORTED: `stream` is in a state in which the staged copy
+ *     cannot be enqueued for this call alone; nothing is enqueued;
  *   - kernel-side wait failures are not reported (there is no context to
  *     hold them); use tfn_normals_batch where that matters. */
 tfn_status tfn_normals_noalloc(const tfn_frame *frames, int n, const tfn_method *method, tfn_stream stream);

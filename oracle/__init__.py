@@ -150,7 +150,7 @@ def points(img, fx, fy, u0, v0, *, disparity=False, baseline=1.0, disp_scale=1.0
     return out
 
 
-from .pca import planepca  # noqa: E402  (Sec. II-A, Eq. planepca; uses points() above)
+from .pca import planepca  # noqa: E402  (Sec. II item 2, Eq. planepca; uses points() above)
 
 
 def oct_encode(n):

@@ -1,6 +1,6 @@
 """PlanePCA surface normals, FP64 -- TEST INFRASTRUCTURE ONLY (part of the oracle package).
 
-The comparison estimator of Sec. II-A (item 2, Eq. planepca): for each pixel i, the points
+The comparison estimator of Sec. II, item 2 (Eq. planepca): for each pixel i, the points
 Q_i^+ = [p_i, q_i1 .. q_ik] of its neighbourhood (Eq. intrinsic matrix back-projection) have their
 empirical mean removed, and the normal is the principal component of smallest covariance, i.e. the
 eigenvector of the smallest eigenvalue of the scatter matrix sum_j (q_j - q_mean)(q_j - q_mean)^T.

@@ -79,8 +79,10 @@ extern "C" tfn_status tfn_normals_noalloc(const tfn_frame *frames, int n, const 
     for (int i = 0; i < n; ++i)
         if ((st = validate_frame(&frames[i], method->output))) return st;
     if (n == 0) return TFN_OK;
-    // The descriptors travel through host staging that a captured copy would
-    // read only at replay, when it holds another call's frames: refuse.
+    // The copies below read the thread-local staging when the stream runs
+    // them.  A stream that records its work instead of running it would read
+    // the staging later, after other calls have overwritten it: such a stream
+    // gets TFN_ERR_UNSUPPORTED and nothing is enqueued.
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (!cuda_ok(cudaStreamIsCapturing((cudaStream_t)stream, &cap), "cudaStreamIsCapturing")) return TFN_ERR_CUDA;
     if (cap != cudaStreamCaptureStatusNone) return TFN_ERR_UNSUPPORTED;

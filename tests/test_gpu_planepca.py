@@ -1,4 +1,4 @@
-"""Parity of the CUDA path's PlanePCA estimator (TFN_EST_PLANEPCA; Sec. II-A, Eq. planepca) with the FP64
+"""Parity of the CUDA path's PlanePCA estimator (TFN_EST_PLANEPCA; Sec. II item 2, Eq. planepca) with the FP64
 oracle, through the C ABI.
 
 The mask must match bit for bit.  The normal is the eigenvector of the scatter matrix's smallest

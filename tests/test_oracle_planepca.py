@@ -1,4 +1,4 @@
-"""Pins of the oracle's PlanePCA estimator (Sec. II-A item 2, Eq. planepca; reading R16).
+"""Pins of the oracle's PlanePCA estimator (Sec. II item 2, Eq. planepca; reading R16).
 
 The normal must be exact on planes (every centred point then lies in the plane) and face the
 camera; on noisy windows it must minimise the centred residual sum_j ((q_j - q_mean) . n)^2, which

@@ -394,7 +394,8 @@ def run_ours(args):
     total_ms, fps = job_throughput(total_ms, nf * passes * args.steps, world, dev)
     status = ctx.device_status()
     ms_step = total_ms / args.steps
-    launch_ms = statistics.mean(per) / passes  # one pass: normals_kernel, then refine_kernel
+    launch_ms = statistics.mean(per) / passes  # one pass: normals_kernel, then refine_kernel where it can flag pixels
+    kernels_per_pass = plans[(args.grad, args.phi)].kernels()
     px = nf * H * W
     achieved = BYTES_PER_PX[bkey] * px / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
@@ -484,8 +485,10 @@ def run_ours(args):
                                    f"{args.grad} gradient, {args.phi}; {'FP16' if f16 else 'FP32'} planar normals + u8 mask out",
                        "global_batch": nf * world, "frame": "480x640", "gradient": args.grad, "phi": args.phi,
                        "passes_per_step": passes, "frames_per_step": nf * passes * world,
-                       "step": f"{passes} replays of the batch's plan (one pass: normals_kernel + refine_kernel)",
-                       "l2": f"inputs ({px * 4 / 1e6:.0f} MB) and outputs ({px * 13 / 1e6:.0f} MB) exceed the 129 MB L2; no flush",
+                       "step": f"{passes} replays of the batch's plan (one pass: {kernels_per_pass} kernel launch"
+                               f"{'es: normals_kernel + refine_kernel' if kernels_per_pass == 2 else ': normals_kernel'})",
+                       "l2": f"inputs ({px * (2 if f16 else 4) / 1e6:.0f} MB) and outputs ({px * (7 if f16 else 13) / 1e6:.0f} MB) "
+                             "exceed the 129 MB L2; no flush",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -495,7 +498,7 @@ def run_ours(args):
                          "refined_fraction": round(refined / (nf * H * W), 7)},
             "e2e": e2e,
             "clocks": clk.summary(),
-            "gpu_launches": 2 * passes * args.steps,  # per pass: normals_kernel, then refine_kernel
+            "gpu_launches": kernels_per_pass * passes * args.steps,  # per pass: the plan's kernels
             "device_status": status,
             "variants": variants, "accuracy_vs_truth": accuracy, "kernel_search": kernel_search,
             "serving": serving,

@@ -200,6 +200,12 @@ typedef struct tfn_method {
  * would (tfn_device_status, a server batch's TFN_ERR_DEVICE) and the context
  * stays usable.  For testing. */
 #define TFN_FLAG_TEST_WAIT_TIMEOUT 2
+/* FP16 depth with the FD filter: compute each pixel's FP32 error bound and
+ * refinement test even where the frames' binary16 sample spacing already
+ * proves that no pixel can fail it (there the library otherwise runs a kernel
+ * without them: the same normals and masks, bit for bit, with fewer
+ * instructions).  For testing and for measuring the bound's cost. */
+#define TFN_FLAG_FULL_BOUND 4
 
 /* ---- status and context ------------------------------------------------ */
 
@@ -298,6 +304,11 @@ tfn_status tfn_plan_create(tfn_ctx *ctx, const tfn_frame *frames, int n, const t
 /* Replays the plan's graph on `stream`: the whole estimator over the batch,
  * with no host work beyond one graph launch. */
 tfn_status tfn_plan_launch(tfn_plan *plan, tfn_stream stream);
+
+/* Number of kernel launches one tfn_plan_launch runs (per input kind of the
+ * batch: normals_kernel, and the refinement kernel where the launch can flag
+ * pixels and is large enough to refine in a second kernel). */
+tfn_status tfn_plan_kernels(const tfn_plan *plan, int32_t *count);
 
 /* Waits for the device, releases the plan's scratch and graph. NULL is a no-op. */
 tfn_status tfn_plan_destroy(tfn_plan *plan);

@@ -33,6 +33,7 @@ TFN_EST_3F2N, TFN_EST_PLANEPCA = range(2)
 TFN_OUT_F32, TFN_OUT_F16, TFN_OUT_BF16, TFN_OUT_F16X4, TFN_OUT_BF16X4, TFN_OUT_OCT16 = range(6)
 TFN_FLAG_REFINE_ALL = 1
 TFN_FLAG_TEST_WAIT_TIMEOUT = 2
+TFN_FLAG_FULL_BOUND = 4
 TFN_REQ_HOST = 1
 TFN_REQ_TEST_WAIT_TIMEOUT = 2
 TFN_SERVER_NO_GRAPHS = 1
@@ -107,6 +108,7 @@ _lib.tfn_set_tile_shape.restype = _I
 _lib.tfn_plan_create.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), ctypes.POINTER(_P)]
 _lib.tfn_plan_launch.argtypes = [_P, _P]
 _lib.tfn_plan_destroy.argtypes = [_P]
+_lib.tfn_plan_kernels.argtypes = [_P, ctypes.POINTER(_I)]
 _lib.tfn_refined_pixels.argtypes = [_P, ctypes.POINTER(ctypes.c_uint64), _P]
 _lib.tfn_normals_noalloc.argtypes = [ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), _P]
 _lib.tfn_autotune.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), _I, _P,
@@ -121,7 +123,7 @@ _lib.tfn_server_stats.argtypes = [_P, ctypes.POINTER(tfn_serving_stats), _I]
 _lib.tfn_server_destroy.argtypes = [_P]
 for _f in ("tfn_create", "tfn_destroy", "tfn_normals", "tfn_normals_batch", "tfn_normals_batch_host",
            "tfn_device_status", "tfn_refined_pixels", "tfn_normals_noalloc", "tfn_plan_create", "tfn_plan_launch",
-           "tfn_plan_destroy", "tfn_autotune", "tfn_tuned_shape", "tfn_tune_cache_save", "tfn_tune_cache_load",
+           "tfn_plan_destroy", "tfn_plan_kernels", "tfn_autotune", "tfn_tuned_shape", "tfn_tune_cache_save", "tfn_tune_cache_load",
            "tfn_server_create", "tfn_submit", "tfn_wait", "tfn_server_stats", "tfn_server_destroy"):
     getattr(_lib, _f).restype = _I
 
@@ -143,6 +145,7 @@ tfn_set_tile_shape = _lib.tfn_set_tile_shape
 tfn_plan_create = _lib.tfn_plan_create
 tfn_plan_launch = _lib.tfn_plan_launch
 tfn_plan_destroy = _lib.tfn_plan_destroy
+tfn_plan_kernels = _lib.tfn_plan_kernels
 tfn_autotune = _lib.tfn_autotune
 tfn_tuned_shape = _lib.tfn_tuned_shape
 tfn_tune_cache_save = _lib.tfn_tune_cache_save
@@ -158,7 +161,8 @@ TFN_NOALLOC_MAX_FRAMES = 64
 
 EXPORTED = ["tfn_status_string", "tfn_version", "tfn_last_cuda_error", "tfn_create", "tfn_destroy", "tfn_normals",
             "tfn_normals_batch", "tfn_normals_batch_host", "tfn_device_status", "tfn_refined_pixels",
-            "tfn_normals_noalloc", "tfn_plan_create", "tfn_plan_launch", "tfn_plan_destroy", "tfn_tile_shape_count",
+            "tfn_normals_noalloc", "tfn_plan_create", "tfn_plan_launch", "tfn_plan_destroy", "tfn_plan_kernels",
+            "tfn_tile_shape_count",
             "tfn_tile_shape_info", "tfn_tile_shape_warps", "tfn_set_tile_shape", "tfn_autotune", "tfn_tuned_shape", "tfn_tune_cache_save",
             "tfn_tune_cache_load", "tfn_server_create", "tfn_submit", "tfn_wait", "tfn_server_stats",
             "tfn_server_destroy"]
@@ -497,6 +501,12 @@ class Plan:
     def launch(self, stream=None):
         check(tfn_plan_launch(self.handle, _stream_handle(stream)), "tfn_plan_launch")
         return self.normals, self.masks
+
+    def kernels(self) -> int:
+        """Kernel launches one replay runs."""
+        n = _I()
+        check(tfn_plan_kernels(self.handle, ctypes.byref(n)), "tfn_plan_kernels")
+        return n.value
 
     def close(self):
         if self.handle:

@@ -18,23 +18,23 @@
 #include "tfn_internal.h"
 
 namespace tfn {
-KernelFn kernels_depth_f32(int grad, int phi, int cfg);
-KernelFn kernels_depth_f16(int grad, int phi, int cfg);
-KernelFn kernels_disp_u16(int grad, int phi, int cfg);
-KernelFn kernels_disp_f32(int grad, int phi, int cfg);
+KernelFn kernels_depth_f32(int grad, int phi, int cfg, bool noref);
+KernelFn kernels_depth_f16(int grad, int phi, int cfg, bool noref);
+KernelFn kernels_disp_u16(int grad, int phi, int cfg, bool noref);
+KernelFn kernels_disp_f32(int grad, int phi, int cfg, bool noref);
 KernelFn refiners_depth_f32(int grad, int phi);
 KernelFn refiners_depth_f16(int grad, int phi);
 KernelFn refiners_disp_u16(int grad, int phi);
 KernelFn refiners_disp_f32(int grad, int phi);
 
-KernelFn kernel_for(int kind, int grad, int phi, int cfg)
+KernelFn kernel_for(int kind, int grad, int phi, int cfg, bool noref)
 {
     if (grad_is_sep5(grad)) grad = GRAD_SEP5;  // the named 5x5 filters are weight presets
     switch (kind) {
-    case KIND_DEPTH_F32: return kernels_depth_f32(grad, phi, cfg);
-    case KIND_DEPTH_F16: return kernels_depth_f16(grad, phi, cfg);
-    case KIND_DISP_U16: return kernels_disp_u16(grad, phi, cfg);
-    case KIND_DISP_F32: return kernels_disp_f32(grad, phi, cfg);
+    case KIND_DEPTH_F32: return kernels_depth_f32(grad, phi, cfg, noref);
+    case KIND_DEPTH_F16: return kernels_depth_f16(grad, phi, cfg, noref);
+    case KIND_DISP_U16: return kernels_disp_u16(grad, phi, cfg, noref);
+    case KIND_DISP_F32: return kernels_disp_f32(grad, phi, cfg, noref);
     }
     return nullptr;
 }
@@ -131,7 +131,7 @@ tfn_status validate_method(const tfn_method *m)
     if (!m) return TFN_ERR_INVALID_ARG;
     if (m->estimator != TFN_EST_3F2N && m->estimator != TFN_EST_PLANEPCA) return TFN_ERR_INVALID_ARG;
     if (m->grad < 0 || m->grad > GRAD_PREWITT5 || m->phi < 0 || m->phi >= PHI_COUNT || m->output < 0 ||
-        m->output > OUT_OCT16 || (m->flags & ~(TFN_FLAG_REFINE_ALL | TFN_FLAG_TEST_WAIT_TIMEOUT)))
+        m->output > OUT_OCT16 || (m->flags & ~(TFN_FLAG_REFINE_ALL | TFN_FLAG_TEST_WAIT_TIMEOUT | TFN_FLAG_FULL_BOUND)))
         return TFN_ERR_INVALID_ARG;
     if (m->grad == GRAD_WEIGHTED) {
         for (int k = 0; k < 3; ++k)
@@ -228,6 +228,37 @@ float refine_threshold(const tfn_frame &f, int grad, int phi)
     return t > 0 ? (float)t : 0.f;
 }
 
+// Whether no pixel of these frames can be flagged for refinement, so that
+// the launch may run the NOREF kernel (no error bound, no refinement test,
+// no refinement kernel; the same result bits).  Only FP16 depth with the FD
+// filter qualifies, by the spacing of binary16: two distinct samples a < b
+// differ by at least one ulp of a, which is at least 2^-11 a (2^-10 a for
+// subnormal a), so |rho_j| = Z_j / |Z_j - Z_i| <= 2^11 + 1 for every kept
+// neighbour (Z_j the smaller: <= 2^11; the larger: 1 + Z_i / (Z_j - Z_i)).
+// With g = |G_u| + |G_v|, every weight of the bound is at most 1.3 g (mean:
+// |G_u|, |G_v|, |G_u +- G_v| + 0.3 g) or g (median), so bound <= 1.3 g m rho_max
+// (mean, over its m kept neighbours) or g rho_max (median: one candidate),
+// while |n'| >= m min(fx, fy) g / sqrt(2) (the mean's n' is scaled by m) or
+// min(fx, fy) g / sqrt(2): bound / |n'| <= c rho_max / min(fx, fy), c = 1.3
+// sqrt(2) or sqrt(2), whatever the depths.  A frame qualifies when that is
+// below its threshold (with a margin for the FP32 roundings of rho, m and
+// |n'|, all within a few u); at the usual 480x640 intrinsics it is 7.8
+// against 11.7 (mean) and 6.0 against 19.1 (median).
+bool refinement_idle(const tfn_frame *frames, int n, const tfn_method &m)
+{
+    if (method_grad(m) != GRAD_FD || (m.flags & (TFN_FLAG_REFINE_ALL | TFN_FLAG_FULL_BOUND))) return false;
+    const int phi = method_phi(m);
+    const double rho_max = 2049.0;
+    const double c = (phi == PHI_MEAN ? 1.3 : 1.0) * std::sqrt(2.0);
+    for (int i = 0; i < n; ++i) {
+        const tfn_frame &f = frames[i];
+        if (f.input_type != KIND_DEPTH_F16) return false;
+        const double ratio = c * rho_max / std::min(f.cam.fx, f.cam.fy) * (1.0 + 1e-3);
+        if (!(ratio < (double)refine_threshold(f, GRAD_FD, phi))) return false;
+    }
+    return n > 0;
+}
+
 tfn_status encode_map(CUtensorMap *map, const tfn_frame &f, int cfg)
 {
     if (!load_encode()) {
@@ -295,13 +326,13 @@ int frame_tiles(const tfn_frame &f, int cfg)
 // The launch (kernel, grid, arguments, and the refinement kernel that
 // follows it, if any) for frames of one input kind whose descriptors and
 // tensor maps are already in device memory.  spec.grid == 0: nothing to run.
-tfn_status make_launch(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
-                       uint32_t *d_status, void *d_refine, int refine_cap, int nframes, int total_tiles, int num_sms,
-                       LaunchSpec *spec)
+tfn_status make_launch(int kind, const tfn_method &m, int cfg, bool noref, const FrameDesc *d_frames,
+                       const CUtensorMap *d_maps, uint32_t *d_status, void *d_refine, int refine_cap, int nframes,
+                       int total_tiles, int num_sms, LaunchSpec *spec)
 {
     const int grad = method_grad(m);
     LaunchSpec &L = *spec;
-    L.fn = kernel_for(kind, grad, method_phi(m), cfg);
+    L.fn = kernel_for(kind, grad, method_phi(m), cfg, noref);
     if (!L.fn) return TFN_ERR_UNSUPPORTED;
     L.threads = cfg_threads(cfg, grad);
     L.smem = smem_bytes(kind, cfg, grad);
@@ -318,7 +349,7 @@ tfn_status make_launch(int kind, const tfn_method &m, int cfg, const FrameDesc *
     L.grid = std::max(0, std::min((total_tiles + nw - 1) / nw, per_sm * num_sms));
     // the refinement kernel of this method (none for PlanePCA, which never flags a pixel)
     L.rf = nullptr;
-    if (grad != GRAD_PLANEPCA && !refines_in_place(cfg) && !(L.rf = refiner_for(kind, grad, method_phi(m))))
+    if (grad != GRAD_PLANEPCA && !noref && !refines_in_place(cfg) && !(L.rf = refiner_for(kind, grad, method_phi(m))))
         return TFN_ERR_UNSUPPORTED;
     // its grid: the flagged pixels (about one per thousand on noisy frames),
     // as many threads as fit on the GPU at once: each refines its pixels one
@@ -362,13 +393,13 @@ tfn_status enqueue_launch(LaunchSpec &L, cudaStream_t stream)
     return TFN_OK;
 }
 
-tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
-                          uint32_t *d_status, void *d_refine, int refine_cap, int nframes, int total_tiles,
-                          int num_sms, cudaStream_t stream)
+tfn_status launch_normals(int kind, const tfn_method &m, int cfg, bool noref, const FrameDesc *d_frames,
+                          const CUtensorMap *d_maps, uint32_t *d_status, void *d_refine, int refine_cap, int nframes,
+                          int total_tiles, int num_sms, cudaStream_t stream)
 {
     LaunchSpec L;
-    tfn_status st = make_launch(kind, m, cfg, d_frames, d_maps, d_status, d_refine, refine_cap, nframes, total_tiles,
-                                num_sms, &L);
+    tfn_status st = make_launch(kind, m, cfg, noref, d_frames, d_maps, d_status, d_refine, refine_cap, nframes,
+                                total_tiles, num_sms, &L);
     if (st) return st;
     return enqueue_launch(L, stream);
 }
@@ -501,8 +532,9 @@ tfn_status launch_group(tfn_ctx *c, const tfn_frame *frames, int n, const tfn_me
     c->last_slot = si;
     if (!s.done) TFN_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
 
-    tfn_status lst = launch_normals(kind, m, cfg, slot_descs(s.dev), slot_maps(s.dev, s.cap), status ? status : c->status,
-                                    slot_refine(s.dev, s.cap), kRefineCap, n, total, c->num_sms, stream);
+    tfn_status lst = launch_normals(kind, m, cfg, refinement_idle(frames, n, m), slot_descs(s.dev), slot_maps(s.dev, s.cap),
+                                    status ? status : c->status, slot_refine(s.dev, s.cap), kRefineCap, n, total,
+                                    c->num_sms, stream);
     if (lst) return lst;
     TFN_CUDA(cudaEventRecord(s.done, stream));
     return TFN_OK;
@@ -865,8 +897,9 @@ tfn_status tfn_plan_create(tfn_ctx *c, const tfn_frame *frames, int n, const tfn
             const int cfg = run_cfg[i];
             int total = 0;
             for (int k = i; k < j; ++k) total += frame_tiles(frames[k], cfg);
-            lst = launch_normals(frames[i].input_type, *m, cfg, slot_descs(p->dev) + i, slot_maps(p->dev, n) + i,
-                                 c->status, slot_refine(p->dev, n), kRefineCap, j - i, total, c->num_sms, cs);
+            lst = launch_normals(frames[i].input_type, *m, cfg, refinement_idle(frames + i, j - i, *m),
+                                 slot_descs(p->dev) + i, slot_maps(p->dev, n) + i, c->status, slot_refine(p->dev, n),
+                                 kRefineCap, j - i, total, c->num_sms, cs);
             i = j;
         }
         if (!cuda_ok(cudaStreamEndCapture(cs, &p->graph), "cudaStreamEndCapture") && lst == TFN_OK) lst = TFN_ERR_CUDA;
@@ -891,6 +924,23 @@ tfn_status tfn_plan_launch(tfn_plan *p, tfn_stream stream)
     DeviceGuard g(p->ctx->device);
     if (!g.ok) return TFN_ERR_CUDA;
     TFN_CUDA(cudaGraphLaunch(p->exec, (cudaStream_t)stream));
+    return TFN_OK;
+}
+
+tfn_status tfn_plan_kernels(const tfn_plan *p, int32_t *count)
+{
+    if (!p || !p->graph || !count) return TFN_ERR_INVALID_ARG;
+    size_t nn = 0;
+    TFN_CUDA(cudaGraphGetNodes(p->graph, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) TFN_CUDA(cudaGraphGetNodes(p->graph, nodes.data(), &nn));
+    int32_t k = 0;
+    for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        TFN_CUDA(cudaGraphNodeGetType(nodes[i], &t));
+        k += t == cudaGraphNodeTypeKernel;
+    }
+    *count = k;
     return TFN_OK;
 }
 

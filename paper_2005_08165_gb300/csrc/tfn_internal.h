@@ -166,9 +166,10 @@ inline void sep5_weights(int grad, const float *given, float w[5])
     for (int k = 0; k < 5; ++k) w[k] = src[k];
 }
 
-// Kernel entry points, one per (kind, grad, phi, cfg); defined in tfn_k_*.cu.
+// Kernel entry points, one per (kind, grad, phi, cfg), and the NOREF forms
+// (noref: FP16 depth with FD only, else nullptr); defined in tfn_k_*.cu.
 typedef void (*KernelFn)(LaunchArgs);
-KernelFn kernel_for(int kind, int grad, int phi, int cfg);
+KernelFn kernel_for(int kind, int grad, int phi, int cfg, bool noref = false);
 // The refinement kernel of (kind, grad, phi); nullptr for PlanePCA.
 KernelFn refiner_for(int kind, int grad, int phi);
 
@@ -201,12 +202,16 @@ struct LaunchSpec {
     LaunchArgs args;
 };
 // d_refine: the launch's refinement list (refine_list_bytes(refine_cap), 128-byte aligned).
-tfn_status make_launch(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
-                       uint32_t *d_status, void *d_refine, int refine_cap, int nframes, int total_tiles, int num_sms,
-                       LaunchSpec *spec);
+// noref: run the NOREF kernel (refinement_idle holds for the launch's frames).
+tfn_status make_launch(int kind, const tfn_method &m, int cfg, bool noref, const FrameDesc *d_frames,
+                       const CUtensorMap *d_maps, uint32_t *d_status, void *d_refine, int refine_cap, int nframes,
+                       int total_tiles, int num_sms, LaunchSpec *spec);
 tfn_status enqueue_launch(LaunchSpec &spec, cudaStream_t stream);
-tfn_status launch_normals(int kind, const tfn_method &m, int cfg, const FrameDesc *d_frames, const CUtensorMap *d_maps,
-                          uint32_t *d_status, void *d_refine, int refine_cap, int nframes, int total_tiles,
-                          int num_sms, cudaStream_t stream);
+tfn_status launch_normals(int kind, const tfn_method &m, int cfg, bool noref, const FrameDesc *d_frames,
+                          const CUtensorMap *d_maps, uint32_t *d_status, void *d_refine, int refine_cap, int nframes,
+                          int total_tiles, int num_sms, cudaStream_t stream);
+// Whether the FP16 depth frames' sample spacing proves that no pixel can be
+// flagged for refinement (FD filter only; see its definition).
+bool refinement_idle(const tfn_frame *frames, int n, const tfn_method &m);
 
 }  // namespace tfn

@@ -3,6 +3,9 @@
 #include "tfn_kernel.cuh"
 
 namespace tfn {
-KernelFn kernels_disp_f32(int grad, int phi, int cfg) { return dev::select_kernel<KIND_DISP_F32>(grad, phi, cfg); }
+KernelFn kernels_disp_f32(int grad, int phi, int cfg, bool noref)
+{
+    return dev::select_kernel<KIND_DISP_F32>(grad, phi, cfg, noref);
+}
 KernelFn refiners_disp_f32(int grad, int phi) { return dev::select_refiner<KIND_DISP_F32>(grad, phi); }
 }  // namespace tfn

@@ -843,7 +843,12 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
 // that of (up-right, down-left) -s (B + F): the candidate sum is s T with T
 // below (n3n = G_v - G_u = -n3), and the candidates are s times the products
 // num F or num B.
-template <int KIND, int PHI>
+//
+// NOREF: the launch's frames are known never to need refinement (FP16 depth,
+// see refinement_idle on the host), so the error bound and the refinement
+// test are not computed; every other operation, and so every result bit, is
+// that of NOREF = false.
+template <int KIND, int PHI, bool NOREF>
 __device__ __forceinline__ void row_step_fd2(const Row<KIND, GRAD_FD> &P, const Row<KIND, GRAD_FD> &C,
                                              const Row<KIND, GRAD_FD> &N, UpCarry2 &cy, const f2 (&uc2)[2], float vc,
                                              float fx, float fy, float thr, float (&ox)[4], float (&oy)[4],
@@ -905,14 +910,14 @@ __device__ __forceinline__ void row_step_fd2(const Row<KIND, GRAD_FD> &P, const 
         }
 
         f2 mF, scale;
-        float mbound[2];
+        float mbound[2] = {};
         if constexpr (PHI == PHI_MEAN) {
             // sum over the pairs (j, -j) of num_p (rho_j - rho_-j) = s T,
             // carried unnormalised: n' scaled by m > 0 keeps its direction
             const f2 T = fma2(gu, add2(Fr, Bl), fma2(gv, add2(Fd, Bu), fma2(n2, add2(Fdr, Bul), mul2(n3n, add2(Bur, Fdl)))));
             mF = disp ? neg2(T) : T;
 #pragma unroll
-            for (int l = 0; l < 2; ++l) {
+            for (int l = 0; l < 2 && !NOREF; ++l) {
                 // bound of the candidate sum's rounding: sum_p |num_p| (|rho_j| + |rho_-j|),
                 // which the host's threshold multiplies by K1 u.  One-pass gradients
                 // (within 5u each) put up to 5u (|G_u| + |G_v|) on a diagonal
@@ -967,7 +972,7 @@ __device__ __forceinline__ void row_step_fd2(const Row<KIND, GRAD_FD> &P, const 
                 const bool odd = cnt & 1;
                 const float md = odd ? sv[3] : __fmul_rn(0.5f, __fadd_rn(sv[3], sv[4]));
                 med[l] = disp ? -md : md;
-                mbound[l] = odd ? fabsf(sv[3]) : fmaxf(fabsf(sv[3]), fabsf(sv[4]));
+                if constexpr (!NOREF) mbound[l] = odd ? fabsf(sv[3]) : fmaxf(fabsf(sv[3]), fabsf(sv[4]));
             }
             mF = pk(med[0], med[1]);
             scale = bc(1.f);
@@ -980,14 +985,14 @@ __device__ __forceinline__ void row_step_fd2(const Row<KIND, GRAD_FD> &P, const 
         const f2 nzp = pk((flat[0] || !ev_ok[0]) ? 1.f : -Q.x, (flat[1] || !ev_ok[1]) ? 1.f : -Q.y);
         const f2 nn = fma2(nxp, nxp, fma2(nyp, nyp, mul2(nzp, nzp)));
         const f2 rs = pk(ev_ok[0] ? rsqrt_approx(nn.x) : 0.f, ev_ok[1] ? rsqrt_approx(nn.y) : 0.f);
-        const f2 lim = mul2(bc(thr), mul2(nn, rs));
+        const f2 lim = NOREF ? bc(0.f) : mul2(bc(thr), mul2(nn, rs));
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
             const int k = h + 2 * l;
             const float r = lane_of(rs, l);
             // refine unless bound <= thr |n'|; written so that a NaN (|n'|
             // overflowed) also refines, and thr < 0 refines every pixel
-            const bool refine = ev_ok[l] && !flat[l] && !(mbound[l] <= lane_of(lim, l));
+            const bool refine = !NOREF && ev_ok[l] && !flat[l] && !(mbound[l] <= lane_of(lim, l));
             // -n'/|n'|, with +0 (not -0) for zero components and for non-evaluable pixels
             ox[k] = __fmaf_rn(-lane_of(nxp, l), r, 0.f);
             oy[k] = __fmaf_rn(-lane_of(nyp, l), r, 0.f);
@@ -1644,10 +1649,11 @@ static __device__ __noinline__ void list_for_refinement(unsigned long long *rlis
 // row.  No warp ever waits for another.  Rows at or below the frame's last
 // row read as holes, and so does the TMA zero fill above the first row and
 // beyond the right edge, so borders need no special case.
-template <int KIND, int GRAD, int PHI, int CFG>
+template <int KIND, int GRAD, int PHI, int CFG, bool NOREF>
 __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? fd_ctas_per_sm(CFG) : 0)
     normals_kernel(const __grid_constant__ LaunchArgs args)
 {
+    static_assert(!NOREF || (GRAD == GRAD_FD && KIND == KIND_DEPTH_F16), "only FP16 depth with FD has a NOREF form");
     typedef typename KindTraits<KIND>::T T;
     typedef Row<KIND, GRAD> R;
     constexpr int TH = kCfgs[CFG].th, CR = kCfgs[CFG].cr, NST = cfg_nst(CFG, GRAD), NW = cta_warps(CFG, GRAD);
@@ -1812,7 +1818,8 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
                 pca_row<KIND, GRAD>(P, C, N, uc, __fsub_rn((float)y, v0), rfx, rfy, ztc, ox, oy, oz, mw);
                 rb = 0;
             } else if constexpr (GRAD == GRAD_FD) {
-                row_step_fd2<KIND, PHI>(P, C, N, cy, uc2, __fsub_rn((float)y, v0), fx, fy, thr, ox, oy, oz, mw, rb);
+                row_step_fd2<KIND, PHI, NOREF>(P, C, N, cy, uc2, __fsub_rn((float)y, v0), fx, fy, thr, ox, oy, oz, mw,
+                                               rb);
             } else {
                 row_step<KIND, GRAD, PHI>(P, C, N, cy, uc, __fsub_rn((float)y, v0), fx, fy, thr, wts, gu, gv, ox, oy,
                                           oz, mw, rb);
@@ -2020,11 +2027,23 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
     }
 }
 
+// noref: the NOREF form (FP16 depth with the FD filter only; nullptr otherwise).
 template <int KIND>
-KernelFn select_kernel(int grad, int phi, int cfg)
+KernelFn select_kernel(int grad, int phi, int cfg, bool noref)
 {
+    if (noref) {
+        if constexpr (KIND == KIND_DEPTH_F16) {
+#define TFN_K(P, C) \
+    if (grad == GRAD_FD && phi == P && cfg == C) return &normals_kernel<KIND, GRAD_FD, P, C, true>;
+#define TFN_KC(P) TFN_K(P, 0) TFN_K(P, 1) TFN_K(P, 2) TFN_K(P, 3) TFN_K(P, 4) TFN_K(P, 5)
+            TFN_KC(PHI_MEAN) TFN_KC(PHI_MEDIAN)
+#undef TFN_KC
+#undef TFN_K
+        }
+        return nullptr;
+    }
 #define TFN_K(G, P, C)                                                                        \
-    if (grad == G && phi == P && cfg == C) return &normals_kernel<KIND, G, P, C>;
+    if (grad == G && phi == P && cfg == C) return &normals_kernel<KIND, G, P, C, false>;
 #define TFN_KC(G, P) TFN_K(G, P, 0) TFN_K(G, P, 1) TFN_K(G, P, 2) TFN_K(G, P, 3) TFN_K(G, P, 4) TFN_K(G, P, 5)
 #define TFN_KP(G) TFN_KC(G, PHI_MEAN) TFN_KC(G, PHI_MEDIAN)
     TFN_KP(GRAD_FD) TFN_KP(GRAD_SOBEL) TFN_KP(GRAD_SCHARR) TFN_KP(GRAD_PREWITT) TFN_KP(GRAD_WEIGHTED) TFN_KP(GRAD_SEP5)

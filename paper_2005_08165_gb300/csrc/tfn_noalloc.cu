@@ -132,8 +132,8 @@ extern "C" tfn_status tfn_normals_noalloc(const tfn_frame *frames, int n, const 
         while (j < n && frames[j].input_type == frames[i].input_type) ++j;
         int total = 0;
         for (int k = i; k < j; ++k) total += frame_tiles(frames[k], run_cfg[i]);
-        st = launch_normals(frames[i].input_type, *method, run_cfg[i], d->desc + i, d->maps + i, d->status, d->refine,
-                            kNoallocRefineCap, j - i, total, sms, s);
+        st = launch_normals(frames[i].input_type, *method, run_cfg[i], refinement_idle(frames + i, j - i, *method),
+                            d->desc + i, d->maps + i, d->status, d->refine, kNoallocRefineCap, j - i, total, sms, s);
         if (st) return st;
         i = j;
     }

@@ -114,8 +114,9 @@ struct GroupBuf {
 // A batch's kernels as a CUDA graph: the status word's reset, then per
 // launch (input kind) normals_kernel and its refinement kernel, if any.
 // Captured once per key (the method's flags, then per launch its kind, tile
-// shape and whether it refines in a second kernel); replayed with each
-// kernel node's grid and arguments updated to the batch.
+// shape, whether it runs the NOREF kernel and whether it refines in a second
+// kernel: together they fix the kernels); replayed with each kernel node's
+// grid and arguments updated to the batch.
 struct GraphEntry {
     std::vector<int> key;
     cudaGraph_t graph = nullptr;
@@ -253,12 +254,13 @@ tfn_status enqueue_kernels_graph(tfn_server *s, Pipe &p, const std::vector<tfn_f
                      "cudaMemcpyAsync(tensor maps)"))
             return TFN_ERR_CUDA;
         LaunchSpec L;
-        tfn_status st = make_launch(kind, m, cfg, slot_descs(g.dev), slot_maps(g.dev, g.cap), p.status_dev,
+        const bool noref = refinement_idle(fr.data(), n, m);
+        tfn_status st = make_launch(kind, m, cfg, noref, slot_descs(g.dev), slot_maps(g.dev, g.cap), p.status_dev,
                                     slot_refine(g.dev, g.cap), kRefineCap, n, tiles, c->num_sms, &L);
         if (st) return st;
         if (L.grid < 1) continue;
         specs.push_back(L);
-        key.insert(key.end(), {kind, cfg, L.rf != nullptr});
+        key.insert(key.end(), {kind, cfg, noref, L.rf != nullptr});
     }
     GraphEntry *ge = nullptr;
     for (GraphEntry &e : p.graphs)

@@ -8,9 +8,9 @@
 // The rows reach shared memory through a per-warp ring of TMA 2D copies
 // (boxes of CR rows x 128 columns plus a 16-byte halo each side, one mbarrier
 // per stage); normals and mask leave through vectorised streaming stores.
-// Holes decode to 2^100 (see kHole), the TMA zero fill outside the image is a
-// hole, and rows past the bottom read as holes, so borders need no special
-// case.
+// Holes decode to 2^100 (see kHole), and the TMA zero fill outside the image
+// (rows above the first and past the last, columns beyond the edges) is a
+// hole, so borders need no special case.
 //
 // Arithmetic (Sec. III of Fan et al.):
 //   filters          FD on depth: G = 1/Z_{+1} - 1/Z_{-1} = (Z_{-1} - Z_{+1}) /
@@ -471,17 +471,6 @@ __device__ __forceinline__ void set_row(Row<KIND, GRAD_FD> &R, const float (&z)[
     R.p[1] = pk(z[1], z[3]);
     R.p[2] = pk(z[2], z[4]);
     R.p[3] = pk(z[3], z[5]);
-}
-
-template <int KIND, int GRAD>
-__device__ __forceinline__ void hole_row(Row<KIND, GRAD> &R)
-{
-    const float z[6] = {kHole, kHole, kHole, kHole, kHole, kHole};
-    set_row(R, z);
-    if constexpr (Row<KIND, GRAD>::kW) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) R.wh[c] = R.wl[c] = 0.f;
-    }
 }
 
 // Reads row `jr` of a staged box (BOXW samples per row, the lane's pixels at
@@ -1483,29 +1472,41 @@ static __device__ __noinline__ void store4_cold(OutDesc fd, int fmt, int u, int 
     }
 }
 
+// Normals and mask of a full quad of row v in a planar layout (fmt OUT_F32,
+// OUT_F16 or OUT_BF16).
+__device__ __forceinline__ void store4_planar(const OutDesc &fd, int fmt, int u, int v, const float (&x)[4],
+                                              const float (&y)[4], const float (&zz)[4], uint32_t mw)
+{
+    char *row = fd.out + (int64_t)v * fd.out_pitch;
+    uint8_t *mrow = fd.mask + (int64_t)v * fd.mask_pitch;
+    if (fmt == OUT_F32) {
+        __stcs(reinterpret_cast<float4 *>(row + (int64_t)u * 4), make_float4(x[0], x[1], x[2], x[3]));
+        __stcs(reinterpret_cast<float4 *>(row + fd.out_plane + (int64_t)u * 4), make_float4(y[0], y[1], y[2], y[3]));
+        __stcs(reinterpret_cast<float4 *>(row + 2 * fd.out_plane + (int64_t)u * 4), make_float4(zz[0], zz[1], zz[2], zz[3]));
+    } else {
+        // (one branch on the launch's format, so that each pair is converted once)
+        auto put = [&](int ff) {
+            __stcs(reinterpret_cast<uint2 *>(row + (int64_t)u * 2), make_uint2(pack2(x[0], x[1], ff), pack2(x[2], x[3], ff)));
+            __stcs(reinterpret_cast<uint2 *>(row + fd.out_plane + (int64_t)u * 2),
+                   make_uint2(pack2(y[0], y[1], ff), pack2(y[2], y[3], ff)));
+            __stcs(reinterpret_cast<uint2 *>(row + 2 * fd.out_plane + (int64_t)u * 2),
+                   make_uint2(pack2(zz[0], zz[1], ff), pack2(zz[2], zz[3], ff)));
+        };
+        if (fmt == OUT_F16)
+            put(OUT_F16);
+        else
+            put(OUT_BF16);
+    }
+    __stcs(reinterpret_cast<unsigned int *>(mrow + u), mw);
+}
+
 // Normals and mask of 4 pixels of row v: FP32 and FP16/BF16 planar full
 // quads inline, everything else through store4_cold.
 __device__ __forceinline__ void store4(const OutDesc &fd, int fmt, int u, int v, int n, const float (&x)[4],
                                        const float (&y)[4], const float (&zz)[4], uint32_t mw)
 {
-    if (n == 4 && fmt == OUT_F32) {
-        char *row = fd.out + (int64_t)v * fd.out_pitch;
-        uint8_t *mrow = fd.mask + (int64_t)v * fd.mask_pitch;
-        __stcs(reinterpret_cast<float4 *>(row + (int64_t)u * 4), make_float4(x[0], x[1], x[2], x[3]));
-        __stcs(reinterpret_cast<float4 *>(row + fd.out_plane + (int64_t)u * 4), make_float4(y[0], y[1], y[2], y[3]));
-        __stcs(reinterpret_cast<float4 *>(row + 2 * fd.out_plane + (int64_t)u * 4), make_float4(zz[0], zz[1], zz[2], zz[3]));
-        __stcs(reinterpret_cast<unsigned int *>(mrow + u), mw);
-        return;
-    }
-    if (n == 4 && (fmt == OUT_F16 || fmt == OUT_BF16)) {
-        char *row = fd.out + (int64_t)v * fd.out_pitch;
-        uint8_t *mrow = fd.mask + (int64_t)v * fd.mask_pitch;
-        __stcs(reinterpret_cast<uint2 *>(row + (int64_t)u * 2), make_uint2(pack2(x[0], x[1], fmt), pack2(x[2], x[3], fmt)));
-        __stcs(reinterpret_cast<uint2 *>(row + fd.out_plane + (int64_t)u * 2),
-               make_uint2(pack2(y[0], y[1], fmt), pack2(y[2], y[3], fmt)));
-        __stcs(reinterpret_cast<uint2 *>(row + 2 * fd.out_plane + (int64_t)u * 2),
-               make_uint2(pack2(zz[0], zz[1], fmt), pack2(zz[2], zz[3], fmt)));
-        __stcs(reinterpret_cast<unsigned int *>(mrow + u), mw);
+    if (n == 4 && fmt <= OUT_BF16) {
+        store4_planar(fd, fmt, u, v, x, y, zz, mw);
         return;
     }
     store4_cold(fd, fmt, u, v, n, x[0], x[1], x[2], x[3], y[0], y[1], y[2], y[3], zz[0], zz[1], zz[2], zz[3], mw);
@@ -1646,9 +1647,9 @@ static __device__ __noinline__ void list_for_refinement(unsigned long long *rlis
 // (box: 128 columns plus a 16-byte halo on each side), filled by TMA 2D
 // copies that lane 0 issues and completed on one mbarrier per stage; a stage
 // is refilled with the chunk NST ahead as soon as the warp has read its last
-// row.  No warp ever waits for another.  Rows at or below the frame's last
-// row read as holes, and so does the TMA zero fill above the first row and
-// beyond the right edge, so borders need no special case.
+// row.  No warp ever waits for another.  The TMA zero fill outside the frame
+// (above the first row, past the last, beyond the edges) reads as holes, so
+// borders need no special case.
 template <int KIND, int GRAD, int PHI, int CFG, bool NOREF>
 __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? fd_ctas_per_sm(CFG) : 0)
     normals_kernel(const __grid_constant__ LaunchArgs args)
@@ -1718,17 +1719,15 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
         const int x = (lt % txs) * 128 - PADX;
         const int y = (lt / txs) * TH - HR + (cc % NCH) * CR;
         const uint32_t bar = smem_addr(&full[warp][cc % NST]);
-        if (y < __ldg(&f->H)) {
-            const CUtensorMap *map = args.maps + pf;
-            if (pf != fenced) {
-                fence_tensormap_acquire(map);
-                fenced = pf;
-            }
-            mbar_expect_tx(bar, BOX_BYTES);
-            tma_load_2d(smem_addr(ring + (cc % NST) * STRIDE), map, x, y, bar);
-        } else {
-            mbar_arrive(bar);  // every row of this chunk is past the bottom: nothing to copy
+        // (a chunk partly or wholly past the bottom row is copied too: the
+        // copy fills those rows with zeros, which decode as holes)
+        const CUtensorMap *map = args.maps + pf;
+        if (pf != fenced) {
+            fence_tensormap_acquire(map);
+            fenced = pf;
         }
+        mbar_expect_tx(bar, BOX_BYTES);
+        tma_load_2d(smem_addr(ring + (cc % NST) * STRIDE), map, x, y, bar);
     };
     if (lane == 0)
 #pragma unroll
@@ -1766,12 +1765,12 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
         const f2 uc2[2] = {pk(uc[0], uc[2]), pk(uc[1], uc[3])};  // (FD: the pixel pairs)
 
         // Sample row j (0 .. TH+2HR-1) of the item is image row y0 - HR + j;
-        // rows at or past the bottom read as holes.  The rows arrive in
-        // order, so the chunk state advances incrementally: row jr of chunk cc.
-        const int rows_in = H - (y0 - HR);
+        // rows at or past the bottom arrive as the copy's zero fill (holes).
+        // The rows arrive in order, so the chunk state advances
+        // incrementally: row jr of chunk cc.
         int jr = 0, cc = i * NCH;
         const unsigned char *stage = ring;
-        // (load(in_frame) reads row jr of `stage` into registers)
+        // (the row loops that fetch one row at a time: load() reads row jr of `stage` into registers)
         auto fetch_with = [&](auto &&load, int j) -> bool {
             if (jr == 0) {
                 const int st = cc % NST;
@@ -1781,7 +1780,7 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
                     return false;
                 }
             }
-            load(j < rows_in);
+            load();
             if (++jr == CR) {  // the stage's last row is in registers: refill it
                 __syncwarp();
                 if (lane == 0) {
@@ -1793,17 +1792,6 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
             }
             return true;
         };
-        auto fetch = [&](R &row, int j) -> bool {
-            return fetch_with(
-                [&](bool in_frame) {
-                    if (in_frame)
-                        load_row<KIND, GRAD, BOXW, PADX>(stage, jr, lane, row);
-                    else
-                        hole_row(row);
-                },
-                j);
-        };
-
         unsigned long long pend_a = 0, pend_b = 0;  // (INPLACE) bit 4 s + k: row y0 + s, column x0 + k
         typename CarryOf<GRAD>::type cy;
         if constexpr (GRAD == GRAD_FD) cy.q = fd_carry;
@@ -1824,7 +1812,11 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
                 row_step<KIND, GRAD, PHI>(P, C, N, cy, uc, __fsub_rn((float)y, v0), fx, fy, thr, wts, gu, gv, ox, oy,
                                           oz, mw, rb);
             }
-            if (y < H && nvalid > 0) {
+            // The common case under one test: a full quad of a row inside the
+            // frame, planar output, no point cloud, nothing to refine.
+            if (y < H && nvalid == 4 && !has_pts && rb == 0 && args.out_fmt <= OUT_BF16) {
+                store4_planar(out, args.out_fmt, x0, y, ox, oy, oz, mw);
+            } else if (y < H && nvalid > 0) {
                 rb &= (1u << min(nvalid, 4)) - 1u;
                 // pixels whose FP32 error bound is too loose: mask bit 1 set
                 // (bit k of rb to bit 8k + 1), and listed for refine_kernel
@@ -1845,23 +1837,68 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
         if constexpr (!SEP5) {
             const df g0[4] = {};  // (3x3 filters compute their gradients in row_step)
             R P, C, N;
-            if (!fetch(C, 0) || !fetch(N, 1)) {
-                failed = true;
-                break;
-            }
-            if constexpr (GRAD != GRAD_PLANEPCA) carry_down(C, N, cy);
-            P = C;
-            C = N;
-            // (a rolled loop: unrolling it to rotate the roles of P, C, N costs
-            // more in instruction fetch than the row copies it saves)
-            for (int s = 0; s < TH; ++s) {
-                if (!fetch(N, s + 2)) {
+            // Two forms of the row loop, each the faster for its Phi (measured on
+            // the 256-frame batch): the median's row step, the larger, runs
+            // best in one flat loop that fetches row by row; the mean's in a
+            // loop over chunks with a rolled loop over each chunk's rows.
+            if constexpr (PHI == PHI_MEDIAN) {
+                auto fetch = [&](R &row, int j) -> bool {
+                    return fetch_with([&]() { load_row<KIND, GRAD, BOXW, PADX>(stage, jr, lane, row); }, j);
+                };
+                if (!fetch(C, 0) || !fetch(N, 1)) {
                     failed = true;
                     break;
                 }
-                emit(P, C, N, s, g0, g0);
+                if constexpr (GRAD != GRAD_PLANEPCA) carry_down(C, N, cy);
                 P = C;
                 C = N;
+                for (int s = 0; s < TH; ++s) {
+                    if (!fetch(N, s + 2)) {
+                        failed = true;
+                        break;
+                    }
+                    emit(P, C, N, s, g0, g0);
+                    P = C;
+                    C = N;
+                }
+            } else {
+                // Chunk by chunk (the item's TH + 2 sample rows fill NCH chunks
+                // exactly): wait for the chunk's stage, roll through its rows,
+                // then refill the stage; the first chunk's first two rows start
+                // the window.  (Rolled loops: unrolling the row loop to rotate the
+                // roles of P, C, N costs more in instruction fetch than the row
+                // copies it saves.)
+                int s = 0;  // output row of the item
+                for (int ch = 0; ch < NCH; ++ch, ++cc) {
+                    const int st = cc % NST;
+                    const unsigned char *const stg = ring + st * STRIDE;
+                    if (!__all_sync(0xffffffffu, mbar_wait(smem_addr(&full[warp][st]), (uint32_t)((cc / NST) & 1)))) {
+                        fail_cc = cc;
+                        failed = true;
+                        break;
+                    }
+                    int r = 0;
+                    if (ch == 0) {
+                        load_row<KIND, GRAD, BOXW, PADX>(stg, 0, lane, C);
+                        load_row<KIND, GRAD, BOXW, PADX>(stg, 1, lane, N);
+                        if constexpr (GRAD != GRAD_PLANEPCA) carry_down(C, N, cy);
+                        P = C;
+                        C = N;
+                        r = 2;
+                    }
+#pragma unroll 1
+                    for (; r < CR; ++r, ++s) {
+                        load_row<KIND, GRAD, BOXW, PADX>(stg, r, lane, N);
+                        emit(P, C, N, s, g0, g0);
+                        P = C;
+                        C = N;
+                    }
+                    __syncwarp();
+                    if (lane == 0) {  // every row of the stage has been read: refill it
+                        fence_async_shared();
+                        issue(cc + NST);
+                    }
+                }
             }
         } else {
             // 5x5 filters: sample row j's derivative and smoothing go to ring
@@ -1872,17 +1909,7 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
             int wslot = 0;
             float z8[8];
             auto take = [&](R &row, int j) -> bool {
-                if (!fetch_with(
-                        [&](bool in_frame) {
-                            if (in_frame) {
-                                load_row8<KIND, BOXW, PADX>(stage, jr, lane, z8);
-                            } else {
-#pragma unroll
-                                for (int c = 0; c < 8; ++c) z8[c] = kHole;
-                            }
-                        },
-                        j))
-                    return false;
+                if (!fetch_with([&]() { load_row8<KIND, BOXW, PADX>(stage, jr, lane, z8); }, j)) return false;
                 df Dh[4], Sh[4];
                 sep5_row<KIND>(z8, sw, Dh, Sh);
                 float4 *q = dring + wslot * (4 * 32);

@@ -128,6 +128,25 @@ __device__ __forceinline__ df df_div(df a, df b)
     return fast_two_sum(q1, q2);
 }
 
+// Unnormalised double-float for the long weighted sums of the 5x5 filters:
+// the high parts are added exactly (TwoSum) or multiplied exactly (FMA
+// residual), the low parts and those errors are accumulated in FP32, and the
+// pair is not renormalised after each step (8 and 3 operations instead of 11
+// and 6).  h + l keeps the terms' sum to about u^2 of their magnitudes, as
+// the normalised operations do; df_norm renormalises (exactly) at the end.
+__device__ __forceinline__ df dfl_add(df a, df b)
+{
+    const df s = two_sum(a.h, b.h);
+    return {s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l))};
+}
+__device__ __forceinline__ df dfl_sub(df a, df b) { return dfl_add(a, df_neg(b)); }
+__device__ __forceinline__ df dfl_mul_f(df a, float b)
+{
+    const float p = __fmul_rn(a.h, b);
+    return {p, __fmaf_rn(a.l, b, __fmaf_rn(a.h, b, -p))};
+}
+__device__ __forceinline__ df df_norm(df a) { return two_sum(a.h, a.l); }
+
 __device__ __forceinline__ float df_val(df a) { return __fadd_rn(a.h, a.l); }
 
 // ------------------------------------------------------------ pixel pairs
@@ -380,14 +399,14 @@ __device__ __forceinline__ EdgeR edge_recip(float delta)
     return {r, __fmul_rn(delta, r)};
 }
 
-// edge_recip on a pair of edges.
+// edge_recip on a pair of edges, keeping delta (d) instead of k: its users
+// form k = delta r inside their sums.
 struct EdgeR2 {
-    f2 r, k;
+    f2 r, d;
 };
 __device__ __forceinline__ EdgeR2 edge_recip2(f2 delta)
 {
-    const f2 r = mul2(delta, rcp2(fma2(delta, delta, bc(kEdgeEps))));
-    return {r, mul2(delta, r)};
+    return {mul2(delta, rcp2(fma2(delta, delta, bc(kEdgeEps)))), delta};
 }
 
 // A hole's stand-in value, 2^100.  Its difference with any valid sample
@@ -436,25 +455,19 @@ struct Row {
     float wh[kW ? 6 : 1], wl[kW ? 6 : 1];
 };
 
-// FD rows hold the samples as the pairs of pixel pairs (1, 3) and (2, 4) of
-// row_step_fd2: p[0] = (z0, z2), p[1] = (z1, z3), p[2] = (z2, z4),
-// p[3] = (z3, z5).  (z2 and z3 sit in two pairs each.)
-template <int KIND>
-struct Row<KIND, GRAD_FD> {
-    static constexpr bool kW = false;
-    f2 p[4];
-};
-
 // Sample c (0 .. 5) of a row.
 template <int KIND, int GRAD>
 __device__ __forceinline__ float sample(const Row<KIND, GRAD> &R, int c)
 {
     return R.z[c];
 }
-template <int KIND>
-__device__ __forceinline__ float sample(const Row<KIND, GRAD_FD> &R, int c)
+
+// The sample pair (z_i, z_{i+2}) of a row: row_step_fd2 takes a lane's pixels
+// 1 and 3, then 2 and 4, as pairs, whose windows sit on these pairs.
+template <int KIND, int GRAD>
+__device__ __forceinline__ f2 zpair(const Row<KIND, GRAD> &R, int i)
 {
-    return c == 0 ? R.p[0].x : c == 1 ? R.p[1].x : c == 2 ? R.p[2].x : c == 3 ? R.p[1].y : c == 4 ? R.p[2].y : R.p[3].y;
+    return pk(R.z[i], R.z[i + 2]);
 }
 
 // Fills a row with its 6 decoded samples.
@@ -463,14 +476,6 @@ __device__ __forceinline__ void set_row(Row<KIND, GRAD> &R, const float (&z)[6])
 {
 #pragma unroll
     for (int c = 0; c < 6; ++c) R.z[c] = z[c];
-}
-template <int KIND>
-__device__ __forceinline__ void set_row(Row<KIND, GRAD_FD> &R, const float (&z)[6])
-{
-    R.p[0] = pk(z[0], z[2]);
-    R.p[1] = pk(z[1], z[3]);
-    R.p[2] = pk(z[2], z[4]);
-    R.p[3] = pk(z[3], z[5]);
 }
 
 // Reads row `jr` of a staged box (BOXW samples per row, the lane's pixels at
@@ -645,12 +650,12 @@ __device__ __forceinline__ void carry_down(const Row<KIND, GRAD_FD> &C, const Ro
     constexpr bool disp = KindTraits<KIND>::disparity;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const f2 Cl = C.p[h], Cc = C.p[1 + h], Cr = C.p[2 + h], Nc = N.p[1 + h];
+        const f2 Cl = zpair(C, h), Cc = zpair(C, 1 + h), Cr = zpair(C, 2 + h), Nc = zpair(N, 1 + h);
         const EdgeR2 v = edge_recip2(sub2(Nc, Cc));  // (y, c)   -> (y+1, c)
         const EdgeR2 d = edge_recip2(sub2(Nc, Cl));  // (y, c-1) -> (y+1, c)
         const EdgeR2 a = edge_recip2(sub2(Nc, Cr));  // (y, c+1) -> (y+1, c)
         cy.put(h, mul2(disp ? Nc : Cc, v.r), mul2(disp ? Nc : Cl, d.r), mul2(disp ? Nc : Cr, a.r),
-               add2(add2(v.k, d.k), a.k));
+               fma2(v.d, v.r, fma2(d.d, d.r, mul2(a.d, a.r))));
     }
 }
 
@@ -847,15 +852,15 @@ __device__ __forceinline__ void row_step_fd2(const Row<KIND, GRAD_FD> &P, const 
     constexpr bool one_pass = kFdOnePassMean && PHI == PHI_MEAN && !disp;
     const f2 vc2 = bc(vc), fx2 = bc(fx), fy2 = bc(fy);
     // the edges to column c-1 of pixels c = 1, 3 (the next pair's come from this pair)
-    EdgeR2 ehm = edge_recip2(sub2(C.p[1], C.p[0]));  // (y, c-1) -> (y, c)
-    EdgeR2 edm = edge_recip2(sub2(N.p[1], C.p[0]));  // (y, c-1) -> (y+1, c)
-    EdgeR2 eam = edge_recip2(sub2(N.p[0], C.p[1]));  // (y, c)   -> (y+1, c-1)
+    EdgeR2 ehm = edge_recip2(sub2(zpair(C, 1), zpair(C, 0)));  // (y, c-1) -> (y, c)
+    EdgeR2 edm = edge_recip2(sub2(zpair(N, 1), zpair(C, 0)));  // (y, c-1) -> (y+1, c)
+    EdgeR2 eam = edge_recip2(sub2(zpair(N, 0), zpair(C, 1)));  // (y, c)   -> (y+1, c-1)
     mword = 0;
     rbits = 0;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const f2 Cl = C.p[h], Cc = C.p[1 + h], Cr = C.p[2 + h];
-        const f2 Nl = N.p[h], Nc = N.p[1 + h], Nr = N.p[2 + h], Pc = P.p[1 + h];
+        const f2 Cl = zpair(C, h), Cc = zpair(C, 1 + h), Cr = zpair(C, 2 + h);
+        const f2 Nl = zpair(N, h), Nc = zpair(N, 1 + h), Nr = zpair(N, 2 + h), Pc = zpair(P, 1 + h);
         const EdgeR2 eh = edge_recip2(sub2(Cr, Cc));  // (y, c)   -> (y, c+1)
         const EdgeR2 ed = edge_recip2(sub2(Nr, Cc));  // (y, c)   -> (y+1, c+1)
         const EdgeR2 ea = edge_recip2(sub2(Nc, Cr));  // (y, c+1) -> (y+1, c)
@@ -867,7 +872,9 @@ __device__ __forceinline__ void row_step_fd2(const Row<KIND, GRAD_FD> &P, const 
         const f2 Fdl = mul2(disp ? Cc : Nl, eam.r);
         f2 Bu, Bul, Bur, ku;
         cy.get(h, Bu, Bul, Bur, ku);
-        const f2 m = add2(add2(add2(eh.k, ehm.k), add2(ev.k, ed.k)), add2(eam.k, ku));
+        // the candidate count: delta r over the 8 edges (1 to a few ulp for a
+        // kept neighbour, 0 for a dropped one), the up edges' sum carried
+        const f2 m = fma2(eh.d, eh.r, fma2(ehm.d, ehm.r, fma2(ev.d, ev.r, fma2(ed.d, ed.r, fma2(eam.d, eam.r, ku)))));
 
         // gradients (as h + l), evaluability and the special case, per pixel
         const df2 Gu = fd_term2<KIND, one_pass>(Cl, Cr), Gv = fd_term2<KIND, one_pass>(Pc, Nc);
@@ -992,7 +999,7 @@ __device__ __forceinline__ void row_step_fd2(const Row<KIND, GRAD_FD> &P, const 
 
         // the carry for the pixels below: their up, up-left and up-right neighbours
         cy.put(h, mul2(disp ? Nc : Cc, ev.r), mul2(disp ? Nc : Cl, edm.r), mul2(disp ? Nc : Cr, ea.r),
-               add2(add2(ev.k, edm.k), ea.k));
+               fma2(ev.d, ev.r, fma2(edm.d, edm.r, mul2(ea.d, ea.r))));
         // this pair's edges to column c+1 are the next pair's to column c-1
         ehm = eh;
         edm = ed;
@@ -1007,9 +1014,11 @@ __device__ __forceinline__ void row_step_fd2(const Row<KIND, GRAD_FD> &P, const 
 // smoothing profile (s0, s1, s2) across it.  As each sample row arrives, a
 // lane computes at its 4 columns the row's derivative Dh = d1 (w_{+1} -
 // w_{-1}) + d2 (w_{+2} - w_{-2}) and smoothing Sh = s0 w_0 + s1 (w_{-1} +
-// w_{+1}) + s2 (w_{-2} + w_{+2}) (w = 1/Z or the disparity), both
-// compensated, and keeps them for 5 rows; then G_u = sum_a s_|a| Dh(y + a)
-// and G_v = d1 (Sh(y+1) - Sh(y-1)) + d2 (Sh(y+2) - Sh(y-2)).  The common
+// w_{+1}) + s2 (w_{-2} + w_{+2}) (w = 1/Z or the disparity), both as
+// unnormalised double-float pairs (exact tap differences, then the dfl_
+// operations), and keeps them for 5 rows; then G_u = sum_a s_|a| Dh(y + a)
+// and G_v = d1 (Sh(y+1) - Sh(y-1)) + d2 (Sh(y+2) - Sh(y-2)), renormalised
+// once at the end.  The common
 // normalisation is dropped (it cancels from the direction).  A value whose
 // needed taps include a hole is NaN, which marks the pixels that use it as
 // not evaluable; zero-weight terms are never read.
@@ -1084,15 +1093,16 @@ __device__ __forceinline__ void sep5_row(const float (&z)[8], const Sep5W &w, df
     for (int k = 0; k < 4; ++k) {
         const int c = k + 2;
         const bool ok1 = ok[c - 1] && ok[c + 1], ok2 = ok[c - 2] && ok[c + 2];
-        const df t1 = w.d1 != 0.f ? df_mul_f(diff(c - 1, c + 1), w.d1) : zero;
-        const df t2 = w.d2 != 0.f ? df_mul_f(diff(c - 2, c + 2), w.d2) : zero;
+        // (unnormalised pairs: the ring keeps them so, the vertical sums renormalise)
+        const df t1 = w.d1 != 0.f ? dfl_mul_f(diff(c - 1, c + 1), w.d1) : zero;
+        const df t2 = w.d2 != 0.f ? dfl_mul_f(diff(c - 2, c + 2), w.d2) : zero;
         const bool dok = (w.d1 == 0.f || ok1) && (w.d2 == 0.f || ok2);
-        Dh[k] = dok ? df_add(t1, t2) : df_nan();
-        const df a0 = w.s0 != 0.f ? df_mul_f(val(c), w.s0) : zero;
-        const df a1 = w.s1 != 0.f ? df_mul_f(df_add(val(c - 1), val(c + 1)), w.s1) : zero;
-        const df a2 = w.s2 != 0.f ? df_mul_f(df_add(val(c - 2), val(c + 2)), w.s2) : zero;
+        Dh[k] = dok ? dfl_add(t1, t2) : df_nan();
+        const df a0 = w.s0 != 0.f ? dfl_mul_f(val(c), w.s0) : zero;
+        const df a1 = w.s1 != 0.f ? dfl_mul_f(dfl_add(val(c - 1), val(c + 1)), w.s1) : zero;
+        const df a2 = w.s2 != 0.f ? dfl_mul_f(dfl_add(val(c - 2), val(c + 2)), w.s2) : zero;
         const bool sok = (w.s0 == 0.f || ok[c]) && (w.s1 == 0.f || ok1) && (w.s2 == 0.f || ok2);
-        Sh[k] = sok ? df_add(a0, df_add(a1, a2)) : df_nan();
+        Sh[k] = sok ? dfl_add(a0, dfl_add(a1, a2)) : df_nan();
     }
 }
 
@@ -1947,45 +1957,44 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
                     const float4 h = ring_at(2, 0), l = ring_at(2, 1);
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        gu[k] = sw.s0 != 0.f ? df_mul_f(df{f4_at(h, k), f4_at(l, k)}, sw.s0) : zero;
+                        gu[k] = sw.s0 != 0.f ? dfl_mul_f(df{f4_at(h, k), f4_at(l, k)}, sw.s0) : zero;
                 }
                 {
                     const float4 h1 = ring_at(1, 0), l1 = ring_at(1, 1), h3 = ring_at(3, 0), l3 = ring_at(3, 1);
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        t[k] = sw.s1 != 0.f ? df_mul_f(df_add(df{f4_at(h1, k), f4_at(l1, k)}, df{f4_at(h3, k), f4_at(l3, k)}),
-                                                       sw.s1)
+                        t[k] = sw.s1 != 0.f ? dfl_mul_f(dfl_add(df{f4_at(h1, k), f4_at(l1, k)}, df{f4_at(h3, k), f4_at(l3, k)}),
+                                                        sw.s1)
                                             : zero;
                 }
                 {
                     const float4 h0 = ring_at(0, 0), l0 = ring_at(0, 1), h4 = ring_at(4, 0), l4 = ring_at(4, 1);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const df t2 = sw.s2 != 0.f ? df_mul_f(df_add(df{f4_at(h0, k), f4_at(l0, k)},
-                                                                     df{f4_at(h4, k), f4_at(l4, k)}),
-                                                              sw.s2)
+                        const df t2 = sw.s2 != 0.f ? dfl_mul_f(dfl_add(df{f4_at(h0, k), f4_at(l0, k)},
+                                                                       df{f4_at(h4, k), f4_at(l4, k)}),
+                                                               sw.s2)
                                                    : zero;
-                        gu[k] = df_add(gu[k], df_add(t[k], t2));
+                        gu[k] = df_norm(dfl_add(gu[k], dfl_add(t[k], t2)));
                     }
                 }
                 {
                     const float4 h1 = ring_at(1, 2), l1 = ring_at(1, 3), h3 = ring_at(3, 2), l3 = ring_at(3, 3);
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        gv[k] = sw.d1 != 0.f ? df_mul_f(df_add(df{f4_at(h3, k), f4_at(l3, k)},
-                                                               df_neg(df{f4_at(h1, k), f4_at(l1, k)})),
-                                                        sw.d1)
+                        gv[k] = sw.d1 != 0.f ? dfl_mul_f(dfl_sub(df{f4_at(h3, k), f4_at(l3, k)}, df{f4_at(h1, k), f4_at(l1, k)}),
+                                                         sw.d1)
                                              : zero;
                 }
                 {
                     const float4 h0 = ring_at(0, 2), l0 = ring_at(0, 3), h4 = ring_at(4, 2), l4 = ring_at(4, 3);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const df t2 = sw.d2 != 0.f ? df_mul_f(df_add(df{f4_at(h4, k), f4_at(l4, k)},
-                                                                     df_neg(df{f4_at(h0, k), f4_at(l0, k)})),
-                                                              sw.d2)
+                        const df t2 = sw.d2 != 0.f ? dfl_mul_f(dfl_sub(df{f4_at(h4, k), f4_at(l4, k)},
+                                                                       df{f4_at(h0, k), f4_at(l0, k)}),
+                                                               sw.d2)
                                                    : zero;
-                        gv[k] = df_add(gv[k], t2);
+                        gv[k] = df_norm(dfl_add(gv[k], t2));
                     }
                 }
                 emit(P, C, N, s, gu, gv);

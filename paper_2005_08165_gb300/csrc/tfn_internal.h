@@ -116,12 +116,16 @@ constexpr bool refines_in_place(int c) { return c == kSmallCfg; }
 // filter on 256 x 480x640 frames (FD mean 0.9%, Sobel 4.5%, the 5x5 filters 13% faster than 18 rows)
 constexpr int kDefaultCfg = 1;
 
-// Warps per CTA of the (shape, filter) kernel.  The FD kernels (128
+// The 3x3 filters (FD, Sobel, Scharr, Prewitt, the weighted family) run the
+// pixel-pair row step (row_step2) with the row carry in shared memory; the
+// 5x5 filters and PlanePCA run the scalar one.
+constexpr bool grad_is_pair(int grad) { return grad >= GRAD_FD && grad <= GRAD_WEIGHTED; }
+// Warps per CTA of the (shape, filter) kernel.  The 3x3 kernels (128
 // registers) run 2-warp CTAs in the default shapes, 8 of them per SM, whose
-// finer grain scheduled better than 4 x 4 warps; the other filters 4-warp
-// CTAs.
-constexpr int cta_warps(int c, int grad) { return grad == GRAD_FD ? kCfgs[c].fd_warps : kCfgs[c].warps; }
-// CTAs per SM that the FD kernels are compiled for (their register bound).
+// finer grain scheduled better than 4 x 4 warps (`fd_warps`); the 5x5 filters
+// and PlanePCA 4-warp CTAs (`warps`).
+constexpr int cta_warps(int c, int grad) { return grad_is_pair(grad) ? kCfgs[c].fd_warps : kCfgs[c].warps; }
+// CTAs per SM that the 3x3 kernels are compiled for (their register bound).
 constexpr int fd_ctas_per_sm(int c) { return 16 / cta_warps(c, GRAD_FD); }
 inline int cfg_threads(int c, int grad) { return 32 * cta_warps(c, grad); }
 inline int kind_elem_size(int kind) { return (kind == KIND_DEPTH_F32 || kind == KIND_DISP_F32) ? 4 : 2; }
@@ -139,13 +143,13 @@ constexpr bool grad_is_sep5(int grad) { return grad >= GRAD_SEP5 && grad <= GRAD
 // derivative ring a third stage makes shared memory the occupancy limit
 // (2 CTAs = 8 warps per SM instead of the 12 their registers allow), and a
 // chunk of 8 rows takes far longer to compute than one copy takes to land.
-// The FD kernels keep 2 as well: with their carry buffer (below) 3 stages
+// The 3x3 kernels keep 2 as well: with their carry buffer (below) 3 stages
 // would make shared memory the occupancy limit.
 constexpr int cfg_nst(int c, int grad)
 {
-    return (grad_is_sep5(grad) || grad == GRAD_FD) && kCfgs[c].nst > 2 ? 2 : kCfgs[c].nst;
+    return (grad_is_sep5(grad) || grad_is_pair(grad)) && kCfgs[c].nst > 2 ? 2 : kCfgs[c].nst;
 }
-// The FD kernels keep each lane's carry from one row to the next (the rho of
+// The 3x3 kernels keep each lane's carry from one row to the next (the rho of
 // the up, up-left and up-right neighbours and their count, 8 floats per
 // pixel pair) in shared memory rather than in registers: 2 pairs x 2 x 16
 // bytes per lane.
@@ -153,7 +157,7 @@ constexpr size_t kFdCarryBytes = 2 * 2 * 32 * 16;
 inline size_t smem_bytes(int kind, int c, int grad)
 {
     return (size_t)cta_warps(c, grad) * (cfg_nst(c, grad) * stage_stride(kind, c) + (grad_is_sep5(grad) ? kSep5RingBytes : 0) +
-                                         (grad == GRAD_FD ? kFdCarryBytes : 0)) +
+                                         (grad_is_pair(grad) ? kFdCarryBytes : 0)) +
            128;
 }
 // The profiles (d1 d2 s0 s1 s2) of a 5x5 filter: the named members' fixed

@@ -151,7 +151,7 @@ __device__ __forceinline__ float df_val(df a) { return __fadd_rn(a.h, a.l); }
 
 // ------------------------------------------------------------ pixel pairs
 //
-// The FD kernels write a lane's four pixels as two pairs (see row_step_fd2).
+// The 3x3 kernels write a lane's four pixels as two pairs (see row_step2).
 // An f2 holds one value of each pixel of a pair, and these helpers apply the
 // same correctly rounded operation to both: two scalar operations each,
 // never contracted or reassociated, so a pair computes exactly what two
@@ -462,7 +462,7 @@ __device__ __forceinline__ float sample(const Row<KIND, GRAD> &R, int c)
     return R.z[c];
 }
 
-// The sample pair (z_i, z_{i+2}) of a row: row_step_fd2 takes a lane's pixels
+// The sample pair (z_i, z_{i+2}) of a row: row_step2 takes a lane's pixels
 // 1 and 3, then 2 and 4, as pairs, whose windows sit on these pairs.
 template <int KIND, int GRAD>
 __device__ __forceinline__ f2 zpair(const Row<KIND, GRAD> &R, int i)
@@ -610,13 +610,13 @@ __device__ __forceinline__ void carry_down(const Row<KIND, GRAD> &C, const Row<K
     }
 }
 
-// FD: the carry of the pixel pairs (pair 0: pixels 1 and 3, pair 1: pixels
+// The 3x3 filters: the carry of the pixel pairs (pair 0: pixels 1 and 3, pair 1: pixels
 // 2 and 4): the magnitudes B of the rho of the up, up-left and up-right
 // neighbours (rho = -B on depth, +B on disparity) and how many of the three
 // are kept.  It lives in shared memory, this lane's slots of its warp's
 // buffer (kFdCarryBytes): pair h at q[64 h] = (B_u, B_ul) and q[64 h + 32] =
 // (B_ur, k_u), so that a pair's carry occupies registers only between its
-// load and its store in row_step_fd2.
+// load and its store in row_step2.
 struct UpCarry2 {
     float4 *q;
     __device__ __forceinline__ void get(int h, f2 &bu, f2 &bul, f2 &bur, f2 &ku) const
@@ -633,19 +633,19 @@ struct UpCarry2 {
         q[64 * h + 32] = make_float4(bur.x, bur.y, ku.x, ku.y);
     }
 };
-template <int GRAD>
+template <int GRAD, bool PAIR = grad_is_pair(GRAD)>
 struct CarryOf {
     typedef UpCarry type;
 };
-template <>
-struct CarryOf<GRAD_FD> {
+template <int GRAD>
+struct CarryOf<GRAD, true> {
     typedef UpCarry2 type;
 };
 
-// carry_down for FD rows.  Edge p -> q with r = 1/(s_q - s_p): seen from q,
-// rho = -s_p r on depth and s_q r on disparity (rho_bwd).
-template <int KIND>
-__device__ __forceinline__ void carry_down(const Row<KIND, GRAD_FD> &C, const Row<KIND, GRAD_FD> &N, UpCarry2 &cy)
+// carry_down for the 3x3 filters' rows.  Edge p -> q with r = 1/(s_q - s_p):
+// seen from q, rho = -s_p r on depth and s_q r on disparity (rho_bwd).
+template <int KIND, int GRAD>
+__device__ __forceinline__ void carry_down(const Row<KIND, GRAD> &C, const Row<KIND, GRAD> &N, UpCarry2 &cy)
 {
     constexpr bool disp = KindTraits<KIND>::disparity;
 #pragma unroll
@@ -659,8 +659,8 @@ __device__ __forceinline__ void carry_down(const Row<KIND, GRAD_FD> &C, const Ro
     }
 }
 
-// One row of a lane's 4 pixels (Sec. III end to end) for the filters other
-// than FD (those run row_step_fd2), given the sample rows above (P), at (C)
+// One row of a lane's 4 pixels (Sec. III end to end) for the 5x5 filters
+// (the 3x3 filters run row_step2), given the sample rows above (P), at (C)
 // and below (N) and the carry from the row above; leaves the carry for the
 // next row in `cy`.  Outputs the normal components, the mask bits and the
 // bits of the pixels whose FP32 error bound is too loose.  Every product is
@@ -674,7 +674,7 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
                                          float (&ox)[4], float (&oy)[4], float (&oz)[4], uint32_t &mword,
                                          unsigned &rbits)
 {
-    static_assert(GRAD != GRAD_FD, "the FD filter runs row_step_fd2");
+    static_assert(GRAD == GRAD_SEP5, "the 3x3 filters run row_step2");
     // edges of this row (c -> c+1) and to the row below, computed pixel by
     // pixel: pixel c needs those of columns c-1 and c only
     EdgeR h[5], ed[5], ea[5];
@@ -700,39 +700,10 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
         const float m = __fadd_rn(__fadd_rn(__fadd_rn(h[c].k, h[c - 1].k), __fadd_rn(ev.k, ed[c].k)),
                                   __fadd_rn(ea[c - 1].k, cy.ku[k]));
 
-        // gradients (as h + l), the special case and evaluability
-        df Gu, Gv;
-        bool ev_ok;
-        if constexpr (GRAD == GRAD_WEIGHTED) {
-            const float w0 = wts[0], w1 = wts[1], w2 = wts[2];
-            Gu = filter_sum_w(tap_diff(P, c - 1, P, c + 1), tap_diff(C, c - 1, C, c + 1), tap_diff(N, c - 1, N, c + 1),
-                              w0, w1, w2);
-            Gv = filter_sum_w(tap_diff(P, c - 1, N, c - 1), tap_diff(P, c, N, c), tap_diff(P, c + 1, N, c + 1), w0,
-                              w1, w2);
-            // tap (row a, column b) is needed when its row's weight is non-zero in the horizontal
-            // filter (outer columns) or its column's weight in the vertical one (outer rows)
-            const bool n0 = w0 != 0.f, n1 = w1 != 0.f, n2 = w2 != 0.f;
-            float mx = zi;
-            mx = fmaxf(mx, n0 ? P.z[c - 1] : 0.f);
-            mx = fmaxf(mx, (n0 || n2) ? P.z[c + 1] : 0.f);
-            mx = fmaxf(mx, (n0 || n2) ? N.z[c - 1] : 0.f);
-            mx = fmaxf(mx, n2 ? N.z[c + 1] : 0.f);
-            mx = fmaxf(mx, n1 ? fmaxf(fmaxf(P.z[c], N.z[c]), fmaxf(C.z[c - 1], C.z[c + 1])) : 0.f);
-            ev_ok = mx <= kValidHi;
-        } else if constexpr (GRAD == GRAD_SEP5) {
-            // the 5x5 gradients come from the caller, NaN where a needed tap is a hole
-            Gu = gin_u[k];
-            Gv = gin_v[k];
-            ev_ok = zi <= kValidHi && Gu.h == Gu.h && Gv.h == Gv.h;
-        } else {
-            Gu = filter_sum<GRAD>(tap_diff(P, c - 1, P, c + 1), tap_diff(C, c - 1, C, c + 1),
-                                  tap_diff(N, c - 1, N, c + 1));
-            Gv = filter_sum<GRAD>(tap_diff(P, c - 1, N, c - 1), tap_diff(P, c, N, c), tap_diff(P, c + 1, N, c + 1));
-            const float mp = fmaxf(fmaxf(P.z[c - 1], P.z[c]), P.z[c + 1]);
-            const float mc = fmaxf(fmaxf(C.z[c - 1], zi), C.z[c + 1]);
-            const float mn = fmaxf(fmaxf(N.z[c - 1], N.z[c]), N.z[c + 1]);
-            ev_ok = fmaxf(fmaxf(mp, mc), mn) <= kValidHi;
-        }
+        // the 5x5 gradients come from the caller as h + l, NaN where a needed
+        // tap is a hole; evaluability and the special case
+        const df Gu = gin_u[k], Gv = gin_v[k];
+        const bool ev_ok = zi <= kValidHi && Gu.h == Gu.h && Gv.h == Gv.h;
         // Sec. III special case: both gradients exactly zero (an h + l pair
         // vanishes only when both parts do)
         bool flat = Gu.h == 0.f && Gu.l == 0.f && Gv.h == 0.f && Gv.l == 0.f;
@@ -819,14 +790,57 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
     }
 }
 
-// row_step for the FD filter, two pixels at a time.  A lane's pixels 1 and 3
-// form one pair and pixels 2 and 4 the other: their windows sit on the same
-// sample pairs (Row<KIND, GRAD_FD>), so each edge, rho, gradient and sum is
-// written once for a pair (add2, mul2, fma2), and the pair's carry lives in
-// shared memory between rows (UpCarry2).  With compensated gradients the
-// operations and their order are those of row_step, bit for bit; the mean's
-// one-pass gradients (kFdOnePassMean) change only the gradient quotient and
-// the bound.
+// The smoothed 3x3 filters' gradients of a pair's two pixels (columns 1 + h
+// and 3 + h of the lane's window), each as the scalar step computes them:
+// exact tap differences and the compensated filter sum (weighted: the
+// caller's row weights); and each pixel's evaluability (every tap with a
+// non-zero weight in either filter inside the frame and valid).
+template <int KIND, int GRAD>
+__device__ __forceinline__ void grad_pair(const Row<KIND, GRAD> &P, const Row<KIND, GRAD> &C, const Row<KIND, GRAD> &N,
+                                          int h, const float (&wts)[3], df2 &Gu, df2 &Gv, bool (&ev_ok)[2])
+{
+    df gu[2], gv[2];
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        const int c = 1 + h + 2 * l;
+        if constexpr (GRAD == GRAD_WEIGHTED) {
+            const float w0 = wts[0], w1 = wts[1], w2 = wts[2];
+            gu[l] = filter_sum_w(tap_diff(P, c - 1, P, c + 1), tap_diff(C, c - 1, C, c + 1),
+                                 tap_diff(N, c - 1, N, c + 1), w0, w1, w2);
+            gv[l] = filter_sum_w(tap_diff(P, c - 1, N, c - 1), tap_diff(P, c, N, c), tap_diff(P, c + 1, N, c + 1), w0,
+                                 w1, w2);
+            // tap (row a, column b) is needed when its row's weight is non-zero in the horizontal
+            // filter (outer columns) or its column's weight in the vertical one (outer rows)
+            const bool n0 = w0 != 0.f, n1 = w1 != 0.f, n2 = w2 != 0.f;
+            float mx = C.z[c];
+            mx = fmaxf(mx, n0 ? P.z[c - 1] : 0.f);
+            mx = fmaxf(mx, (n0 || n2) ? P.z[c + 1] : 0.f);
+            mx = fmaxf(mx, (n0 || n2) ? N.z[c - 1] : 0.f);
+            mx = fmaxf(mx, n2 ? N.z[c + 1] : 0.f);
+            mx = fmaxf(mx, n1 ? fmaxf(fmaxf(P.z[c], N.z[c]), fmaxf(C.z[c - 1], C.z[c + 1])) : 0.f);
+            ev_ok[l] = mx <= kValidHi;
+        } else {
+            gu[l] = filter_sum<GRAD>(tap_diff(P, c - 1, P, c + 1), tap_diff(C, c - 1, C, c + 1),
+                                     tap_diff(N, c - 1, N, c + 1));
+            gv[l] = filter_sum<GRAD>(tap_diff(P, c - 1, N, c - 1), tap_diff(P, c, N, c), tap_diff(P, c + 1, N, c + 1));
+            const float mp = fmaxf(fmaxf(P.z[c - 1], P.z[c]), P.z[c + 1]);
+            const float mc = fmaxf(fmaxf(C.z[c - 1], C.z[c]), C.z[c + 1]);
+            const float mn = fmaxf(fmaxf(N.z[c - 1], N.z[c]), N.z[c + 1]);
+            ev_ok[l] = fmaxf(fmaxf(mp, mc), mn) <= kValidHi;
+        }
+    }
+    Gu = {pk(gu[0].h, gu[1].h), pk(gu[0].l, gu[1].l)};
+    Gv = {pk(gv[0].h, gv[1].h), pk(gv[0].l, gv[1].l)};
+}
+
+// The row step of the 3x3 filters, two pixels at a time.  A lane's pixels 1
+// and 3 form one pair and pixels 2 and 4 the other: their windows sit on the
+// same sample pairs (zpair), so each edge, rho and sum is written once for a
+// pair (add2, mul2, fma2), and the pair's carry lives in shared memory
+// between rows (UpCarry2).  The gradients: FD's quotients on the pairs
+// (fd_term2; one-pass for the mean on depth when kFdOnePassMean is set), the
+// smoothed filters' per pixel as the scalar step computes them (grad_pair:
+// exact tap differences, compensated filter sums).
 //
 // rho of the neighbours: an edge p -> q with r = 1/(s_q - s_p) gives p the
 // rho s_q r (depth) or -s_p r (disparity), and q the rho -s_p r or s_q r; the
@@ -842,14 +856,15 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
 // see refinement_idle on the host), so the error bound and the refinement
 // test are not computed; every other operation, and so every result bit, is
 // that of NOREF = false.
-template <int KIND, int PHI, bool NOREF>
-__device__ __forceinline__ void row_step_fd2(const Row<KIND, GRAD_FD> &P, const Row<KIND, GRAD_FD> &C,
-                                             const Row<KIND, GRAD_FD> &N, UpCarry2 &cy, const f2 (&uc2)[2], float vc,
-                                             float fx, float fy, float thr, float (&ox)[4], float (&oy)[4],
-                                             float (&oz)[4], uint32_t &mword, unsigned &rbits)
+template <int KIND, int GRAD, int PHI, bool NOREF>
+__device__ __forceinline__ void row_step2(const Row<KIND, GRAD> &P, const Row<KIND, GRAD> &C, const Row<KIND, GRAD> &N,
+                                          UpCarry2 &cy, const f2 (&uc2)[2], float vc, float fx, float fy, float thr,
+                                          const float (&wts)[3], float (&ox)[4], float (&oy)[4], float (&oz)[4],
+                                          uint32_t &mword, unsigned &rbits)
 {
+    static_assert(grad_is_pair(GRAD), "row_step2 runs the 3x3 filters");
     constexpr bool disp = KindTraits<KIND>::disparity;
-    constexpr bool one_pass = kFdOnePassMean && PHI == PHI_MEAN && !disp;
+    constexpr bool one_pass = GRAD == GRAD_FD && kFdOnePassMean && PHI == PHI_MEAN && !disp;
     const f2 vc2 = bc(vc), fx2 = bc(fx), fy2 = bc(fy);
     // the edges to column c-1 of pixels c = 1, 3 (the next pair's come from this pair)
     EdgeR2 ehm = edge_recip2(sub2(zpair(C, 1), zpair(C, 0)));  // (y, c-1) -> (y, c)
@@ -877,15 +892,25 @@ __device__ __forceinline__ void row_step_fd2(const Row<KIND, GRAD_FD> &P, const 
         const f2 m = fma2(eh.d, eh.r, fma2(ehm.d, ehm.r, fma2(ev.d, ev.r, fma2(ed.d, ed.r, fma2(eam.d, eam.r, ku)))));
 
         // gradients (as h + l), evaluability and the special case, per pixel
-        const df2 Gu = fd_term2<KIND, one_pass>(Cl, Cr), Gv = fd_term2<KIND, one_pass>(Pc, Nc);
+        df2 Gu, Gv;
         bool ev_ok[2], flat[2];
+        if constexpr (GRAD == GRAD_FD) {
+            Gu = fd_term2<KIND, one_pass>(Cl, Cr);
+            Gv = fd_term2<KIND, one_pass>(Pc, Nc);
 #pragma unroll
-        for (int l = 0; l < 2; ++l) {
-            ev_ok[l] = fmaxf(fmaxf(fmaxf(lane_of(Cl, l), lane_of(Cc, l)), lane_of(Cr, l)),
-                             fmaxf(lane_of(Pc, l), lane_of(Nc, l))) <= kValidHi;
-            // Sec. III special case: both gradients exactly zero (an FD term's
-            // low part is 0 whenever its high part is)
-            flat[l] = lane_of(Gu.h, l) == 0.f && lane_of(Gv.h, l) == 0.f;
+            for (int l = 0; l < 2; ++l) {
+                ev_ok[l] = fmaxf(fmaxf(fmaxf(lane_of(Cl, l), lane_of(Cc, l)), lane_of(Cr, l)),
+                                 fmaxf(lane_of(Pc, l), lane_of(Nc, l))) <= kValidHi;
+                // Sec. III special case: both gradients exactly zero (an FD term's
+                // low part is 0 whenever its high part is)
+                flat[l] = lane_of(Gu.h, l) == 0.f && lane_of(Gv.h, l) == 0.f;
+            }
+        } else {
+            grad_pair<KIND, GRAD>(P, C, N, h, wts, Gu, Gv, ev_ok);
+#pragma unroll
+            for (int l = 0; l < 2; ++l)  // (an h + l pair vanishes only when both parts do)
+                flat[l] = lane_of(Gu.h, l) == 0.f && lane_of(Gu.l, l) == 0.f && lane_of(Gv.h, l) == 0.f &&
+                          lane_of(Gv.l, l) == 0.f;
         }
         f2 gu, gv, n2, n3n;
         if constexpr (one_pass) {
@@ -1661,7 +1686,7 @@ static __device__ __noinline__ void list_for_refinement(unsigned long long *rlis
 // (above the first row, past the last, beyond the edges) reads as holes, so
 // borders need no special case.
 template <int KIND, int GRAD, int PHI, int CFG, bool NOREF>
-__global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? fd_ctas_per_sm(CFG) : 0)
+__global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), grad_is_pair(GRAD) ? fd_ctas_per_sm(CFG) : 0)
     normals_kernel(const __grid_constant__ LaunchArgs args)
 {
     static_assert(!NOREF || (GRAD == GRAD_FD && KIND == KIND_DEPTH_F16), "only FP16 depth with FD has a NOREF form");
@@ -1804,7 +1829,7 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
         };
         unsigned long long pend_a = 0, pend_b = 0;  // (INPLACE) bit 4 s + k: row y0 + s, column x0 + k
         typename CarryOf<GRAD>::type cy;
-        if constexpr (GRAD == GRAD_FD) cy.q = fd_carry;
+        if constexpr (grad_is_pair(GRAD)) cy.q = fd_carry;
         // output row y0 + s from sample rows P (above), C and N (below); the
         // 5x5 filters' gradients come in gu, gv
         auto emit = [&](const R &P, const R &C, const R &N, int s, const df(&gu)[4], const df(&gv)[4]) {
@@ -1815,9 +1840,9 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), GRAD == GRAD_FD ? f
             if constexpr (GRAD == GRAD_PLANEPCA) {
                 pca_row<KIND, GRAD>(P, C, N, uc, __fsub_rn((float)y, v0), rfx, rfy, ztc, ox, oy, oz, mw);
                 rb = 0;
-            } else if constexpr (GRAD == GRAD_FD) {
-                row_step_fd2<KIND, PHI, NOREF>(P, C, N, cy, uc2, __fsub_rn((float)y, v0), fx, fy, thr, ox, oy, oz, mw,
-                                               rb);
+            } else if constexpr (grad_is_pair(GRAD)) {
+                row_step2<KIND, GRAD, PHI, NOREF>(P, C, N, cy, uc2, __fsub_rn((float)y, v0), fx, fy, thr, wts, ox, oy,
+                                                  oz, mw, rb);
             } else {
                 row_step<KIND, GRAD, PHI>(P, C, N, cy, uc, __fsub_rn((float)y, v0), fx, fy, thr, wts, gu, gv, ox, oy,
                                           oz, mw, rb);

@@ -154,10 +154,19 @@ constexpr int cfg_nst(int c, int grad)
 // pixel pair) in shared memory rather than in registers: 2 pairs x 2 x 16
 // bytes per lane.
 constexpr size_t kFdCarryBytes = 2 * 2 * 32 * 16;
+// The smoothed 3x3 filters also keep each sample row's horizontal tap
+// differences (w[c+1] - w[c-1] as h + l at the lane's 4 columns) for the three
+// output rows that use them: a ring of 3 rows x 2 pairs x 16 bytes per lane.
+constexpr size_t kDRingBytes = 3 * 2 * 32 * 16;
+// Shared memory per warp for the row carry (and the ring) of the 3x3 kernels.
+constexpr size_t carry_bytes(int grad)
+{
+    return grad_is_pair(grad) ? kFdCarryBytes + (grad != GRAD_FD ? kDRingBytes : 0) : 0;
+}
 inline size_t smem_bytes(int kind, int c, int grad)
 {
     return (size_t)cta_warps(c, grad) * (cfg_nst(c, grad) * stage_stride(kind, c) + (grad_is_sep5(grad) ? kSep5RingBytes : 0) +
-                                         (grad_is_pair(grad) ? kFdCarryBytes : 0)) +
+                                         carry_bytes(grad)) +
            128;
 }
 // The profiles (d1 d2 s0 s1 s2) of a 5x5 filter: the named members' fixed

@@ -487,9 +487,10 @@ def test_plan_graph_replay_matches_batch(torch, tfn, ctx):
     plan.close()
 
 
-@pytest.mark.parametrize("grad,phi", [("fd", "mean"), ("scharr", "median")])
+@pytest.mark.parametrize("grad,phi", [("fd", "mean"), ("scharr", "median"), ("sobel", "mean"), ("prewitt", "median")])
 def test_tile_shapes_give_identical_bits(torch, tfn, grad, phi):
-    # every compiled tile shape (the autotuner's choices) computes the same bits
+    # every compiled tile shape (the autotuner's choices) computes the same bits; (sobel, mean) keeps
+    # the rows' tap differences in the shared-memory ring, the medians compute them per row
     frames = depth_frames([(67, 131), (480, 640), (33, 64)], 1700)
     inputs = [to_dev(torch, tfn, img) for img, _ in frames]
     cams = [cam for _, cam in frames]

@@ -773,14 +773,14 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
             const float rho8[8] = {rr, rl, rd, ru, rdr, rul, rur, rdl};
             const float num8[8] = {gu, -gu, gv, -gv, n2, -n2, n3, -n3};
             float s[8];
-            unsigned sgn = 0;  // sign bit of the next sentinel: +inf, -inf, +inf, ...
+            float sent = __uint_as_float(0x7f800000u);  // the next sentinel: +inf, -inf, +inf, ...
             int cnt = 0;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const bool kept = rho8[q] != 0.f;
                 cnt += kept;
-                s[q] = kept ? __fmul_rn(num8[q], rho8[q]) : __uint_as_float(0x7f800000u | sgn);
-                sgn ^= kept ? 0u : 0x80000000u;
+                s[q] = kept ? __fmul_rn(num8[q], rho8[q]) : sent;
+                sent = kept ? sent : -sent;
             }
 #define TFN_CE(i, j)                         \
     {                                        \
@@ -795,7 +795,7 @@ __device__ __forceinline__ void row_step(const Row<KIND, GRAD> &P, const Row<KIN
             TFN_CE(1, 4) TFN_CE(3, 6)
             TFN_CE(1, 2) TFN_CE(3, 4) TFN_CE(5, 6)
 #undef TFN_CE
-            const bool odd = cnt & 1;
+            const bool odd = sent < 0.f;  // (8 - cnt missing: odd with cnt)
             none = cnt == 0;
             mF = odd ? s[3] : __fmul_rn(0.5f, __fadd_rn(s[3], s[4]));
             mbound = odd ? fabsf(s[3]) : fmaxf(fabsf(s[3]), fabsf(s[4]));
@@ -1019,14 +1019,12 @@ __device__ __forceinline__ void row_step2(const Row<KIND, GRAD> &P, const Row<KI
 #pragma unroll
             for (int l = 0; l < 2; ++l) {
                 float sv[8];
-                unsigned sgn = 0;  // sign bit of the next sentinel: +inf, -inf, +inf, ...
-                int cnt = 0;
+                float sent = __uint_as_float(0x7f800000u);  // the next sentinel: +inf, -inf, +inf, ...
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const bool kept = lane_of(mag[q], l) != 0.f;
-                    cnt += kept;
-                    sv[q] = kept ? lane_of(pr[q], l) : __uint_as_float(0x7f800000u | sgn);
-                    sgn ^= kept ? 0u : 0x80000000u;
+                    sv[q] = kept ? lane_of(pr[q], l) : sent;
+                    sent = kept ? sent : -sent;
                 }
 #define TFN_CE(i, j)                           \
     {                                          \
@@ -1043,7 +1041,9 @@ __device__ __forceinline__ void row_step2(const Row<KIND, GRAD> &P, const Row<KI
 #undef TFN_CE
                 // (the median of s times the products is s times theirs: the
                 // sentinels keep the middle slots on the kept candidates)
-                const bool odd = cnt & 1;
+                // the count of kept candidates, 8 minus the missing ones, is odd
+                // when an odd number is missing: when the next sentinel is -inf
+                const bool odd = sent < 0.f;
                 const float md = odd ? sv[3] : __fmul_rn(0.5f, __fadd_rn(sv[3], sv[4]));
                 med[l] = disp ? -md : md;
                 if constexpr (!NOREF) mbound[l] = odd ? fabsf(sv[3]) : fmaxf(fabsf(sv[3]), fabsf(sv[4]));

@@ -612,13 +612,13 @@ __device__ __forceinline__ void carry_down(const Row<KIND, GRAD> &C, const Row<K
 
 // Whether a 3x3 kernel keeps its rows' horizontal tap differences in the
 // shared-memory ring (computed once per sample row, read by the three output
-// rows that use them) instead of computing them for each output row: the
-// Sobel, Scharr and Prewitt means, 4-4.6% faster with it on the 256-frame
-// batch; the medians and the weighted family measured 1-3.5% slower (their
-// larger row steps spill).
+// rows that use them) instead of computing them for each output row:
+// Sobel, Scharr and Prewitt, 4-7% faster with it (means) and up to 2.5%
+// (medians) on the 256-frame batch; the weighted family measured 1% slower
+// (its row step spills with it).
 constexpr bool uses_dring(int grad, int phi)
 {
-    return (grad == GRAD_SOBEL || grad == GRAD_SCHARR || grad == GRAD_PREWITT) && phi == PHI_MEAN;
+    return (grad == GRAD_SOBEL || grad == GRAD_SCHARR || grad == GRAD_PREWITT) && (phi == PHI_MEAN || phi == PHI_MEDIAN);
 }
 
 // A row's horizontal tap differences w[c+1] - w[c-1] (exact, as h + l) at the

@@ -247,11 +247,12 @@ int tfn_tile_shape_count(void);
  * (each thread computes 4 columns x rows_per_thread pixels). */
 tfn_status tfn_tile_shape_info(int index, int *tile_w, int *tile_h, int *rows_per_thread);
 
-/* Warps per thread block (CTA) of shape `index`: for the FD filter
- * (*fd_warps) and for every other filter and PlanePCA (*warps).  Shapes that
- * share a height differ in this width; a work item is always one warp's.
- * (An interface of this library: the paper has no counterpart.) */
-tfn_status tfn_tile_shape_warps(int index, int *fd_warps, int *warps);
+/* Warps per thread block (CTA) of shape `index`: for the 3x3 filters (FD,
+ * Sobel, Scharr, Prewitt, the weighted family: *warps_3x3) and for the 5x5
+ * filters and PlanePCA (*warps_other).  Shapes that share a height differ in
+ * these widths; a work item is always one warp's.  (An interface of this
+ * library: the paper has no counterpart.) */
+tfn_status tfn_tile_shape_warps(int index, int *warps_3x3, int *warps_other);
 
 /* Forces the tile shape used by later calls of this context; index -1 (the
  * default) uses the context's tune table (see tfn_autotune), and for

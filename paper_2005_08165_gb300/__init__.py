@@ -481,7 +481,7 @@ def tile_shapes():
 
 
 def tile_shape_warps():
-    """[(warps per CTA for FD, for the other filters)] for every compiled tile shape."""
+    """[(warps per CTA for the 3x3 filters, for the 5x5 filters and PlanePCA)] for every compiled tile shape."""
     out = []
     for i in range(tfn_tile_shape_count()):
         a, b = ctypes.c_int(), ctypes.c_int()

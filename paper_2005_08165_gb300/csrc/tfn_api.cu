@@ -969,11 +969,11 @@ tfn_status tfn_tile_shape_info(int index, int *tile_w, int *tile_h, int *rows_pe
     return TFN_OK;
 }
 
-tfn_status tfn_tile_shape_warps(int index, int *fd_warps, int *warps)
+tfn_status tfn_tile_shape_warps(int index, int *warps_3x3, int *warps_other)
 {
     if (index < 0 || index >= kNumCfg) return TFN_ERR_INVALID_ARG;
-    if (fd_warps) *fd_warps = kCfgs[index].fd_warps;
-    if (warps) *warps = kCfgs[index].warps;
+    if (warps_3x3) *warps_3x3 = kCfgs[index].warps3;
+    if (warps_other) *warps_other = kCfgs[index].warps5;
     return TFN_OK;
 }
 

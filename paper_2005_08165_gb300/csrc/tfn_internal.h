@@ -95,12 +95,12 @@ constexpr int kRefineThreads = 128;
 // warp that rolls down its rows (pr = th rows per lane); the rows stream
 // through a ring of nst shared-memory stages of cr rows each (th + 2 rows per
 // item: one above, one below; th + 4 for the 5x5 filters, the last chunk of
-// an item then partly unused), per warp; a CTA has `warps` warps (fd_warps
-// for the FD filter).  Shapes 4 and 5 repeat the heights of shapes 1 and 2
+// an item then partly unused), per warp; a CTA has `warps3` warps for the
+// 3x3 filters and `warps5` for the 5x5 filters and PlanePCA.  Shapes 4 and 5 repeat the heights of shapes 1 and 2
 // with other CTA widths, so that the autotuner chooses the threads per CTA
 // as well as the item height.
 struct TileCfg {
-    int tw, th, pr, cr, nst, warps, fd_warps;
+    int tw, th, pr, cr, nst, warps5, warps3;
 };
 constexpr int kNumCfg = 6;
 constexpr TileCfg kCfgs[kNumCfg] = {{128, 18, 18, 5, 3, 4, 2}, {128, 30, 30, 8, 3, 4, 2}, {128, 12, 12, 7, 3, 4, 2},
@@ -122,11 +122,11 @@ constexpr int kDefaultCfg = 1;
 constexpr bool grad_is_pair(int grad) { return grad >= GRAD_FD && grad <= GRAD_WEIGHTED; }
 // Warps per CTA of the (shape, filter) kernel.  The 3x3 kernels (128
 // registers) run 2-warp CTAs in the default shapes, 8 of them per SM, whose
-// finer grain scheduled better than 4 x 4 warps (`fd_warps`); the 5x5 filters
-// and PlanePCA 4-warp CTAs (`warps`).
-constexpr int cta_warps(int c, int grad) { return grad_is_pair(grad) ? kCfgs[c].fd_warps : kCfgs[c].warps; }
+// finer grain scheduled better than 4 x 4 warps (`warps3`); the 5x5 filters
+// and PlanePCA 4-warp CTAs (`warps5`).
+constexpr int cta_warps(int c, int grad) { return grad_is_pair(grad) ? kCfgs[c].warps3 : kCfgs[c].warps5; }
 // CTAs per SM that the 3x3 kernels are compiled for (their register bound).
-constexpr int fd_ctas_per_sm(int c) { return 16 / cta_warps(c, GRAD_FD); }
+constexpr int ctas3_per_sm(int c) { return 16 / cta_warps(c, GRAD_FD); }
 inline int cfg_threads(int c, int grad) { return 32 * cta_warps(c, grad); }
 inline int kind_elem_size(int kind) { return (kind == KIND_DEPTH_F32 || kind == KIND_DISP_F32) ? 4 : 2; }
 // Halo columns loaded on each side so that the TMA box starts on a 16-byte boundary.
@@ -153,7 +153,7 @@ constexpr int cfg_nst(int c, int grad)
 // the up, up-left and up-right neighbours and their count, 8 floats per
 // pixel pair) in shared memory rather than in registers: 2 pairs x 2 x 16
 // bytes per lane.
-constexpr size_t kFdCarryBytes = 2 * 2 * 32 * 16;
+constexpr size_t kCarry3Bytes = 2 * 2 * 32 * 16;
 // The smoothed 3x3 filters also keep each sample row's horizontal tap
 // differences (w[c+1] - w[c-1] as h + l at the lane's 4 columns) for the three
 // output rows that use them: a ring of 3 rows x 2 pairs x 16 bytes per lane.
@@ -161,7 +161,7 @@ constexpr size_t kDRingBytes = 3 * 2 * 32 * 16;
 // Shared memory per warp for the row carry (and the ring) of the 3x3 kernels.
 constexpr size_t carry_bytes(int grad)
 {
-    return grad_is_pair(grad) ? kFdCarryBytes + (grad != GRAD_FD ? kDRingBytes : 0) : 0;
+    return grad_is_pair(grad) ? kCarry3Bytes + (grad != GRAD_FD ? kDRingBytes : 0) : 0;
 }
 inline size_t smem_bytes(int kind, int c, int grad)
 {

@@ -634,7 +634,7 @@ __device__ __forceinline__ df2 hdiff_pair(const Row<KIND, GRAD> &R, int h)
 // 2 and 4): the magnitudes B of the rho of the up, up-left and up-right
 // neighbours (rho = -B on depth, +B on disparity) and how many of the three
 // are kept.  It lives in shared memory, this lane's slots of its warp's
-// buffer (kFdCarryBytes): pair h at q[64 h] = (B_u, B_ul) and q[64 h + 32] =
+// buffer (kCarry3Bytes): pair h at q[64 h] = (B_u, B_ul) and q[64 h + 32] =
 // (B_ur, k_u), so that a pair's carry occupies registers only between its
 // load and its store in row_step2.
 struct UpCarry2 {
@@ -1740,7 +1740,7 @@ static __device__ __noinline__ void list_for_refinement(unsigned long long *rlis
 // (above the first row, past the last, beyond the edges) reads as holes, so
 // borders need no special case.
 template <int KIND, int GRAD, int PHI, int CFG, bool NOREF>
-__global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), grad_is_pair(GRAD) ? fd_ctas_per_sm(CFG) : 0)
+__global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), grad_is_pair(GRAD) ? ctas3_per_sm(CFG) : 0)
     normals_kernel(const __grid_constant__ LaunchArgs args)
 {
     static_assert(!NOREF || (GRAD == GRAD_FD && KIND == KIND_DEPTH_F16), "only FP16 depth with FD has a NOREF form");
@@ -1770,7 +1770,7 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), grad_is_pair(GRAD) 
     // (5x5 filters) this lane's slots of the per-warp ring of row derivatives and smoothings
     float4 *const dring = reinterpret_cast<float4 *>(sbase + NW * NST * STRIDE + warp * kSep5RingBytes) + lane;
     // (FD) this lane's slots of the per-warp carry buffer
-    float4 *const fd_carry = reinterpret_cast<float4 *>(sbase + NW * NST * STRIDE + warp * carry_bytes(GRAD)) + lane;
+    float4 *const carry3 = reinterpret_cast<float4 *>(sbase + NW * NST * STRIDE + warp * carry_bytes(GRAD)) + lane;
     if (lane == 0) {
 #pragma unroll
         for (int s = 0; s < NST; ++s) mbar_init(smem_addr(&full[warp][s]), 1);
@@ -1884,8 +1884,8 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), grad_is_pair(GRAD) 
         unsigned long long pend_a = 0, pend_b = 0;  // (INPLACE) bit 4 s + k: row y0 + s, column x0 + k
         typename CarryOf<GRAD>::type cy;
         if constexpr (grad_is_pair(GRAD)) {
-            cy.q = fd_carry;
-            cy.d = fd_carry + kFdCarryBytes / 16;  // (smoothed filters: the tap-difference ring after it)
+            cy.q = carry3;
+            cy.d = carry3 + kCarry3Bytes / 16;  // (smoothed filters: the tap-difference ring after it)
             cy.p0 = 0;
             cy.ring = uses_dring(GRAD, PHI);
         }

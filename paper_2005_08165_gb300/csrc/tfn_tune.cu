@@ -11,7 +11,7 @@
 //
 //   tfn-tune 2
 //   device <name with spaces as '_'> sms <SM count> cc <major>.<minor>
-//   entry <input> <grad> <phi> <output> <tile_w> <tile_h> <rows_per_thread> <fd_warps> <warps> <ms>
+//   entry <input> <grad> <phi> <output> <tile_w> <tile_h> <rows_per_thread> <warps_3x3> <warps_other> <ms>
 //
 // Shapes are stored by geometry (item size and CTA widths), not by index, so
 // that a cache stays valid across builds that compile a different list of
@@ -43,12 +43,12 @@ std::string device_line(int dev)
     return buf;
 }
 
-// (version 1 entries give no widths: the default ones, 2 warps for FD and 4 for the others)
-int shape_index(int tw, int th, int pr, int fdw = 2, int w = 4)
+// (version 1 entries give no widths: the default ones, 2 warps for the 3x3 filters and 4 for the others)
+int shape_index(int tw, int th, int pr, int w3 = 2, int w5 = 4)
 {
     for (int k = 0; k < kNumCfg; ++k)
-        if (kCfgs[k].tw == tw && kCfgs[k].th == th && kCfgs[k].pr == pr && kCfgs[k].fd_warps == fdw &&
-            kCfgs[k].warps == w)
+        if (kCfgs[k].tw == tw && kCfgs[k].th == th && kCfgs[k].pr == pr && kCfgs[k].warps3 == w3 &&
+            kCfgs[k].warps5 == w5)
             return k;
     return -1;
 }
@@ -135,7 +135,7 @@ tfn_status tfn_tune_cache_save(tfn_ctx *c, const char *path)
                     const int t = c->tuned[k][gi][p][o];
                     if (t < 0) continue;
                     ok = ok && fprintf(f, "entry %d %d %d %d %d %d %d %d %d %.6f\n", k, gi, p, o, kCfgs[t].tw,
-                                       kCfgs[t].th, kCfgs[t].pr, kCfgs[t].fd_warps, kCfgs[t].warps,
+                                       kCfgs[t].th, kCfgs[t].pr, kCfgs[t].warps3, kCfgs[t].warps5,
                                        (double)c->tuned_ms[k][gi][p][o]) > 0;
                 }
     ok = (fclose(f) == 0) && ok;
@@ -175,18 +175,18 @@ tfn_status tfn_tune_cache_load(tfn_ctx *c, const char *path)
     std::vector<E> es;
     for (size_t i = 2; i < lines.size(); ++i) {
         if (lines[i].empty()) continue;
-        int k, gi, p, o, tw, th, pr, fdw = 2, w = 4, used = 0;
+        int k, gi, p, o, tw, th, pr, w3 = 2, w5 = 4, used = 0;
         float ms;
         const bool parsed =
-            v2 ? sscanf(lines[i].c_str(), "entry %d %d %d %d %d %d %d %d %d %f%n", &k, &gi, &p, &o, &tw, &th, &pr, &fdw,
-                        &w, &ms, &used) == 10
+            v2 ? sscanf(lines[i].c_str(), "entry %d %d %d %d %d %d %d %d %d %f%n", &k, &gi, &p, &o, &tw, &th, &pr, &w3,
+                        &w5, &ms, &used) == 10
                : sscanf(lines[i].c_str(), "entry %d %d %d %d %d %d %d %f%n", &k, &gi, &p, &o, &tw, &th, &pr, &ms,
                         &used) == 8;
         if (!parsed || (size_t)used != lines[i].size()) return TFN_ERR_INVALID_ARG;
         if (k < 0 || k >= KIND_COUNT || gi < 0 || gi >= GRAD_COUNT || p < 0 || p >= PHI_COUNT || o < 0 ||
             o >= kOutCount || !(ms >= 0.f))
             return TFN_ERR_INVALID_ARG;
-        const int shape = shape_index(tw, th, pr, fdw, w);
+        const int shape = shape_index(tw, th, pr, w3, w5);
         if (shape >= 0) es.push_back({k, gi, p, o, shape, ms});
     }
     for (const E &e : es) {

@@ -249,7 +249,7 @@ def test_autotune_table_and_cache_file(torch, tfn, ctx, tmp_path):
         c.save_tune_cache(path)
     text = open(path).read().splitlines()
     assert text[0] == "tfn-tune 2" and text[1].startswith("device ") and len(text) == 3
-    # the entry names the shape by its geometry: item size, then the CTA widths (FD, others)
+    # the entry names the shape by its geometry: item size, then the CTA widths (3x3 filters, others)
     fields = text[2].split()
     shapes, warps = tfn.tile_shapes(), tfn.tile_shape_warps()
     assert tuple(map(int, fields[5:8])) == shapes[best] and tuple(map(int, fields[8:10])) == warps[best]

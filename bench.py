@@ -803,7 +803,8 @@ def run_serving(torch, tfn, ctx, dev, depth_dev, n_req):
                                 "mean_batch": round(st["mean_batch_frames"], 1),
                                 "gpixels_per_s": round(st["pixels"] / st["elapsed_s"] / 1e9, 2),
                                 "max_batches_in_flight": int(st["max_batches_in_flight"]),
-                                "device_overlaps": int(st["device_overlaps"]), "graph_launches": int(st["graph_launches"])}
+                                "device_overlaps": int(st["device_overlaps"]), "graph_launches": int(st["graph_launches"]),
+                                "graph_captures": int(st["graph_captures"])}
             mix["poisson"] = []
             for frac in (0.5, 0.8, 1.0):
                 runs = []
@@ -811,14 +812,15 @@ def run_serving(torch, tfn, ctx, dev, depth_dev, n_req):
                     got, st = serve_stream(tfn, srv, frames, order, tfn.TFN_REQ_HOST, rate=frac * sat,
                                            seed=int(frac * 10) + 100 * rep)
                     runs.append((got, st["latency_p50_us"] / 1e3, st["latency_p99_us"] / 1e3, st["mean_batch_frames"],
-                                 st["admitted_while_busy"]))
+                                 st["admitted_while_busy"], st["graph_captures"]))
                 mix["poisson"].append({"offered_per_s": round(frac * sat, 1),
                                        "achieved_per_s": round(statistics.median(r[0] for r in runs), 1),
                                        "p50_ms": round(statistics.median(r[1] for r in runs), 3),
                                        "p99_ms": round(statistics.median(r[2] for r in runs), 3),
                                        "p99_ms_runs": [round(r[2], 3) for r in runs],
                                        "mean_batch": round(statistics.median(r[3] for r in runs), 1),
-                                       "admitted_while_busy": int(statistics.median(r[4] for r in runs))})
+                                       "admitted_while_busy": int(statistics.median(r[4] for r in runs)),
+                                       "graph_captures": [int(r[5]) for r in runs]})
         return mix
 
     out["mix_host"] = mix_runs(True, 3)

@@ -388,6 +388,9 @@ typedef struct tfn_serving_stats {
     uint64_t admitted_while_busy;   /* requests admitted while an earlier batch was in flight */
     uint64_t device_overlaps;       /* batches whose kernels started on the device before the
                                        previous batch's kernels had finished (CUDA events) */
+    uint64_t graph_captures;        /* of graph_launches, those whose graph was captured first
+                                       (a new combination of input kinds and tile shapes, or one
+                                       evicted from the pipeline's 64 graphs since) */
 } tfn_serving_stats;
 
 /* Creates a server on ctx's device.  The server owns a context of its own

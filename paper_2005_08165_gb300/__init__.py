@@ -83,7 +83,8 @@ class tfn_serving_stats(ctypes.Structure):
                 ("latency_samples", ctypes.c_uint64), ("queued", ctypes.c_int32), ("in_flight", ctypes.c_int32),
                 ("staging_bytes_in_use", ctypes.c_size_t), ("staging_bytes_capacity", ctypes.c_size_t),
                 ("graph_launches", ctypes.c_uint64), ("max_batches_in_flight", ctypes.c_uint64),
-                ("admitted_while_busy", ctypes.c_uint64), ("device_overlaps", ctypes.c_uint64)]
+                ("admitted_while_busy", ctypes.c_uint64), ("device_overlaps", ctypes.c_uint64),
+                ("graph_captures", ctypes.c_uint64)]
 
 
 _P = ctypes.c_void_p

@@ -100,6 +100,7 @@ struct Result {
 struct Batch {
     int pipe;
     bool has_block;
+    bool captured = false;  // its kernels were captured into a new graph (not replayed from one)
     std::vector<Request> reqs;
     tfn_status launch_status = TFN_OK;  // failure while enqueueing
 };
@@ -123,7 +124,7 @@ struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     std::vector<cudaGraphNode_t> fn_node, rf_node;  // per launch
 };
-constexpr size_t kMaxGraphs = 16;  // per pipeline
+constexpr size_t kMaxGraphs = 64;  // per pipeline, least recently used first out
 
 struct Pipe {
     cudaStream_t stream = nullptr;
@@ -167,7 +168,7 @@ struct tfn_server {
     // statistics (under mu)
     uint64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, rejected = 0, batches = 0, batch_frames = 0;
     uint64_t pixels = 0;
-    uint64_t graph_launches = 0, max_inflight = 0, admitted_busy = 0, device_overlaps = 0;
+    uint64_t graph_launches = 0, graph_captures = 0, max_inflight = 0, admitted_busy = 0, device_overlaps = 0;
     Clock::time_point t0;
     std::vector<float> lat_us;  // ring of the last kLatencyWindow latencies
     size_t lat_next = 0;
@@ -210,7 +211,8 @@ void destroy_graph(GraphEntry &e)
 // Enqueues a batch's kernels (frames of any input kinds, device pointers)
 // on the pipeline's stream from one of its graphs: the frames grouped by
 // input kind, one launch each, the descriptors in the pipeline's own slots.
-tfn_status enqueue_kernels_graph(tfn_server *s, Pipe &p, const std::vector<tfn_frame> &dev, const tfn_method &m)
+tfn_status enqueue_kernels_graph(tfn_server *s, Pipe &p, const std::vector<tfn_frame> &dev, const tfn_method &m,
+                                 bool *captured)
 {
     tfn_ctx *c = s->ctx;
     std::vector<LaunchSpec> specs;
@@ -262,9 +264,16 @@ tfn_status enqueue_kernels_graph(tfn_server *s, Pipe &p, const std::vector<tfn_f
         specs.push_back(L);
         key.insert(key.end(), {kind, cfg, noref, L.rf != nullptr});
     }
+    // the graphs are kept in order of use: a hit moves to the back, a capture
+    // past the limit evicts the front (the least recently used)
     GraphEntry *ge = nullptr;
-    for (GraphEntry &e : p.graphs)
-        if (e.key == key) ge = &e;
+    for (size_t i = 0; i < p.graphs.size(); ++i)
+        if (p.graphs[i].key == key) {
+            std::rotate(p.graphs.begin() + i, p.graphs.begin() + i + 1, p.graphs.end());
+            ge = &p.graphs.back();
+            break;
+        }
+    *captured = ge == nullptr;
     if (ge) {
         for (size_t i = 0; i < specs.size(); ++i) {
             LaunchSpec &L = specs[i];
@@ -288,7 +297,7 @@ tfn_status enqueue_kernels_graph(tfn_server *s, Pipe &p, const std::vector<tfn_f
             }
         }
     } else {
-        if (p.graphs.size() >= kMaxGraphs) {  // (the oldest goes)
+        if (p.graphs.size() >= kMaxGraphs) {  // (the least recently used goes)
             destroy_graph(p.graphs.front());
             p.graphs.erase(p.graphs.begin());
         }
@@ -381,7 +390,7 @@ tfn_status enqueue_batch(tfn_server *s, Batch &b, size_t block_off)
     // the pipeline's status word themselves)
     tfn_status st;
     if (s->use_graphs) {
-        st = enqueue_kernels_graph(s, p, dev, m);
+        st = enqueue_kernels_graph(s, p, dev, m, &b.captured);
     } else {
         st = cuda_ok(cudaMemsetAsync(p.status_dev, 0, 2 * sizeof(uint32_t), p.stream), "cudaMemsetAsync(status)")
                  ? run_batch(s->ctx, dev.data(), (int)dev.size(), m, p.stream, p.status_dev)
@@ -479,6 +488,7 @@ void launcher_main(tfn_server *s)
         }
         lk.lock();
         if (b.launch_status == TFN_OK && s->use_graphs) ++s->graph_launches;
+        if (b.captured) ++s->graph_captures;
         s->inflight.push_back(std::move(b));
         s->max_inflight = std::max<uint64_t>(s->max_inflight, s->inflight.size());
         s->cv_retire.notify_one();
@@ -757,9 +767,10 @@ tfn_status tfn_server_stats(tfn_server *s, tfn_serving_stats *o, int reset)
     o->max_batches_in_flight = s->max_inflight;
     o->admitted_while_busy = s->admitted_busy;
     o->device_overlaps = s->device_overlaps;
+    o->graph_captures = s->graph_captures;
     if (reset) {
         s->submitted = s->completed = s->failed = s->cancelled = s->rejected = s->batches = s->batch_frames = 0;
-        s->graph_launches = s->max_inflight = s->admitted_busy = s->device_overlaps = 0;
+        s->graph_launches = s->graph_captures = s->max_inflight = s->admitted_busy = s->device_overlaps = 0;
         s->pixels = 0;
         s->t0 = now;
         s->lat_us.clear();

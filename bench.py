@@ -667,8 +667,18 @@ SERVE_SIZES = ((240, 320), (480, 640), (720, 1280), (1080, 1920))
 def serve_stream(tfn, srv, frames, order, flags, rate=None, seed=0):
     """Submits requests order[i] -> frames[order[i]] (a list per pool entry of prebuilt tfn_frame slots; a
     slot is reused only after its previous request completed), open loop with Poisson arrivals at `rate`
-    requests/s, or as fast as possible (rate None).  Returns (requests/s achieved, server stats)."""
+    requests/s, or as fast as possible (rate None).  Returns (requests/s achieved, server stats, the
+    99th percentile of how late a Poisson submission was against its schedule, in ms, and how many
+    submissions had to wait for their slot's previous request).  A slot wait makes the generator
+    closed-loop for a moment and releases the submissions behind it as a burst; with four slots per
+    pool entry a Poisson run at half the saturated rate meets one only behind a request that was
+    already slow.
+
+    Python's cyclic garbage collector is off during the loop, for the same reason: one of its pauses
+    would hold the submissions back and then release them as a burst, which the server would rightly
+    count as queueing but which is the load generator's, not the server's."""
     import ctypes
+    import gc
     import random
     rnd = random.Random(seed)
     submit, wait = tfn.tfn_submit, tfn.tfn_wait
@@ -677,28 +687,41 @@ def serve_stream(tfn, srv, frames, order, flags, rate=None, seed=0):
     res = ctypes.c_int()
     outstanding = {}
     used = [0] * len(frames)
+    late = []
+    blocked = 0
     srv.stats(reset=True)
-    start = time.perf_counter()
-    due = start
-    for p in order:
-        if rate:
-            due += rnd.expovariate(rate)
-            while time.perf_counter() < due:
-                pass
-        slots = frames[p]
-        j = used[p] % len(slots)
-        used[p] += 1
-        key = (p, j)
-        if key in outstanding:
-            tfn.check(wait(h, outstanding.pop(key), 60000, ctypes.byref(res)), "tfn_wait")
+    gc_was = gc.isenabled()
+    gc.disable()
+    try:
+        start = time.perf_counter()
+        due = start
+        for p in order:
+            if rate:
+                due += rnd.expovariate(rate)
+                now = time.perf_counter()
+                while now < due:
+                    now = time.perf_counter()
+                late.append(now - due)
+            slots = frames[p]
+            j = used[p] % len(slots)
+            used[p] += 1
+            key = (p, j)
+            if key in outstanding:
+                w0 = time.perf_counter()
+                tfn.check(wait(h, outstanding.pop(key), 60000, ctypes.byref(res)), "tfn_wait")
+                tfn.check(res.value, "request")
+                blocked += time.perf_counter() - w0 > 50e-6
+            tfn.check(submit(h, ctypes.byref(slots[j]), flags, ctypes.byref(t)), "tfn_submit")
+            outstanding[key] = t.value
+        for tk in outstanding.values():
+            tfn.check(wait(h, tk, 60000, ctypes.byref(res)), "tfn_wait")
             tfn.check(res.value, "request")
-        tfn.check(submit(h, ctypes.byref(slots[j]), flags, ctypes.byref(t)), "tfn_submit")
-        outstanding[key] = t.value
-    for tk in outstanding.values():
-        tfn.check(wait(h, tk, 60000, ctypes.byref(res)), "tfn_wait")
-        tfn.check(res.value, "request")
-    dt = time.perf_counter() - start
-    return len(order) / dt, srv.stats()
+        dt = time.perf_counter() - start
+    finally:
+        if gc_was:
+            gc.enable()
+    late_p99 = sorted(late)[int(0.99 * (len(late) - 1))] * 1e3 if late else 0.0
+    return len(order) / dt, srv.stats(), late_p99, blocked
 
 
 def run_serving(torch, tfn, ctx, dev, depth_dev, n_req):
@@ -744,7 +767,7 @@ def run_serving(torch, tfn, ctx, dev, depth_dev, n_req):
     with tfn.Server(ctx, grad="fd", phi="mean", output="f16") as srv:
         serve_stream(tfn, srv, frames16, list(range(nf)), 0)  # warm-up
         order = [k % nf for k in range(8 * nf)]
-        fps16, st = serve_stream(tfn, srv, frames16, order, 0)
+        fps16, st, _, _ = serve_stream(tfn, srv, frames16, order, 0)
     out["fp16_serving_device"] = {"frames_per_s": round(fps16, 1), "p50_ms": round(st["latency_p50_us"] / 1e3, 3),
                                   "p99_ms": round(st["latency_p99_us"] / 1e3, 3),
                                   "mean_batch": round(st["mean_batch_frames"], 1),
@@ -753,7 +776,7 @@ def run_serving(torch, tfn, ctx, dev, depth_dev, n_req):
     del nrm, d16, o16
     # the serving mix: resolutions uniform over SERVE_SIZES, FP32/FP16 uniform, per-request intrinsics
     # fx = fy = 481.2 W/640 x U(0.95, 1.05); host buffers (page-locked); 4 scenes per resolution and type,
-    # 2 output slots each
+    # 4 output slots each (1.4 GB of page-locked outputs; at most 128 requests in flight when saturated)
     rng = np.random.default_rng(10 ** 6)
     pool = []
     pool_cams = []
@@ -766,7 +789,7 @@ def run_serving(torch, tfn, ctx, dev, depth_dev, n_req):
             for arr in (img, img.astype(np.float16)):
                 inp = torch.from_numpy(arr).pin_memory()
                 slots = []
-                for _ in range(2):
+                for _ in range(4):
                     n_ = torch.empty((3, Hh, Ww), dtype=torch.float32, pin_memory=True)
                     m_ = torch.empty((Hh, Ww), dtype=torch.uint8, pin_memory=True)
                     slots.append((tfn.make_frame(inp, n_, m_, r.camera), n_, m_))
@@ -797,7 +820,7 @@ def run_serving(torch, tfn, ctx, dev, depth_dev, n_req):
                "requests": n_req, "cuda_graphs": graphs, "passes_per_rate": passes}
         with tfn.Server(ctx, grad="fd", phi="mean", output="f32", graphs=graphs) as srv:
             serve_stream(tfn, srv, frames, order[:256], tfn.TFN_REQ_HOST)  # warm-up
-            sat, st = serve_stream(tfn, srv, frames, order, tfn.TFN_REQ_HOST)
+            sat, st, _, _ = serve_stream(tfn, srv, frames, order, tfn.TFN_REQ_HOST)
             mix["saturated"] = {"requests_per_s": round(sat, 1), "p50_ms": round(st["latency_p50_us"] / 1e3, 3),
                                 "p99_ms": round(st["latency_p99_us"] / 1e3, 3),
                                 "mean_batch": round(st["mean_batch_frames"], 1),
@@ -809,10 +832,10 @@ def run_serving(torch, tfn, ctx, dev, depth_dev, n_req):
             for frac in (0.5, 0.8, 1.0):
                 runs = []
                 for rep in range(passes):
-                    got, st = serve_stream(tfn, srv, frames, order, tfn.TFN_REQ_HOST, rate=frac * sat,
+                    got, st, late, blocked = serve_stream(tfn, srv, frames, order, tfn.TFN_REQ_HOST, rate=frac * sat,
                                            seed=int(frac * 10) + 100 * rep)
                     runs.append((got, st["latency_p50_us"] / 1e3, st["latency_p99_us"] / 1e3, st["mean_batch_frames"],
-                                 st["admitted_while_busy"], st["graph_captures"]))
+                                 st["admitted_while_busy"], st["graph_captures"], late, blocked))
                 mix["poisson"].append({"offered_per_s": round(frac * sat, 1),
                                        "achieved_per_s": round(statistics.median(r[0] for r in runs), 1),
                                        "p50_ms": round(statistics.median(r[1] for r in runs), 3),
@@ -820,7 +843,9 @@ def run_serving(torch, tfn, ctx, dev, depth_dev, n_req):
                                        "p99_ms_runs": [round(r[2], 3) for r in runs],
                                        "mean_batch": round(statistics.median(r[3] for r in runs), 1),
                                        "admitted_while_busy": int(statistics.median(r[4] for r in runs)),
-                                       "graph_captures": [int(r[5]) for r in runs]})
+                                       "graph_captures": [int(r[5]) for r in runs],
+                                       "client_late_p99_ms": [round(r[6], 3) for r in runs],
+                                       "slot_waits": [int(r[7]) for r in runs]})
         return mix
 
     out["mix_host"] = mix_runs(True, 3)

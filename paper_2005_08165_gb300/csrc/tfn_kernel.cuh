@@ -309,45 +309,83 @@ __device__ __forceinline__ Vec3 refine_candidates(const float (&z)[3][3], const 
                                                   int v, float fx, float fy, float u0, float v0)
 {
     const float zi = z[1][1];
+    // the candidates in fixed slots q = 2 p + side (pair p's neighbour j_p,
+    // then -j_p), so that they stay in registers; kept[q]: the neighbour is
+    // valid and differs from the centre
     df R[8];
+    bool kept[8];
     int m = 0;
+#pragma unroll
     for (int p = 0; p < 4; ++p) {
         const int du = pair_du(p), dv = pair_dv(p);
         df num = Gu;
         if (p == 1) num = Gv;
         if (p == 2) num = df_add(Gu, Gv);
         if (p == 3) num = df_add(Gu, df_neg(Gv));
+#pragma unroll
         for (int side = 0; side < 2; ++side) {
-            const int a = 1 + (side ? -dv : dv), b = 1 + (side ? -du : du);
+            const int a = 1 + (side ? -dv : dv), b = 1 + (side ? -du : du), q = 2 * p + side;
             const float zj = z[a][b];
             const df nj = side ? df_neg(num) : num;
-            if (!ok[a][b] || zj == zi) continue;
-            df r;
-            if (KindTraits<KIND>::disparity)  // Z_j / dz_j = d_i / (d_i - d_j)
-                r = df_div(df_mul_f(nj, zi), two_sum(zi, -zj));
-            else
-                r = df_div(df_mul_f(nj, zj), two_sum(zj, -zi));
-            R[m++] = r;
+            kept[q] = ok[a][b] && zj != zi;
+            R[q] = df{0.f, 0.f};
+            if (kept[q]) {
+                if (KindTraits<KIND>::disparity)  // Z_j / dz_j = d_i / (d_i - d_j)
+                    R[q] = df_div(df_mul_f(nj, zi), two_sum(zi, -zj));
+                else
+                    R[q] = df_div(df_mul_f(nj, zj), two_sum(zj, -zi));
+            }
+            m += kept[q] ? 1 : 0;
         }
     }
     df F = {0.f, 0.f};
     if (PHI == PHI_MEAN) {
-        for (int k = 0; k < m; ++k) F = df_add(F, R[k]);
+        // the kept candidates summed in slot order
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (kept[q]) F = df_add(F, R[q]);
         F = df_div(F, df{(float)m, 0.f});
     } else {
-        for (int i = 1; i < m; ++i) {  // insertion sort by the leading part
-            df x = R[i];
-            int k = i - 1;
-            while (k >= 0 && R[k].h > x.h) {
-                R[k + 1] = R[k];
-                --k;
-            }
-            R[k + 1] = x;
+        // The kept candidates in ascending order of their leading parts, ties
+        // in slot order (a stable sort), by a sorting network over all 8
+        // slots keyed on (leading part, slot): a dropped slot holds a
+        // sentinel, +inf, -inf, +inf, ... in turn, so that the kept ones
+        // always straddle the middle slots 3 and 4.
+        float sh[8], sl[8];
+        int si[8];
+        float sent = __uint_as_float(0x7f800000u);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            sh[q] = kept[q] ? R[q].h : sent;
+            sl[q] = kept[q] ? R[q].l : 0.f;
+            si[q] = q;
+            sent = kept[q] ? sent : -sent;
         }
+#define TFN_CE2(i, j)                                                            \
+    {                                                                            \
+        const bool sw_ = sh[i] > sh[j] || (sh[i] == sh[j] && si[i] > si[j]);     \
+        const float h_ = sw_ ? sh[j] : sh[i], l_ = sw_ ? sl[j] : sl[i];          \
+        const int i_ = sw_ ? si[j] : si[i];                                      \
+        sh[j] = sw_ ? sh[i] : sh[j];                                             \
+        sl[j] = sw_ ? sl[i] : sl[j];                                             \
+        si[j] = sw_ ? si[i] : si[j];                                             \
+        sh[i] = h_;                                                              \
+        sl[i] = l_;                                                              \
+        si[i] = i_;                                                              \
+    }
+        TFN_CE2(0, 2) TFN_CE2(1, 3) TFN_CE2(4, 6) TFN_CE2(5, 7)
+        TFN_CE2(0, 4) TFN_CE2(1, 5) TFN_CE2(2, 6) TFN_CE2(3, 7)
+        TFN_CE2(0, 1) TFN_CE2(2, 3) TFN_CE2(4, 5) TFN_CE2(6, 7)
+        TFN_CE2(2, 4) TFN_CE2(3, 5)
+        TFN_CE2(1, 4) TFN_CE2(3, 6)
+        TFN_CE2(1, 2) TFN_CE2(3, 4) TFN_CE2(5, 6)
+#undef TFN_CE2
+        // m kept: the middle one is slot 3 (m odd), the middle two slots 3
+        // and 4 (m even)
         if (m > 0) {
-            F = R[m / 2];
+            F = df{sh[3], sl[3]};
             if (!(m & 1)) {
-                F = df_add(R[m / 2 - 1], R[m / 2]);
+                F = df_add(df{sh[3], sl[3]}, df{sh[4], sl[4]});
                 F = {0.5f * F.h, 0.5f * F.l};
             }
         }

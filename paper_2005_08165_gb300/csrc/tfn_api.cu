@@ -385,8 +385,21 @@ tfn_status enqueue_launch(LaunchSpec &L, cudaStream_t stream)
     if (!cuda_ok(cudaLaunchKernel((const void *)L.fn, dim3(L.grid), dim3(L.threads), params, L.smem, stream),
                  "cudaLaunchKernel"))
         return TFN_ERR_CUDA;
-    if (L.rf && !cuda_ok(cudaLaunchKernel((const void *)L.rf, dim3(L.rf_grid), dim3(kRefineThreads), params, 0, stream),
-                         "cudaLaunchKernel(refine)")) {
+    if (!L.rf) return TFN_OK;
+    // the refinement kernel as a programmatic dependent launch: scheduled
+    // while normals_kernel's last blocks run, it waits on the device for that
+    // grid's completion (griddepcontrol.wait) instead of starting after it
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(L.rf_grid);
+    lc.blockDim = dim3(kRefineThreads);
+    lc.dynamicSmemBytes = 0;
+    lc.stream = stream;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    if (!cuda_ok(cudaLaunchKernelExC(&lc, (const void *)L.rf, params), "cudaLaunchKernelEx(refine)")) {
         cudaMemsetAsync(L.d_refine, 0, 128, stream);  // (what the refinement kernel would have zeroed)
         return TFN_ERR_CUDA;
     }

@@ -1816,6 +1816,11 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), grad_is_pair(GRAD) 
         fence_async_shared();
     }
     __syncwarp();
+    // The refinement kernel that follows on the stream (a programmatic
+    // dependent launch) may be scheduled now: its blocks take the SMs this
+    // grid leaves, and wait for the grid's completion before reading the
+    // list.  (No dependent, no effect.)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     const int gw = blockIdx.x * NW + warp, nw = gridDim.x * NW, total = args.total_tiles;
 
@@ -2248,6 +2253,10 @@ __device__ __forceinline__ void refine_at(const LaunchArgs &args, int fi, int x,
 template <int KIND, int GRAD, int PHI>
 __global__ void __launch_bounds__(kRefineThreads) refine_kernel(const __grid_constant__ LaunchArgs args)
 {
+    // launched as a programmatic dependent of normals_kernel: wait until that
+    // grid has completed and its writes (the list, the normals) are visible
+    // (returns at once in a launch without the dependency)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const unsigned long long cnt = *args.rcount;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x, nth = (long long)gridDim.x * blockDim.x;
     unsigned nref = 0;

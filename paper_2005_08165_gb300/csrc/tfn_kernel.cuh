@@ -119,12 +119,17 @@ __device__ __forceinline__ df df_mul(df a, df b)
     return fast_two_sum(p.h, __fadd_rn(p.l, __fmaf_rn(a.h, b.l, __fmul_rn(a.l, b.h))));
 }
 
-// Long division in double-float: q1 = a/b, correct with the residual.
+// Long division in double-float (Dekker's): q1 = a_h / b_h from the
+// hardware reciprocal (within about 2u), the residual a - b q1 in
+// double-float (nearly exact), and its quotient as the correction; h + l is
+// then within a few u^2 of a / b, relative, for operands and residuals in
+// the normal range.  No branch: the refinement's eight quotients can overlap.
 __device__ __forceinline__ df df_div(df a, df b)
 {
-    float q1 = __fdiv_rn(a.h, b.h);
-    df r = df_add(a, df_neg(df_mul_f(b, q1)));
-    float q2 = __fdiv_rn(r.h, b.h);
+    const float rb = rcp_approx(b.h);
+    const float q1 = __fmul_rn(a.h, rb);
+    const df r = df_add(a, df_neg(df_mul_f(b, q1)));
+    const float q2 = __fmul_rn(r.h, rb);
     return fast_two_sum(q1, q2);
 }
 
@@ -328,23 +333,27 @@ __device__ __forceinline__ Vec3 refine_candidates(const float (&z)[3][3], const 
             const float zj = z[a][b];
             const df nj = side ? df_neg(num) : num;
             kept[q] = ok[a][b] && zj != zi;
-            R[q] = df{0.f, 0.f};
-            if (kept[q]) {
-                if (KindTraits<KIND>::disparity)  // Z_j / dz_j = d_i / (d_i - d_j)
-                    R[q] = df_div(df_mul_f(nj, zi), two_sum(zi, -zj));
-                else
-                    R[q] = df_div(df_mul_f(nj, zj), two_sum(zj, -zi));
-            }
+            // (computed for every slot, without a branch, so that the eight
+            // quotients overlap; a dropped slot's value may be inf or NaN
+            // and is never selected)
+            if (KindTraits<KIND>::disparity)  // Z_j / dz_j = d_i / (d_i - d_j)
+                R[q] = df_div(df_mul_f(nj, zi), two_sum(zi, -zj));
+            else
+                R[q] = df_div(df_mul_f(nj, zj), two_sum(zj, -zi));
             m += kept[q] ? 1 : 0;
         }
     }
     df F = {0.f, 0.f};
     if (PHI == PHI_MEAN) {
-        // the kept candidates summed in slot order
+        // the kept candidates summed pairwise (a dropped slot adds an exact 0)
+        df t[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (kept[q]) F = df_add(F, R[q]);
-        F = df_div(F, df{(float)m, 0.f});
+        for (int q = 0; q < 8; ++q) t[q] = kept[q] ? R[q] : df{0.f, 0.f};
+#pragma unroll
+        for (int w = 1; w < 8; w *= 2)
+#pragma unroll
+            for (int q = 0; q < 8; q += 2 * w) t[q] = df_add(t[q], t[q + w]);
+        F = df_div(t[0], df{(float)m, 0.f});
     } else {
         // The kept candidates in ascending order of their leading parts, ties
         // in slot order (a stable sort), by a sorting network over all 8

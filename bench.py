@@ -394,7 +394,7 @@ def run_ours(args):
     total_ms, fps = job_throughput(total_ms, nf * passes * args.steps, world, dev)
     status = ctx.device_status()
     ms_step = total_ms / args.steps
-    launch_ms = statistics.mean(per) / passes  # one pass: normals_kernel, then refine_kernel where it can flag pixels
+    launch_ms = statistics.mean(per) / passes  # one pass: the plan's kernels (the FD mean: normals_kernel alone)
     kernels_per_pass = plans[(args.grad, args.phi)].kernels()
     px = nf * H * W
     achieved = BYTES_PER_PX[bkey] * px / (launch_ms * 1e-3) / 1e9

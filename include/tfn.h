@@ -308,8 +308,20 @@ tfn_status tfn_plan_launch(tfn_plan *plan, tfn_stream stream);
 
 /* Number of kernel launches one tfn_plan_launch runs (per input kind of the
  * batch: normals_kernel, and the refinement kernel where the launch can flag
- * pixels and is large enough to refine in a second kernel). */
+ * pixels and refines them in a second kernel: not for the FD mean, whose
+ * kernel refines its own, nor for the short items of small launches). */
 tfn_status tfn_plan_kernels(const tfn_plan *plan, int32_t *count);
+
+/* The name of kernel `index` (0 .. tfn_plan_kernels - 1, in the order the
+ * plan's graph lists its kernel nodes) as the compiler emitted it: a mangled
+ * C++ name whose template arguments give the instance (input kind, filter,
+ * Phi, tile shape, and whether it is the form without the error bound), as a
+ * profiler lists it.  `*name` points into the CUDA runtime's own storage and
+ * stays valid while the library is loaded.  No counterpart in the paper:
+ * introspection of which compiled kernel a plan replays.  Errors:
+ * TFN_ERR_INVALID_ARG for a NULL argument or an index out of range,
+ * TFN_ERR_CUDA if the runtime cannot name the kernel. */
+tfn_status tfn_plan_kernel_name(const tfn_plan *plan, int32_t index, const char **name);
 
 /* Waits for the device, releases the plan's scratch and graph. NULL is a no-op. */
 tfn_status tfn_plan_destroy(tfn_plan *plan);

@@ -110,6 +110,7 @@ _lib.tfn_plan_create.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINT
 _lib.tfn_plan_launch.argtypes = [_P, _P]
 _lib.tfn_plan_destroy.argtypes = [_P]
 _lib.tfn_plan_kernels.argtypes = [_P, ctypes.POINTER(_I)]
+_lib.tfn_plan_kernel_name.argtypes = [_P, _I, ctypes.POINTER(ctypes.c_char_p)]
 _lib.tfn_refined_pixels.argtypes = [_P, ctypes.POINTER(ctypes.c_uint64), _P]
 _lib.tfn_normals_noalloc.argtypes = [ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), _P]
 _lib.tfn_autotune.argtypes = [_P, ctypes.POINTER(tfn_frame), _I, ctypes.POINTER(tfn_method), _I, _P,
@@ -124,7 +125,7 @@ _lib.tfn_server_stats.argtypes = [_P, ctypes.POINTER(tfn_serving_stats), _I]
 _lib.tfn_server_destroy.argtypes = [_P]
 for _f in ("tfn_create", "tfn_destroy", "tfn_normals", "tfn_normals_batch", "tfn_normals_batch_host",
            "tfn_device_status", "tfn_refined_pixels", "tfn_normals_noalloc", "tfn_plan_create", "tfn_plan_launch",
-           "tfn_plan_destroy", "tfn_plan_kernels", "tfn_autotune", "tfn_tuned_shape", "tfn_tune_cache_save", "tfn_tune_cache_load",
+           "tfn_plan_destroy", "tfn_plan_kernels", "tfn_plan_kernel_name", "tfn_autotune", "tfn_tuned_shape", "tfn_tune_cache_save", "tfn_tune_cache_load",
            "tfn_server_create", "tfn_submit", "tfn_wait", "tfn_server_stats", "tfn_server_destroy"):
     getattr(_lib, _f).restype = _I
 
@@ -147,6 +148,7 @@ tfn_plan_create = _lib.tfn_plan_create
 tfn_plan_launch = _lib.tfn_plan_launch
 tfn_plan_destroy = _lib.tfn_plan_destroy
 tfn_plan_kernels = _lib.tfn_plan_kernels
+tfn_plan_kernel_name = _lib.tfn_plan_kernel_name
 tfn_autotune = _lib.tfn_autotune
 tfn_tuned_shape = _lib.tfn_tuned_shape
 tfn_tune_cache_save = _lib.tfn_tune_cache_save
@@ -163,6 +165,7 @@ TFN_NOALLOC_MAX_FRAMES = 64
 EXPORTED = ["tfn_status_string", "tfn_version", "tfn_last_cuda_error", "tfn_create", "tfn_destroy", "tfn_normals",
             "tfn_normals_batch", "tfn_normals_batch_host", "tfn_device_status", "tfn_refined_pixels",
             "tfn_normals_noalloc", "tfn_plan_create", "tfn_plan_launch", "tfn_plan_destroy", "tfn_plan_kernels",
+            "tfn_plan_kernel_name",
             "tfn_tile_shape_count",
             "tfn_tile_shape_info", "tfn_tile_shape_warps", "tfn_set_tile_shape", "tfn_autotune", "tfn_tuned_shape", "tfn_tune_cache_save",
             "tfn_tune_cache_load", "tfn_server_create", "tfn_submit", "tfn_wait", "tfn_server_stats",
@@ -508,6 +511,15 @@ class Plan:
         n = _I()
         check(tfn_plan_kernels(self.handle, ctypes.byref(n)), "tfn_plan_kernels")
         return n.value
+
+    def kernel_names(self) -> list:
+        """The (mangled) names of the kernels one replay runs."""
+        out = []
+        for i in range(self.kernels()):
+            nm = ctypes.c_char_p()
+            check(tfn_plan_kernel_name(self.handle, i, ctypes.byref(nm)), "tfn_plan_kernel_name")
+            out.append(nm.value.decode())
+        return out
 
     def close(self):
         if self.handle:

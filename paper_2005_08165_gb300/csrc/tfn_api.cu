@@ -22,6 +22,10 @@ KernelFn kernels_depth_f32(int grad, int phi, int cfg, bool noref);
 KernelFn kernels_depth_f16(int grad, int phi, int cfg, bool noref);
 KernelFn kernels_disp_u16(int grad, int phi, int cfg, bool noref);
 KernelFn kernels_disp_f32(int grad, int phi, int cfg, bool noref);
+KernelFn kernels_depth_f32_fdmean(int cfg);
+KernelFn kernels_depth_f16_fdmean(int cfg);
+KernelFn kernels_disp_u16_fdmean(int cfg);
+KernelFn kernels_disp_f32_fdmean(int cfg);
 KernelFn refiners_depth_f32(int grad, int phi);
 KernelFn refiners_depth_f16(int grad, int phi);
 KernelFn refiners_disp_u16(int grad, int phi);
@@ -30,6 +34,15 @@ KernelFn refiners_disp_f32(int grad, int phi);
 KernelFn kernel_for(int kind, int grad, int phi, int cfg, bool noref)
 {
     if (grad_is_sep5(grad)) grad = GRAD_SEP5;  // the named 5x5 filters are weight presets
+    if (grad == GRAD_FD && phi == PHI_MEAN && !noref) {  // (their own translation units)
+        switch (kind) {
+        case KIND_DEPTH_F32: return kernels_depth_f32_fdmean(cfg);
+        case KIND_DEPTH_F16: return kernels_depth_f16_fdmean(cfg);
+        case KIND_DISP_U16: return kernels_disp_u16_fdmean(cfg);
+        case KIND_DISP_F32: return kernels_disp_f32_fdmean(cfg);
+        }
+        return nullptr;
+    }
     switch (kind) {
     case KIND_DEPTH_F32: return kernels_depth_f32(grad, phi, cfg, noref);
     case KIND_DEPTH_F16: return kernels_depth_f16(grad, phi, cfg, noref);
@@ -349,7 +362,7 @@ tfn_status make_launch(int kind, const tfn_method &m, int cfg, bool noref, const
     L.grid = std::max(0, std::min((total_tiles + nw - 1) / nw, per_sm * num_sms));
     // the refinement kernel of this method (none for PlanePCA, which never flags a pixel)
     L.rf = nullptr;
-    if (grad != GRAD_PLANEPCA && !noref && !refines_in_place(cfg) && !(L.rf = refiner_for(kind, grad, method_phi(m))))
+    if (grad != GRAD_PLANEPCA && !noref && !refines_in_kernel(cfg, grad, method_phi(m)) && !(L.rf = refiner_for(kind, grad, method_phi(m))))
         return TFN_ERR_UNSUPPORTED;
     // its grid: the flagged pixels (about one per thousand on noisy frames),
     // as many threads as fit on the GPU at once: each refines its pixels one
@@ -955,6 +968,30 @@ tfn_status tfn_plan_kernels(const tfn_plan *p, int32_t *count)
     }
     *count = k;
     return TFN_OK;
+}
+
+tfn_status tfn_plan_kernel_name(const tfn_plan *p, int32_t index, const char **name)
+{
+    if (!p || !p->graph || !name || index < 0) return TFN_ERR_INVALID_ARG;
+    size_t nn = 0;
+    TFN_CUDA(cudaGraphGetNodes(p->graph, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) TFN_CUDA(cudaGraphGetNodes(p->graph, nodes.data(), &nn));
+    int32_t k = 0;
+    for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        TFN_CUDA(cudaGraphNodeGetType(nodes[i], &t));
+        if (t != cudaGraphNodeTypeKernel) continue;
+        if (k++ != index) continue;
+        cudaKernelNodeParams kp;
+        TFN_CUDA(cudaGraphKernelNodeGetParams(nodes[i], &kp));
+        const char *nm = nullptr;
+        TFN_CUDA(cudaFuncGetName(&nm, kp.func));
+        if (!nm) return TFN_ERR_CUDA;
+        *name = nm;
+        return TFN_OK;
+    }
+    return TFN_ERR_INVALID_ARG;
 }
 
 tfn_status tfn_plan_destroy(tfn_plan *p)

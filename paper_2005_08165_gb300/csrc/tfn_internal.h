@@ -112,6 +112,21 @@ constexpr int kSmallCfg = 3;
 // short-item shape of small launches, where a second launch would cost more
 // than the refinement.
 constexpr bool refines_in_place(int c) { return c == kSmallCfg; }
+// Whether the (shape, filter, Phi) kernel refines its flagged pixels itself
+// through a per-warp queue, 32 pixels at a time, rather than listing them for
+// the refinement kernel: the FD mean in the other shapes.  Its flagged pixels
+// are rare (about 2 per 128 x 30 item on noisy frames), so a warp drains its
+// queue about once in a launch, where a second kernel costs a launch, its
+// latency-bound reads and its fixed time (256 x 480x640 frames: 0.341 ->
+// 0.334 ms a pass).  The FD median flags almost nothing and ran 0.5% slower
+// with the queue's code; the smoothed 3x3 filters and the 5x5 ones keep the
+// list too, as their shared memory already holds as many CTAs per SM as it
+// can.
+constexpr bool refines_by_queue(int c, int grad, int phi)
+{
+    return c != kSmallCfg && grad == GRAD_FD && phi == PHI_MEAN;
+}
+constexpr bool refines_in_kernel(int c, int grad, int phi) { return refines_in_place(c) || refines_by_queue(c, grad, phi); }
 // the default shape otherwise: the tallest items (the least halo per row) measured fastest for every
 // filter on 256 x 480x640 frames (FD mean 0.9%, Sobel 4.5%, the 5x5 filters 13% faster than 18 rows)
 constexpr int kDefaultCfg = 1;

@@ -1,11 +1,12 @@
-// Kernels for one input kind (depth_f16); the instantiations are split by kind so
-// that the translation units compile in parallel.
+// Kernels for one input kind (depth_f16) except the FD mean's with the error bound
+// (tfn_k_depth_f16_fdmean.cu); the instantiations are split by kind so that the
+// translation units compile in parallel.
 #include "tfn_kernel.cuh"
 
 namespace tfn {
 KernelFn kernels_depth_f16(int grad, int phi, int cfg, bool noref)
 {
-    return dev::select_kernel<KIND_DEPTH_F16>(grad, phi, cfg, noref);
+    return dev::select_kernel<KIND_DEPTH_F16, false>(grad, phi, cfg, noref);
 }
 KernelFn refiners_depth_f16(int grad, int phi) { return dev::select_refiner<KIND_DEPTH_F16>(grad, phi); }
 }  // namespace tfn

@@ -37,8 +37,10 @@
 // cancellation inside the candidate sum (mean) or between the two middle
 // candidates (even median), and the effect of the gradient error; each pixel
 // bounds both, and the rare pixels whose bound exceeds the threshold are
-// listed for refine_kernel, which redoes them in double-float arithmetic
-// (refine_pixel) after the main kernel.
+// redone in double-float arithmetic (refine_pixel): by the main kernel itself
+// for the FD mean (a per-warp queue, 32 pixels at a time) and for the short
+// items of small launches (at the end of each item), otherwise by
+// refine_kernel after the main kernel, from a list.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -1750,16 +1752,17 @@ __device__ __forceinline__ int frame_of_item(const FrameDesc *frames, int nframe
 
 // ------------------------------------------------------------ refinement list
 //
-// The main kernel does not refine: a pixel whose FP32 error bound is too
-// loose keeps its FP32 normal, gets bit 1 set in its mask byte, and is
-// appended to the launch's refinement list (frame index << 32 | y << 16 | x).
-// refine_kernel, launched after it on the same stream, redoes the listed
-// pixels in double-float and clears their bit, and its last block zeroes the
-// count for the list's next launch.  Keeping the double-float
-// code out of the row loop's kernel leaves that loop its registers and
-// instruction cache.  A list that overflows its capacity is not lost: the
-// count still grows, and refine_kernel then finds the flagged pixels by their
-// mask bit instead.
+// Except for the FD mean and the short items of small launches, which refine
+// in the main kernel (see normals_kernel), the main kernel does not refine: a
+// pixel whose FP32 error bound is too loose keeps its FP32 normal, gets bit 1
+// set in its mask byte, and is appended to the launch's refinement list
+// (frame index << 32 | y << 16 | x).  refine_kernel, launched after it on the
+// same stream, redoes the listed pixels in double-float and clears their bit,
+// and its last block zeroes the count for the list's next launch.  Keeping
+// the double-float code out of the row loop's kernel leaves that loop its
+// registers and instruction cache.  A list that overflows its capacity is not
+// lost: the count still grows, and refine_kernel then finds the flagged pixels
+// by their mask bit instead.
 
 // Appends the flagged pixels (bit k of rb: column x0 + k) of row y of frame fi.
 static __device__ __noinline__ void list_for_refinement(unsigned long long *rlist, unsigned long long *rcount, int rcap,
@@ -1769,6 +1772,34 @@ static __device__ __noinline__ void list_for_refinement(unsigned long long *rlis
     const unsigned long long e0 = ((unsigned long long)(unsigned)fi << 32) | ((unsigned)y << 16) | (unsigned)x0;
     for (unsigned long long j = base; rb; ++j, rb &= rb - 1u)
         if (j < (unsigned long long)rcap) rlist[j] = e0 + (unsigned)(__ffs(rb) - 1);
+}
+
+// Refines one flagged pixel (x, y) of frame fi of the launch, and clears its
+// mask bit 1 when CLEAR (the refinement kernel's pixels; a kernel that refines
+// its own pixels never sets the bit).
+template <int KIND, int GRAD, int PHI, bool CLEAR>
+__device__ __forceinline__ void refine_at(const LaunchArgs &args, int fi, int x, int y)
+{
+    const FrameDesc *f = args.frames + fi;
+    OutDesc out;
+    out.out = (char *)__ldg((const unsigned long long *)&f->out);
+    out.out_pitch = __ldg(&f->out_pitch);
+    out.out_plane = __ldg(&f->out_plane);
+    out.mask = (uint8_t *)__ldg((const unsigned long long *)&f->mask);
+    out.mask_pitch = __ldg(&f->mask_pitch);
+    const void *in = (const void *)__ldg((const unsigned long long *)&f->in);
+    const int64_t in_pitch = __ldg(&f->in_pitch);
+    const int H = __ldg(&f->H), W = __ldg(&f->W);
+    const float fx = __ldg(&f->fx), fy = __ldg(&f->fy), u0 = __ldg(&f->u0), v0 = __ldg(&f->v0);
+    Vec3 nr;
+    if constexpr (GRAD == GRAD_SEP5)
+        nr = refine_from_input_sep5<KIND, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0, args.w[0], args.w[1],
+                                               args.w[2], args.w[3], args.w[4]);
+    else
+        nr = refine_from_input<KIND, GRAD, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0, args.w[0], args.w[1],
+                                                args.w[2]);
+    store1(out, args.out_fmt, x, y, nr);
+    if (CLEAR) out.mask[(int64_t)y * out.mask_pitch + x] = 1;
 }
 
 // ------------------------------------------------------------ the kernel
@@ -1798,6 +1829,11 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), grad_is_pair(GRAD) 
     // the short-item shape (launches of few items, e.g. one frame) refines
     // in place at the end of each item: a second launch would cost more there
     constexpr bool INPLACE = refines_in_place(CFG);
+    // the FD mean in the other shapes refines its flagged pixels in this
+    // kernel too, through a per-warp queue that the lanes drain 32 at a time
+    // (not the NOREF form, which flags none)
+    constexpr bool QUEUE = refines_by_queue(CFG, GRAD, PHI) && !NOREF;
+    constexpr bool INKERNEL = INPLACE || QUEUE;
     constexpr int HR = SEP5 ? 2 : 1;                  // halo rows above and below an item
     constexpr int NCH = (TH + 2 * HR + CR - 1) / CR;  // chunks per item: rows y0-HR .. y0+TH-1+HR
     static_assert(SEP5 || (TH + 2) % CR == 0, "3x3 items' chunks tile their rows exactly");
@@ -1810,6 +1846,8 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), grad_is_pair(GRAD) 
 
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long full[NW][NST];
+    // (QUEUE) each warp's queue of flagged pixels: frame index << 32 | y << 16 | x
+    __shared__ unsigned long long rqueue[NW][QUEUE ? 32 : 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // (an offset from smem_raw keeps the compiler's knowledge that this is shared memory)
     unsigned char *const sbase = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
@@ -1878,7 +1916,8 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), grad_is_pair(GRAD) 
     const float wts[3] = {args.w[0], args.w[1], args.w[2]};  // GRAD_WEIGHTED's row weights
     const Sep5W sw = {args.w[0], args.w[1], args.w[2], args.w[3], args.w[4]};  // GRAD_SEP5's profiles
     int cf = 0, fail_cc = 0;
-    unsigned nref = 0;  // (INPLACE) pixels refined by this lane
+    unsigned nref = 0;  // (INPLACE, QUEUE) pixels refined by this lane
+    int qn = 0;         // (QUEUE) entries in the warp's queue (the same in every lane)
     bool failed = false;
     for (int i = 0; !failed; ++i) {
         const int t = gw + i * nw;
@@ -1933,7 +1972,7 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), grad_is_pair(GRAD) 
             }
             return true;
         };
-        unsigned long long pend_a = 0, pend_b = 0;  // (INPLACE) bit 4 s + k: row y0 + s, column x0 + k
+        unsigned long long pend_a = 0, pend_b = 0;  // (INPLACE, QUEUE) bit 4 s + k: row y0 + s, column x0 + k
         typename CarryOf<GRAD>::type cy;
         if constexpr (grad_is_pair(GRAD)) {
             cy.q = carry3;
@@ -1966,11 +2005,11 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), grad_is_pair(GRAD) 
                 rb &= (1u << min(nvalid, 4)) - 1u;
                 // pixels whose FP32 error bound is too loose: mask bit 1 set
                 // (bit k of rb to bit 8k + 1), and listed for refine_kernel
-                if constexpr (!INPLACE) mw |= ((rb * 0x00204081u) & 0x01010101u) << 1;
+                if constexpr (!INKERNEL) mw |= ((rb * 0x00204081u) & 0x01010101u) << 1;
                 store4(out, args.out_fmt, x0, y, nvalid, ox, oy, oz, mw);
                 if (has_pts)  // the fused point cloud of this row
                     store_points4<KIND>(f, x0, y, nvalid, sample(C, 1), sample(C, 2), sample(C, 3), sample(C, 4));
-                if constexpr (INPLACE) {  // (redone after the item)
+                if constexpr (INKERNEL) {  // (redone after the item)
                     if (s < 16)
                         pend_a |= (unsigned long long)rb << (4 * s);
                     else
@@ -2179,6 +2218,39 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), grad_is_pair(GRAD) 
                 ++nref;
             }
         }
+        if constexpr (QUEUE) {
+            // this item's flagged pixels join the warp's queue, in rounds of
+            // at most one per lane; whenever it holds 32, each lane refines
+            // one (the later store to the same pixel wins: the __syncwarp
+            // orders the item's stores before the lanes' refined ones)
+            while (__any_sync(0xffffffffu, (pend_a | pend_b) != 0)) {
+                const bool has = (pend_a | pend_b) != 0;
+                const unsigned bal = __ballot_sync(0xffffffffu, has);
+                const int slot = qn + __popc(bal & ((1u << lane) - 1u));
+                if (has && slot < 32) {  // (a lane past the queue's end keeps its pixel for the next round)
+                    int b;
+                    if (pend_a) {
+                        b = __ffsll((long long)pend_a) - 1;
+                        pend_a &= pend_a - 1;
+                    } else {
+                        b = 64 + __ffsll((long long)pend_b) - 1;
+                        pend_b &= pend_b - 1;
+                    }
+                    rqueue[warp][slot] = ((unsigned long long)(unsigned)cf << 32) |
+                                         ((unsigned)(y0 + (b >> 2)) << 16) | (unsigned)(x0 + (b & 3));
+                }
+                qn = min(qn + __popc(bal), 32);
+                if (qn == 32) {
+                    __syncwarp();
+                    const unsigned long long e = rqueue[warp][lane];
+                    refine_at<KIND, GRAD, PHI, false>(args, (int)(e >> 32), (int)(e & 0xffffu),
+                                                      (int)((e >> 16) & 0xffffu));
+                    ++nref;
+                    __syncwarp();  // (every lane has read its entry before the slots are refilled)
+                    qn = 0;
+                }
+            }
+        }
     }
     if (failed) {
         // a copy did not land in time: flag it, then give the copies this warp
@@ -2192,7 +2264,15 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), grad_is_pair(GRAD) 
         __syncwarp();
         return;
     }
-    if constexpr (INPLACE) {
+    if constexpr (QUEUE) {  // the queue's last entries, fewer than 32
+        __syncwarp();
+        if (lane < qn) {
+            const unsigned long long e = rqueue[warp][lane];
+            refine_at<KIND, GRAD, PHI, false>(args, (int)(e >> 32), (int)(e & 0xffffu), (int)((e >> 16) & 0xffffu));
+            ++nref;
+        }
+    }
+    if constexpr (INKERNEL) {
         // count of refined pixels (diagnostics): one atomic per warp, only if any
         const unsigned tot = __reduce_add_sync(0xffffffffu, nref);
         if (lane == 0 && tot) atomicAdd(args.status + 1, tot);
@@ -2200,11 +2280,20 @@ __global__ void __launch_bounds__(32 * cta_warps(CFG, GRAD), grad_is_pair(GRAD) 
 }
 
 // noref: the NOREF form (FP16 depth with the FD filter only; nullptr otherwise).
-template <int KIND>
+// FDMEAN: the FD mean's kernels with the error bound (true), or every other
+// kernel (false).  The two sets are instantiated in separate translation
+// units: the code of the FD mean's refinement queue, compiled into the same
+// module as the other kernels, changed how the compiler allocated their
+// registers (a 48-byte stack frame in every kernel of the module; the Sobel,
+// Scharr, Prewitt and weighted means ran 3-6% slower, the FP16 forms 0.5-3%),
+// though none of them runs that code.
+template <int KIND, bool FDMEAN>
 KernelFn select_kernel(int grad, int phi, int cfg, bool noref)
 {
+    if ((grad == GRAD_FD && phi == PHI_MEAN && !noref) != FDMEAN) return nullptr;
     if (noref) {
-        if constexpr (KIND == KIND_DEPTH_F16) {
+        // (each kernel is instantiated in one translation unit only)
+        if constexpr (KIND == KIND_DEPTH_F16 && !FDMEAN) {
 #define TFN_K(P, C) \
     if (grad == GRAD_FD && phi == P && cfg == C) return &normals_kernel<KIND, GRAD_FD, P, C, true>;
 #define TFN_KC(P) TFN_K(P, 0) TFN_K(P, 1) TFN_K(P, 2) TFN_K(P, 3) TFN_K(P, 4) TFN_K(P, 5)
@@ -2218,39 +2307,17 @@ KernelFn select_kernel(int grad, int phi, int cfg, bool noref)
     if (grad == G && phi == P && cfg == C) return &normals_kernel<KIND, G, P, C, false>;
 #define TFN_KC(G, P) TFN_K(G, P, 0) TFN_K(G, P, 1) TFN_K(G, P, 2) TFN_K(G, P, 3) TFN_K(G, P, 4) TFN_K(G, P, 5)
 #define TFN_KP(G) TFN_KC(G, PHI_MEAN) TFN_KC(G, PHI_MEDIAN)
-    TFN_KP(GRAD_FD) TFN_KP(GRAD_SOBEL) TFN_KP(GRAD_SCHARR) TFN_KP(GRAD_PREWITT) TFN_KP(GRAD_WEIGHTED) TFN_KP(GRAD_SEP5)
-    TFN_KC(GRAD_PLANEPCA, PHI_MEAN)  // (PlanePCA has no Phi)
+    if constexpr (FDMEAN) {
+        TFN_KC(GRAD_FD, PHI_MEAN)
+    } else {
+        TFN_KC(GRAD_FD, PHI_MEDIAN)
+        TFN_KP(GRAD_SOBEL) TFN_KP(GRAD_SCHARR) TFN_KP(GRAD_PREWITT) TFN_KP(GRAD_WEIGHTED) TFN_KP(GRAD_SEP5)
+        TFN_KC(GRAD_PLANEPCA, PHI_MEAN)  // (PlanePCA has no Phi)
+    }
 #undef TFN_KP
 #undef TFN_KC
 #undef TFN_K
     return nullptr;
-}
-
-// Refines one flagged pixel (x, y) of frame fi of the launch and clears its
-// mask bit 1.
-template <int KIND, int GRAD, int PHI>
-__device__ __forceinline__ void refine_at(const LaunchArgs &args, int fi, int x, int y)
-{
-    const FrameDesc *f = args.frames + fi;
-    OutDesc out;
-    out.out = (char *)__ldg((const unsigned long long *)&f->out);
-    out.out_pitch = __ldg(&f->out_pitch);
-    out.out_plane = __ldg(&f->out_plane);
-    out.mask = (uint8_t *)__ldg((const unsigned long long *)&f->mask);
-    out.mask_pitch = __ldg(&f->mask_pitch);
-    const void *in = (const void *)__ldg((const unsigned long long *)&f->in);
-    const int64_t in_pitch = __ldg(&f->in_pitch);
-    const int H = __ldg(&f->H), W = __ldg(&f->W);
-    const float fx = __ldg(&f->fx), fy = __ldg(&f->fy), u0 = __ldg(&f->u0), v0 = __ldg(&f->v0);
-    Vec3 nr;
-    if constexpr (GRAD == GRAD_SEP5)
-        nr = refine_from_input_sep5<KIND, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0, args.w[0], args.w[1],
-                                               args.w[2], args.w[3], args.w[4]);
-    else
-        nr = refine_from_input<KIND, GRAD, PHI>(in, in_pitch, H, W, x, y, fx, fy, u0, v0, args.w[0], args.w[1],
-                                                args.w[2]);
-    store1(out, args.out_fmt, x, y, nr);
-    out.mask[(int64_t)y * out.mask_pitch + x] = 1;
 }
 
 // The second kernel of a launch: the pixels normals_kernel flagged, from its
@@ -2274,7 +2341,7 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(const __grid_con
             const unsigned long long e = args.rlist[i];
             const int fi = (int)(e >> 32);
             if (fi >= args.nframes) continue;  // (not an entry of this launch's frames)
-            refine_at<KIND, GRAD, PHI>(args, fi, (int)(e & 0xffffu), (int)((e >> 16) & 0xffffu));
+            refine_at<KIND, GRAD, PHI, true>(args, fi, (int)(e & 0xffffu), (int)((e >> 16) & 0xffffu));
             ++nref;
         }
     } else {
@@ -2294,7 +2361,7 @@ __global__ void __launch_bounds__(kRefineThreads) refine_kernel(const __grid_con
                     for (unsigned b = w[j] & 0x02020202u; b; b &= b - 1u) {
                         const int x = 16 * c + 4 * j + ((__ffs(b) - 1) >> 3);
                         if (x < W) {
-                            refine_at<KIND, GRAD, PHI>(args, fi, x, y);
+                            refine_at<KIND, GRAD, PHI, true>(args, fi, x, y);
                             ++nref;
                         }
                     }
@@ -2324,10 +2391,12 @@ KernelFn select_refiner(int grad, int phi)
 #define TFN_R(G, P) \
     if (grad == G && phi == P) return &refine_kernel<KIND, G, P>;
 #define TFN_RP(G) TFN_R(G, PHI_MEAN) TFN_R(G, PHI_MEDIAN)
-    TFN_RP(GRAD_FD) TFN_RP(GRAD_SOBEL) TFN_RP(GRAD_SCHARR) TFN_RP(GRAD_PREWITT) TFN_RP(GRAD_WEIGHTED) TFN_RP(GRAD_SEP5)
+    // (the FD mean refines in its own kernel; PlanePCA never flags a pixel)
+    TFN_R(GRAD_FD, PHI_MEDIAN)
+    TFN_RP(GRAD_SOBEL) TFN_RP(GRAD_SCHARR) TFN_RP(GRAD_PREWITT) TFN_RP(GRAD_WEIGHTED) TFN_RP(GRAD_SEP5)
 #undef TFN_RP
 #undef TFN_R
-    return nullptr;  // (PlanePCA never flags a pixel: no refinement kernel)
+    return nullptr;
 }
 
 }  // namespace dev

@@ -1,8 +1,10 @@
 """Parity of the exact call the benchmark times.
 
 bench.py's step replays a plan: the 256 noisy 480x640 frames, their
-descriptors uploaded once, normals_kernel and refine_kernel captured in a CUDA
-graph.  At that size the launch takes the default tile shape, so the
+descriptors uploaded once, the kernels captured in a CUDA graph.  At that size
+the launch takes the default tile shape.  For the FD mean (the benchmark's
+method) normals_kernel refines its flagged pixels itself, through a per-warp
+queue that must start empty on every replay; for the Sobel median the
 refinement kernel runs inside the graph and its list's count must be reset
 between replays (the kernel's last block does it).  Each replay is checked
 against the FP64 oracle on sampled frames and bit for bit against
@@ -71,5 +73,5 @@ def test_bench_plan_replays_match_oracle_and_batch(torch, batch, grad, phi):
         # every replay refines the same pixels (the list is reset between replays)
         assert refined[0] == refined[1] == refined[2]
         if phi == "mean":
-            assert refined[0] > 0, "the noisy batch flags pixels for the refinement kernel"
+            assert refined[0] > 0, "the noisy batch flags pixels for the double-float path"
     np.testing.assert_equal(refined[0], refined[2])

@@ -13,9 +13,10 @@ launches no refinement kernel.  These tests check:
   boundary, the subnormal range, holes beside them) and the noisy scene batch;
 - the promise: the kernel without the bound gives the same normals and masks, bit for bit, for the
   mean and the median, FP32 and FP16 output, the default and the short-item tile shapes;
-- which kernel ran: a qualifying plan replays one kernel per pass, the same plan with
-  TFN_FLAG_FULL_BOUND two (normals_kernel and the refinement kernel), and so does a plan whose focal
-  length is too short to qualify;
+- which kernel ran, by the names of the kernels a plan replays: a qualifying plan runs the form
+  without the bound (its NOREF template argument true), the same plan with TFN_FLAG_FULL_BOUND the
+  form with it, and so does a plan whose focal length is too short to qualify; for the median the
+  bound form is also followed by the refinement kernel (the FD mean's kernel refines its own pixels);
 - accuracy: the adversarial frames match the FP64 oracle under the usual 1e-3 degree rule.
 """
 import numpy as np
@@ -128,7 +129,7 @@ def _plan_kernels(torch, tfn, ctx, ins, cam, flags, phi="mean"):
     masks = [tfn.empty_image((H, W), torch.uint8) for _ in ins]
     plan = ctx.plan(ins, cam, grad="fd", phi=phi, output="f16", normals=outs, masks=masks, flags=flags)
     try:
-        k = plan.kernels()
+        k = plan.kernel_names()
         plan.launch()
         torch.cuda.synchronize()
     finally:
@@ -136,25 +137,40 @@ def _plan_kernels(torch, tfn, ctx, ins, cam, flags, phi="mean"):
     return k, outs, masks
 
 
-def test_which_kernel_runs(torch, tfn, ctx):
+def _forms(names):
+    # per kernel: "noref" (normals_kernel<..., NOREF = true>), "bound" (NOREF = false) or "refine"
+    out = []
+    for nm in names:
+        if "normals_kernel" in nm:
+            assert ("Lb1EEEv" in nm) != ("Lb0EEEv" in nm), nm
+            out.append("noref" if "Lb1EEEv" in nm else "bound")
+        else:
+            assert "refine_kernel" in nm, nm
+            out.append("refine")
+    return out
+
+
+@pytest.mark.parametrize("phi", ["mean", "median"])
+def test_which_kernel_runs(torch, tfn, ctx, phi):
     imgs = scenes.noisy_batch(40, seed0=4100).astype(np.float16)
     ins = [to_dev(torch, tfn, img) for img in imgs]
-    k0, n0, m0 = _plan_kernels(torch, tfn, ctx, ins, CAM, 0)
-    k1, n1, m1 = _plan_kernels(torch, tfn, ctx, ins, CAM, tfn.TFN_FLAG_FULL_BOUND)
-    assert (k0, k1) == (1, 2)
+    bound = ["bound"] if phi == "mean" else ["bound", "refine"]  # (the FD mean refines in its own kernel)
+    k0, n0, m0 = _plan_kernels(torch, tfn, ctx, ins, CAM, 0, phi)
+    k1, n1, m1 = _plan_kernels(torch, tfn, ctx, ins, CAM, tfn.TFN_FLAG_FULL_BOUND, phi)
+    assert (_forms(k0), _forms(k1)) == (["noref"], bound)
     assert all(torch.equal(a, b) for a, b in zip(n0, n1)) and all(torch.equal(a, b) for a, b in zip(m0, m1))
     # a focal length too short for the proof (1.84 x 2049 / 150 = 25 > the threshold): the bound kernel runs
     short = dict(CAM, fx=150.0, fy=150.0)
-    ks, _, _ = _plan_kernels(torch, tfn, ctx, ins, short, 0)
-    assert ks == 2
+    ks, _, _ = _plan_kernels(torch, tfn, ctx, ins, short, 0, phi)
+    assert _forms(ks) == bound
     # FP32 depth never qualifies
     d32 = [tfn.empty_image((H, W), torch.float32) for _ in range(40)]
     for t, img in zip(d32, imgs):
         t.copy_(torch.from_numpy(img.astype(np.float32)))
     outs = [tfn.empty_normals(H, W, "f32") for _ in d32]
     masks = [tfn.empty_image((H, W), torch.uint8) for _ in d32]
-    plan = ctx.plan(d32, CAM, grad="fd", phi="mean", normals=outs, masks=masks)
-    assert plan.kernels() == 2
+    plan = ctx.plan(d32, CAM, grad="fd", phi=phi, normals=outs, masks=masks)
+    assert _forms(plan.kernel_names()) == bound and plan.kernels() == len(bound)
     plan.close()
 
 

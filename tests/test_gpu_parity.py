@@ -147,10 +147,34 @@ def test_refine_all_path_is_tight(torch, tfn, ctx, grad, phi):
         assert st["over"] == 0 or phi == "median"
 
 
+def test_refinement_queue_takes_every_flagged_pixel(torch, tfn, ctx):
+    # the FD mean refines its flagged pixels in its own kernel, 32 at a time from a per-warp queue:
+    # with every pixel flagged, each warp fills and drains its queue many times per item, across
+    # frames of different sizes (a ragged frame among 40 full ones keeps the default tile shape),
+    # and the queue's last, partial round runs after the warp's last item
+    imgs = list(scenes.noisy_batch(40, seed0=960))
+    frames = [(img, scenes.CAMERA) for img in imgs] + depth_frames([(67, 131), (200, 333)], 970)
+    ctx.refined_pixels()
+    n, m = run_batch(torch, tfn, ctx, frames, grad="fd", phi="mean", flags=tfn.TFN_FLAG_REFINE_ALL)
+    refined = ctx.refined_pixels()
+    evaluable = sum(int((mk == 1).sum()) for mk in m)
+    assert all(set(np.unique(mk).tolist()) <= {0, 1} for mk in m), "a refined pixel has mask bit 1"
+    assert 0.9 * evaluable < refined <= evaluable, (refined, evaluable)  # (flat pixels are not refined)
+    for k in (0, 39, 40, 41):
+        img, cam = frames[k]
+        st = compare(n[k], m[k], img, cam, grad="fd", phi="mean", tol=1e-5)
+        assert st["over"] == 0
+    # and without the flag (the usual few flagged pixels), against the oracle
+    n2, m2 = run_batch(torch, tfn, ctx, frames, grad="fd", phi="mean")
+    for k in (0, 40, 41):
+        img, cam = frames[k]
+        compare(n2[k], m2[k], img, cam, grad="fd", phi="mean")
+
+
 @pytest.mark.parametrize("phi", PHIS)
 def test_refinement_list_overflow_scans_the_mask(torch, tfn, ctx, phi):
-    # every pixel of 40 noisy 480x640 frames flagged (Sobel: the filters other than FD refine in a
-    # second kernel): about 12M, past the 262144 entries of the launch's refinement list, so the
+    # every pixel of 40 noisy 480x640 frames flagged (Sobel: the filters other than the FD mean
+    # refine in a second kernel): about 12M, past the 262144 entries of the launch's refinement list, so the
     # refinement kernel finds them by their mask bit instead.  40 frames take the default tile
     # shape (a launch of fewer items would refine in place).
     imgs = scenes.noisy_batch(40, seed0=950)

@@ -6,8 +6,9 @@ synchronise the device) and cannot create a context.  These tests check,
 through the C ABI, that the allocation-free entry point gives exactly the
 normals and masks of tfn_normals_batch on calls in a row (a later call must
 not see an earlier call's leftovers in the shared scratch array), including a
-call large enough to take the default tile shape and so the refinement kernel
-and the scratch's refinement list; that one of its frames matches the FP64
+call large enough to take the default tile shape (for the Scharr median the
+refinement kernel and the scratch's refinement list, for the FD mean the
+kernel's own refinement queue); that one of its frames matches the FP64
 oracle; that it refuses more frames than its scratch holds; and that it
 refuses to run while its stream is being captured.  The file is named so that
 pytest runs it last.
@@ -61,7 +62,7 @@ def _noalloc(torch, tfn, frames, grad, phi):
 
 
 # call 1: three small frames of mixed sizes (the short-item shape, refining in place);
-# call 2: 40 full frames (the default shape: refinement kernel and the scratch's list);
+# call 2: 40 full frames (the default shape; Scharr median: refinement kernel and the scratch's list);
 # call 3: five small frames again, after the large call's list use
 CALLS = [(7100, [(67, 131), (480, 640), (33, 64)]), (7200, [(480, 640)] * 40), (7300, [(120, 96)] * 5)]
 

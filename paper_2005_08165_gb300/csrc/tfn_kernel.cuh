@@ -435,6 +435,10 @@ __device__ __noinline__ Vec3 refine_pixel(float z00, float z01, float z02, float
 // samples (|delta| >= 2^-39, so delta^2 >= 2^-78) by 2^-32.
 constexpr float kEdgeEps = 7.703719777548943e-34f;
 
+// 2^-60: the one-pass FD mean's n_z' offset that gives a flat pixel its
+// (0, 0, -1) without a test (row_step2).
+constexpr float kFlatEps = 8.673617379884035e-19f;
+
 // r = 1/delta and k = delta * r (1 for delta != 0, 0 for delta == 0) without
 // a branch: delta / (delta^2 + eps) is 1/delta to a relative 2^-32 for every
 // non-zero difference of valid samples and exactly 0 for delta == 0, which is
@@ -1104,8 +1108,20 @@ __device__ __forceinline__ void row_step2(const Row<KIND, GRAD> &P, const Row<KI
         const f2 nxp = PHI == PHI_MEAN ? mul2(mul2(scale, fx2), gu) : mul2(fx2, gu);
         const f2 nyp = PHI == PHI_MEAN ? mul2(mul2(scale, fy2), gv) : mul2(fy2, gv);
         const f2 Q = PHI == PHI_MEAN ? fma2(scale, A, mF) : add2(A, mF);  // -n_z'
-        // (a non-evaluable pixel's median may be a +-inf sentinel: keep n' finite so that rs = 0 zeroes it)
-        const f2 nzp = pk((flat[0] || !ev_ok[0]) ? 1.f : -Q.x, (flat[1] || !ev_ok[1]) ? 1.f : -Q.y);
+        f2 nzp;
+        if constexpr (one_pass) {
+            // Sec. III special case without a test: n_z' = kFlatEps - Q.  A flat
+            // pixel (G_u = G_v = 0) has n' = (0, 0, kFlatEps) exactly, so the
+            // output below is exactly (0, 0, -1) (rsqrt of kFlatEps^2 = 2^-120 is
+            // exact); any other pixel has |n'| >= m fx |G_u| or m fy |G_v|, far
+            // above 2^-60, and nz' moves only where |Q| < 2^-35, by less than
+            // 2^-33 of |n'|.  Every value here is finite for the one-pass
+            // quotients, so a non-evaluable pixel is still zeroed through rs.
+            nzp = sub2(bc(kFlatEps), Q);
+        } else {
+            // (a non-evaluable pixel's median may be a +-inf sentinel: keep n' finite so that rs = 0 zeroes it)
+            nzp = pk((flat[0] || !ev_ok[0]) ? 1.f : -Q.x, (flat[1] || !ev_ok[1]) ? 1.f : -Q.y);
+        }
         const f2 nn = fma2(nxp, nxp, fma2(nyp, nyp, mul2(nzp, nzp)));
         const f2 rs = pk(ev_ok[0] ? rsqrt_approx(nn.x) : 0.f, ev_ok[1] ? rsqrt_approx(nn.y) : 0.f);
         const f2 lim = NOREF ? bc(0.f) : mul2(bc(thr), mul2(nn, rs));
@@ -1115,7 +1131,10 @@ __device__ __forceinline__ void row_step2(const Row<KIND, GRAD> &P, const Row<KI
             const float r = lane_of(rs, l);
             // refine unless bound <= thr |n'|; written so that a NaN (|n'|
             // overflowed) also refines, and thr < 0 refines every pixel
-            const bool refine = !NOREF && ev_ok[l] && !flat[l] && !(mbound[l] <= lane_of(lim, l));
+            // (one-pass mean: an evaluable pixel is flat exactly when its bound is
+            // 0, every weight being 0; otherwise a kept neighbour makes it > 0)
+            const bool notflat = one_pass ? mbound[l] > 0.f : !flat[l];
+            const bool refine = !NOREF && ev_ok[l] && notflat && !(mbound[l] <= lane_of(lim, l));
             // -n'/|n'|, with +0 (not -0) for zero components and for non-evaluable pixels
             ox[k] = __fmaf_rn(-lane_of(nxp, l), r, 0.f);
             oy[k] = __fmaf_rn(-lane_of(nyp, l), r, 0.f);

@@ -340,6 +340,34 @@ def test_special_values_all_holes_constant(torch, tfn, ctx):
     assert (m[0] == 0).all() and (n[0] == 0).all()
 
 
+@pytest.mark.parametrize("kind", ["f32", "f16"])
+def test_plateaus_give_exactly_the_special_case_at_the_default_shape(torch, tfn, ctx, kind):
+    # The FD mean's kernel (one-pass gradients) gives a flat pixel its [0, 0, -1] without a test,
+    # through n_z' = 2^-60 - Q: on 40 noisy 480x640 frames (the default tile shape) with constant-depth
+    # plateaus, every evaluable pixel whose 4 axis neighbours share its depth must come out as exactly
+    # (0, 0, -1), and every frame must still match the oracle.  FP16 depth runs the kernel without the
+    # bound, FP32 the one with it (and its refinement queue).
+    imgs = scenes.noisy_batch(40, seed0=980)
+    for k, img in enumerate(imgs):
+        y0, x0 = 37 + 9 * k, 41 + 11 * k
+        img[y0:y0 + 60, x0:x0 + 90] = np.float32(1.25 + 0.125 * k)  # (exact in FP16 too)
+        img[y0 + 70:y0 + 80, :] = np.float32(3.5)
+    if kind == "f16":
+        imgs = imgs.astype(np.float16)
+    frames = [(img, scenes.CAMERA) for img in imgs]
+    n, m = run_batch(torch, tfn, ctx, frames, grad="fd", phi="mean", output="f32")
+    for k in (0, 17, 39):
+        img = imgs[k]
+        z = img.astype(np.float32)
+        c = z[1:-1, 1:-1]
+        flat = (z[1:-1, :-2] == c) & (z[1:-1, 2:] == c) & (z[:-2, 1:-1] == c) & (z[2:, 1:-1] == c)
+        flat &= m[k][1:-1, 1:-1] == 1
+        assert flat.sum() > 5000
+        nk = n[k][:, 1:-1, 1:-1]
+        assert (nk[0][flat] == 0.0).all() and (nk[1][flat] == 0.0).all() and (nk[2][flat] == -1.0).all()
+        compare(n[k], m[k], img, scenes.CAMERA, grad="fd", phi="mean")
+
+
 def test_invalid_arguments_are_rejected(torch, tfn, ctx):
     img = tfn.empty_image((16, 16), torch.float32)
     img.fill_(1.0)

@@ -362,7 +362,8 @@ tfn_status make_launch(int kind, const tfn_method &m, int cfg, bool noref, const
     L.grid = std::max(0, std::min((total_tiles + nw - 1) / nw, per_sm * num_sms));
     // the refinement kernel of this method (none for PlanePCA, which never flags a pixel)
     L.rf = nullptr;
-    if (grad != GRAD_PLANEPCA && !noref && !refines_in_kernel(cfg, grad, method_phi(m)) && !(L.rf = refiner_for(kind, grad, method_phi(m))))
+    if (grad != GRAD_PLANEPCA && !noref && !refines_in_kernel(cfg, grad, method_phi(m)) &&
+        !(L.rf = refiner_for(kind, grad, method_phi(m))))
         return TFN_ERR_UNSUPPORTED;
     // its grid: the flagged pixels (about one per thousand on noisy frames),
     // as many threads as fit on the GPU at once: each refines its pixels one

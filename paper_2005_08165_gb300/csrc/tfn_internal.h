@@ -118,10 +118,10 @@ constexpr bool refines_in_place(int c) { return c == kSmallCfg; }
 // are rare (about 2 per 128 x 30 item on noisy frames), so a warp drains its
 // queue about once in a launch, where a second kernel costs a launch, its
 // latency-bound reads and its fixed time (256 x 480x640 frames: 0.341 ->
-// 0.334 ms a pass).  The FD median flags almost nothing and ran 0.5% slower
-// with the queue's code; the smoothed 3x3 filters and the 5x5 ones keep the
-// list too, as their shared memory already holds as many CTAs per SM as it
-// can.
+// 0.334 ms a pass).  The FD median flags almost nothing and keeps the list
+// (its refinement kernel finds it empty); the smoothed 3x3 filters and the
+// 5x5 ones keep it too, as their shared memory already holds as many CTAs per
+// SM as it can.
 constexpr bool refines_by_queue(int c, int grad, int phi)
 {
     return c != kSmallCfg && grad == GRAD_FD && phi == PHI_MEAN;

@@ -971,6 +971,13 @@ __device__ __forceinline__ void row_step2(const Row<KIND, GRAD> &P, const Row<KI
     static_assert(grad_is_pair(GRAD), "row_step2 runs the 3x3 filters");
     constexpr bool disp = KindTraits<KIND>::disparity;
     constexpr bool one_pass = GRAD == GRAD_FD && kFdOnePassMean && PHI == PHI_MEAN && !disp;
+    // Whether the mean's special case and flat test come from n_z' = kFlatEps -
+    // Q and the bound (below).  For FD and the symmetric filters a non-zero
+    // gradient always has a kept neighbour in a pair of non-zero weight.  The
+    // weighted family keeps the explicit test: with w0 != w2 that need not
+    // hold, and its row step spilled with the change (0.6% slower; Sobel's
+    // 2.5% faster).
+    constexpr bool flat_by_bound = PHI == PHI_MEAN && !NOREF && GRAD != GRAD_WEIGHTED;
     const f2 vc2 = bc(vc), fx2 = bc(fx), fy2 = bc(fy);
     // the edges to column c-1 of pixels c = 1, 3 (the next pair's come from this pair)
     EdgeR2 ehm = edge_recip2(sub2(zpair(C, 1), zpair(C, 0)));  // (y, c-1) -> (y, c)
@@ -1118,6 +1125,11 @@ __device__ __forceinline__ void row_step2(const Row<KIND, GRAD> &P, const Row<KI
             // 2^-33 of |n'|.  Every value here is finite for the one-pass
             // quotients, so a non-evaluable pixel is still zeroed through rs.
             nzp = sub2(bc(kFlatEps), Q);
+        } else if constexpr (flat_by_bound) {
+            // The same for the other means, whose non-evaluable pixels may
+            // carry a NaN gradient part (from two hole taps) and so keep the
+            // select on evaluability: the flat test's four compares go.
+            nzp = pk(ev_ok[0] ? __fsub_rn(kFlatEps, Q.x) : 1.f, ev_ok[1] ? __fsub_rn(kFlatEps, Q.y) : 1.f);
         } else {
             // (a non-evaluable pixel's median may be a +-inf sentinel: keep n' finite so that rs = 0 zeroes it)
             nzp = pk((flat[0] || !ev_ok[0]) ? 1.f : -Q.x, (flat[1] || !ev_ok[1]) ? 1.f : -Q.y);
@@ -1131,9 +1143,10 @@ __device__ __forceinline__ void row_step2(const Row<KIND, GRAD> &P, const Row<KI
             const float r = lane_of(rs, l);
             // refine unless bound <= thr |n'|; written so that a NaN (|n'|
             // overflowed) also refines, and thr < 0 refines every pixel
-            // (one-pass mean: an evaluable pixel is flat exactly when its bound is
-            // 0, every weight being 0; otherwise a kept neighbour makes it > 0)
-            const bool notflat = one_pass ? mbound[l] > 0.f : !flat[l];
+            // (the means but the weighted family's: an evaluable pixel is flat
+            // exactly when its bound is 0, every weight being 0; otherwise a
+            // kept neighbour makes it > 0)
+            const bool notflat = flat_by_bound ? mbound[l] > 0.f : !flat[l];
             const bool refine = !NOREF && ev_ok[l] && notflat && !(mbound[l] <= lane_of(lim, l));
             // -n'/|n'|, with +0 (not -0) for zero components and for non-evaluable pixels
             ox[k] = __fmaf_rn(-lane_of(nxp, l), r, 0.f);

@@ -100,3 +100,26 @@ def test_null_handles_of_tuner_and_server_are_rejected(tfn, tmp_path):
 def test_library_links_no_torch(tfn):
     out = subprocess.check_output(["ldd", tfn.LIB_PATH], text=True)
     assert "torch" not in out and "c10" not in out
+
+
+def test_each_kernel_instance_is_compiled_once(tfn):
+    # The kernels are instantiated across translation units (per input kind, and the FD mean's with
+    # the error bound apart from the rest): every (kind, filter, Phi, tile shape, NOREF) instance
+    # must exist exactly once, and the FD mean, which refines in its own kernel, has no refinement
+    # kernel.  Host-side launch stubs name the instances.
+    import shutil
+    if not shutil.which("nm"):
+        pytest.skip("nm not available")
+    out = subprocess.check_output(["nm", "-C", tfn.LIB_PATH], text=True)
+    stubs = re.findall(r" t void tfn::dev::(normals_kernel|refine_kernel)<([^>]*)>\(tfn::LaunchArgs\)$", out, re.M)
+    normals = [tuple(int(x) if x.strip().lstrip("-").isdigit() else x.strip() for x in a.split(","))
+               for k, a in stubs if k == "normals_kernel"]
+    refiners = [tuple(int(x) for x in a.split(",")) for k, a in stubs if k == "refine_kernel"]
+    assert len(normals) == len(set(normals)) and len(refiners) == len(set(refiners))
+    kinds, shapes = range(4), range(tfn.tfn_tile_shape_count())
+    want = {(k, g, p, c, "false") for k in kinds for g in (0, 1, 2, 3, 4, 5) for p in (0, 1) for c in shapes}
+    want |= {(k, 9, 0, c, "false") for k in kinds for c in shapes}  # PlanePCA
+    want |= {(1, 0, p, c, "true") for p in (0, 1) for c in shapes}  # FP16 depth, FD, without the bound
+    assert set(normals) == want
+    assert set(refiners) == {(k, g, p) for k in kinds for g in (0, 1, 2, 3, 4, 5) for p in (0, 1)} - \
+        {(k, 0, 0) for k in kinds}
